@@ -1,0 +1,158 @@
+"""CPU oracle for the delayed Slater-determinant update (fp64, plain C).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark are the only callers. The product path never imports it.
+
+Three readings of the paper, all in its column convention (one column of the
+Slater matrix per electron, Sec. I), each loaded from qmc_oracle.c:
+  BRUTE   ratio = det(M_new) / det(M) by two LU determinants (direct calculation)
+  SM      ratio by the matrix determinant lemma (Eq. 1), inverse by the
+          Sherman-Morrison rank-1 formula (Eq. 2)
+  DELAYED ratios by look-ahead determinants of I_k + V'M^{-1}U (Eq. 3), queued
+          accepted moves applied en bloc by Sherman-Morrison-Woodbury (Eq. 4)
+          when k reaches K or the sweep ends (Sec. II)
+plus LU log|det| and LU inverse. Inputs and outputs use the row convention of
+the library (row j of A = electron j); inverses come back in the column-major
+layout of A^{-1} (row c of the returned array is column c of A^{-1}).
+
+Pins (tests/test_oracle_pins.py) tie every function to something other than
+itself: Leibniz-formula determinants, exact rational arithmetic, closed forms
+(Hilbert, Vandermonde, diagonal, permutation) and the paper's invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qmc_oracle.c")
+_LIB = os.path.join(_HERE, "libqmc_oracle.so")
+
+BRUTE, SM, DELAYED = 0, 1, 2
+OK, ERR_ARG, ERR_SINGULAR, ERR_OOM = 0, 1, 3, 4
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp, ip, i8p, u8p = (ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_uint8))
+        lib.oracle_slogdet.argtypes = [ctypes.c_int, dp, dp, ip]
+        lib.oracle_inverse.argtypes = [ctypes.c_int, dp, dp]
+        lib.oracle_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, dp, dp, dp, i8p, dp, u8p, dp, dp, dp, ip,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+        lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                     ip, dp, u8p, u8p, dp, dp, dp, dp, ip]
+        for f in (lib.oracle_slogdet, lib.oracle_inverse, lib.oracle_sweeps, lib.oracle_moves):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def slogdet(a):
+    """(sign, log|det a|) by LU with partial pivoting."""
+    a = _f64(a)
+    n = a.shape[0]
+    la, sg = ctypes.c_double(), ctypes.c_int()
+    st = _load().oracle_slogdet(n, _p(a, ctypes.c_double), ctypes.byref(la), ctypes.byref(sg))
+    if st not in (OK, ERR_SINGULAR):
+        raise OracleError("oracle_slogdet status %d" % st)
+    return sg.value, la.value
+
+
+def inverse(a):
+    """a^{-1} (row-major) by LU and triangular solves."""
+    a = _f64(a)
+    n = a.shape[0]
+    out = np.zeros((n, n))
+    st = _load().oracle_inverse(n, _p(a, ctypes.c_double), _p(out, ctypes.c_double))
+    if st != OK:
+        raise OracleError("oracle_inverse status %d" % st)
+    return out
+
+
+def inverse_colmajor(a):
+    """A^{-1} in the library's layout: row c holds column c of A^{-1}."""
+    return np.ascontiguousarray(inverse(a).T)
+
+
+def sweeps(method, A0, G, U, sigma, K=1, override=None):
+    """Metropolis sweeps from A0 with Gaussians G[s, j, :] and uniforms U[s, j].
+
+    Returns dict(ratios, accepted, A, Ainv (column-major layout), logabs, sign,
+    near_ties)."""
+    A0 = _f64(A0)
+    n = A0.shape[0]
+    G = _f64(G).reshape(-1, n, n)
+    ns = G.shape[0]
+    U = _f64(U).reshape(ns, n)
+    ov = None if override is None else np.ascontiguousarray(override, dtype=np.int8).reshape(ns, n)
+    ratios = np.zeros((ns, n))
+    acc = np.zeros((ns, n), dtype=np.uint8)
+    A = np.zeros((n, n))
+    Ainv = np.zeros((n, n))
+    la, sg, nt = ctypes.c_double(), ctypes.c_int(), ctypes.c_longlong()
+    st = _load().oracle_sweeps(method, n, K, ns, float(sigma), _p(A0, ctypes.c_double),
+                               _p(G, ctypes.c_double), _p(U, ctypes.c_double),
+                               _p(ov, ctypes.c_int8), _p(ratios, ctypes.c_double),
+                               _p(acc, ctypes.c_uint8), _p(A, ctypes.c_double),
+                               _p(Ainv, ctypes.c_double), ctypes.byref(la), ctypes.byref(sg),
+                               ctypes.byref(nt))
+    if st != OK:
+        raise OracleError("oracle_sweeps status %d" % st)
+    return dict(ratios=ratios, accepted=acc.astype(bool), A=A, Ainv=Ainv,
+                logabs=la.value, sign=sg.value, near_ties=nt.value)
+
+
+def moves(method, A0, elec, vrows, decisions, K=1, flush_after=None):
+    """Explicit moves with given decisions. Returns dict(ratios, A, Ainv, logabs, sign)."""
+    A0 = _f64(A0)
+    n = A0.shape[0]
+    elec = np.ascontiguousarray(elec, dtype=np.int32)
+    m = elec.shape[0]
+    vrows = _f64(vrows).reshape(m, n)
+    dec = np.ascontiguousarray(decisions, dtype=np.uint8).reshape(m)
+    fa = None if flush_after is None else np.ascontiguousarray(flush_after, dtype=np.uint8)
+    ratios = np.zeros(m)
+    A = np.zeros((n, n))
+    Ainv = np.zeros((n, n))
+    la, sg = ctypes.c_double(), ctypes.c_int()
+    st = _load().oracle_moves(method, n, K, m, _p(A0, ctypes.c_double),
+                              elec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              _p(vrows, ctypes.c_double), _p(dec, ctypes.c_uint8),
+                              _p(fa, ctypes.c_uint8), _p(ratios, ctypes.c_double),
+                              _p(A, ctypes.c_double), _p(Ainv, ctypes.c_double),
+                              ctypes.byref(la), ctypes.byref(sg))
+    if st != OK:
+        raise OracleError("oracle_moves status %d" % st)
+    return dict(ratios=ratios, A=A, Ainv=Ainv, logabs=la.value, sign=sg.value)

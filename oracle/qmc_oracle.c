@@ -1,0 +1,443 @@
+/*
+ * qmc_oracle.c -- plain, slow, fp64 CPU oracle for the delayed Slater-determinant
+ * update (McDaniel, D'Azevedo, Li, Wong, Kent, "Delayed Slater determinant update
+ * algorithms for high efficiency quantum Monte Carlo").
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library. It shares no code, header,
+ * table or helper with the CUDA path.
+ *
+ * Convention: the paper's. The Slater matrix M has one COLUMN per electron,
+ * M[i][k] = phi_i(r_k) (Sec. I). A move of electron k replaces column k; the
+ * change is the column vector u = (new column) - (old column), so
+ * M_new = M + u e_k' (Sec. I). The caller's matrices use the transposed layout
+ * (one row per electron, A = M'), so every entry point transposes on the way in
+ * and out; an inverse is returned as Minv stored row-major, which is exactly
+ * A^{-1} stored column-major.
+ *
+ * Three implementations of one sweep, each a different reading of the paper:
+ *   O1 brute force: ratio det(M_new)/det(M) from two LU determinants.
+ *   O2 Sherman-Morrison: ratio by the matrix determinant lemma (Eq. 1), inverse
+ *      by the rank-1 Sherman-Morrison formula (Eq. 2).
+ *   O3 delayed: ratios by look-ahead -- the explicit determinant of
+ *      I_k + V' M^{-1} U (Eq. 3) divided by the previous one -- and the queued
+ *      accepted moves applied en bloc by Sherman-Morrison-Woodbury (Eq. 4) when k
+ *      reaches K or the sweep ends (Sec. II). Rejected moves change nothing.
+ *
+ * Metropolis rule: accept iff u < min(1, r^2) (the acceptance probability is
+ * the squared determinant ratio, Sec. I). A per-move override (-1 decide, 0
+ * reject, 1 accept) replays decisions; |min(1, r^2) - u| < 1e-10 counts as a
+ * near tie.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_SINGULAR 3
+#define OR_ERR_OOM 4
+
+#define METHOD_BRUTE 0
+#define METHOD_SM 1
+#define METHOD_DELAYED 2
+
+static const double NEAR_TIE = 1e-10;
+
+/* ------------------------------------------------------------------------ */
+/* Dense LU with partial pivoting (textbook Doolittle, row interchanges).      */
+/* a: n x n row-major, overwritten by L (unit, strictly below) and U.          */
+/* perm[c]: row exchanged with row c at step c. Pivot = largest |a_ic|, first  */
+/* index on ties. Returns 1 if an exactly zero pivot appears.                  */
+/* ------------------------------------------------------------------------ */
+static int lu_factor(int n, double *a, int *perm, int *nswaps)
+{
+    int singular = 0;
+    *nswaps = 0;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        double best = fabs(a[(size_t)c * n + c]);
+        for (int i = c + 1; i < n; ++i) {
+            double v = fabs(a[(size_t)i * n + c]);
+            if (v > best) { best = v; p = i; }
+        }
+        perm[c] = p;
+        if (p != c) {
+            for (int j = 0; j < n; ++j) {
+                double t = a[(size_t)c * n + j];
+                a[(size_t)c * n + j] = a[(size_t)p * n + j];
+                a[(size_t)p * n + j] = t;
+            }
+            ++*nswaps;
+        }
+        double piv = a[(size_t)c * n + c];
+        if (piv == 0.0) { singular = 1; continue; }
+        for (int i = c + 1; i < n; ++i) {
+            double l = a[(size_t)i * n + c] / piv;
+            a[(size_t)i * n + c] = l;
+            for (int j = c + 1; j < n; ++j)
+                a[(size_t)i * n + j] -= l * a[(size_t)c * n + j];
+        }
+    }
+    return singular;
+}
+
+/* log|det a| and sign(det a) of an n x n row-major matrix (a is not modified). */
+int oracle_slogdet(int n, const double *a, double *logabs, int *sign)
+{
+    if (n < 0) return OR_ERR_ARG;
+    if (n == 0) { *logabs = 0.0; *sign = 1; return OR_OK; }
+    double *lu = malloc(sizeof(double) * (size_t)n * n);
+    int *perm = malloc(sizeof(int) * (size_t)n);
+    if (!lu || !perm) { free(lu); free(perm); return OR_ERR_OOM; }
+    memcpy(lu, a, sizeof(double) * (size_t)n * n);
+    int nswaps;
+    int singular = lu_factor(n, lu, perm, &nswaps);
+    double s = (nswaps % 2) ? -1.0 : 1.0, la = 0.0;
+    for (int c = 0; c < n; ++c) {
+        double d = lu[(size_t)c * n + c];
+        if (d < 0) s = -s;
+        la += log(fabs(d));
+    }
+    free(lu); free(perm);
+    if (singular) { *logabs = -INFINITY; *sign = 0; return OR_ERR_SINGULAR; }
+    *logabs = la;
+    *sign = (int)s;
+    return OR_OK;
+}
+
+/* inv = a^{-1} (both n x n row-major) by LU and two triangular solves per
+ * column of the identity. */
+int oracle_inverse(int n, const double *a, double *inv)
+{
+    if (n < 0) return OR_ERR_ARG;
+    if (n == 0) return OR_OK;
+    double *lu = malloc(sizeof(double) * (size_t)n * n);
+    int *perm = malloc(sizeof(int) * (size_t)n);
+    double *x = malloc(sizeof(double) * (size_t)n);
+    if (!lu || !perm || !x) { free(lu); free(perm); free(x); return OR_ERR_OOM; }
+    memcpy(lu, a, sizeof(double) * (size_t)n * n);
+    int nswaps;
+    if (lu_factor(n, lu, perm, &nswaps)) { free(lu); free(perm); free(x); return OR_ERR_SINGULAR; }
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) x[i] = (i == col) ? 1.0 : 0.0;
+        for (int c = 0; c < n; ++c) {          /* apply the row interchanges */
+            int p = perm[c];
+            if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
+        }
+        for (int i = 0; i < n; ++i)             /* L y = P e_col */
+            for (int j = 0; j < i; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
+        for (int i = n - 1; i >= 0; --i) {      /* U x = y */
+            for (int j = i + 1; j < n; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
+            x[i] /= lu[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = x[i];
+    }
+    free(lu); free(perm); free(x);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walker state in the paper's convention.                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n, K, method;
+    double *M;      /* current Slater matrix, column k = electron k           */
+    double *Minv;   /* SM/brute: inverse of M. Delayed: inverse at last flush */
+    double logabs;  /* running log|det M|                                     */
+    double sign;    /* running sign of det M                                  */
+    /* delayed (O3) queue */
+    int k;          /* queued accepted moves                                  */
+    int *elec;      /* electron of queued move m (columns of V are e_elec[m]) */
+    double *U;      /* n x K, column m = change of column elec[m] (stride K)  */
+    double *S;      /* (K+1) x (K+1): I + V' Minv U for the queue + proposal  */
+    double blk_logabs, blk_sign; /* det of the k x k block (product of ratios) */
+    /* pending proposal */
+    int prop_j;
+    double *prop_col;  /* proposed new column                                 */
+    double *u;         /* change u = prop_col - M[:, j]                        */
+    double prop_logabs, prop_sign; /* look-ahead: det of the (k+1) block      */
+    double ratio;
+} walker;
+
+static void walker_free(walker *w)
+{
+    free(w->M); free(w->Minv); free(w->elec); free(w->U); free(w->S);
+    free(w->prop_col); free(w->u);
+}
+
+static int walker_init(walker *w, int n, int K, int method, const double *A_rows)
+{
+    memset(w, 0, sizeof(*w));
+    w->n = n; w->K = K > 0 ? K : 1; w->method = method;
+    size_t nn = (size_t)n * n;
+    w->M = malloc(sizeof(double) * (nn ? nn : 1));
+    w->Minv = malloc(sizeof(double) * (nn ? nn : 1));
+    w->elec = malloc(sizeof(int) * (size_t)w->K);
+    w->U = malloc(sizeof(double) * ((size_t)n * w->K + 1));
+    w->S = malloc(sizeof(double) * (size_t)(w->K + 1) * (w->K + 1));
+    w->prop_col = malloc(sizeof(double) * ((size_t)n + 1));
+    w->u = malloc(sizeof(double) * ((size_t)n + 1));
+    if (!w->M || !w->Minv || !w->elec || !w->U || !w->S || !w->prop_col || !w->u) {
+        walker_free(w); return OR_ERR_OOM;
+    }
+    for (int i = 0; i < n; ++i)          /* M = A': column k = row k of A */
+        for (int k = 0; k < n; ++k) w->M[(size_t)i * n + k] = A_rows[(size_t)k * n + i];
+    int sg;
+    int st = oracle_slogdet(n, w->M, &w->logabs, &sg);
+    if (st) { walker_free(w); return st; }
+    w->sign = sg;
+    st = oracle_inverse(n, w->M, w->Minv);
+    if (st) { walker_free(w); return st; }
+    w->k = 0;
+    w->blk_logabs = 0.0; w->blk_sign = 1.0;
+    return OR_OK;
+}
+
+/* Determinant of the leading m x m block of the (K+1)-stride matrix S. */
+static void small_slogdet(const double *S, int stride, int m, double *logabs, double *sign)
+{
+    double *t = malloc(sizeof(double) * (size_t)(m > 0 ? m * m : 1));
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) t[i * m + j] = S[i * stride + j];
+    int sg;
+    if (oracle_slogdet(m, t, logabs, &sg) != OR_OK) { *logabs = -INFINITY; *sign = 0.0; }
+    else *sign = sg;
+    free(t);
+}
+
+/* Ratio det(M_new)/det(M) for electron j moving to new column `col`. */
+static double walker_propose(walker *w, int j, const double *col)
+{
+    int n = w->n;
+    w->prop_j = j;
+    memcpy(w->prop_col, col, sizeof(double) * n);
+    for (int i = 0; i < n; ++i) w->u[i] = col[i] - w->M[(size_t)i * n + j];
+
+    if (w->method == METHOD_BRUTE) {
+        /* Direct calculation: det of the moved matrix over det of M. */
+        double *Mn = malloc(sizeof(double) * (size_t)n * n);
+        memcpy(Mn, w->M, sizeof(double) * (size_t)n * n);
+        for (int i = 0; i < n; ++i) Mn[(size_t)i * n + j] = col[i];
+        double la_new, la_old; int s_new, s_old;
+        oracle_slogdet(n, Mn, &la_new, &s_new);
+        oracle_slogdet(n, w->M, &la_old, &s_old);
+        free(Mn);
+        w->ratio = (s_new == 0) ? 0.0 : (double)(s_new * s_old) * exp(la_new - la_old);
+    } else if (w->method == METHOD_SM) {
+        /* Eq. 1: det(M + u e_j')/det(M) = 1 + e_j' Minv u. */
+        double t = 1.0;
+        for (int i = 0; i < n; ++i) t += w->Minv[(size_t)j * n + i] * w->u[i];
+        w->ratio = t;
+    } else {
+        /* Eq. 3 look-ahead. The queue gives U (changes) and V (unit columns
+         * e_elec[m]); the proposal appends u and e_j. Entry (a, b) of
+         * I + V' Minv U is delta_ab + row elec[a] of Minv dotted with column b
+         * of U. Rows/columns 0..k-1 were filled when the queue grew; fill the
+         * new border and take the explicit determinant of the (k+1) block. */
+        int k = w->k, st = w->K + 1;
+        const double *urow_j = w->Minv + (size_t)j * n;     /* e_j' Minv */
+        for (int b = 0; b < k; ++b) {                         /* new row k */
+            double t = 0.0;
+            for (int i = 0; i < n; ++i) t += urow_j[i] * w->U[(size_t)i * w->K + b];
+            w->S[k * st + b] = t;
+        }
+        for (int a = 0; a < k; ++a) {                         /* new column k */
+            const double *row = w->Minv + (size_t)w->elec[a] * n;
+            double t = 0.0;
+            for (int i = 0; i < n; ++i) t += row[i] * w->u[i];
+            w->S[a * st + k] = t;
+        }
+        double t = 1.0;
+        for (int i = 0; i < n; ++i) t += urow_j[i] * w->u[i];
+        w->S[k * st + k] = t;
+        small_slogdet(w->S, st, k + 1, &w->prop_logabs, &w->prop_sign);
+        if (w->prop_sign == 0.0) w->ratio = 0.0;
+        else w->ratio = w->prop_sign * w->blk_sign * exp(w->prop_logabs - w->blk_logabs);
+    }
+    return w->ratio;
+}
+
+/* Apply the queued moves to Minv by Sherman-Morrison-Woodbury (Eq. 4):
+ * Minv <- Minv - (Minv U) (I_k + V' Minv U)^{-1} (V' Minv). */
+static int walker_flush(walker *w)
+{
+    if (w->method != METHOD_DELAYED || w->k == 0) return OR_OK;
+    int n = w->n, k = w->k, st = w->K + 1, KK = w->K;
+    double *S = malloc(sizeof(double) * (size_t)k * k);
+    double *Sinv = malloc(sizeof(double) * (size_t)k * k);
+    double *MU = malloc(sizeof(double) * (size_t)n * k);     /* Minv U, n x k */
+    double *VM = malloc(sizeof(double) * (size_t)k * n);     /* V' Minv, k x n */
+    double *X = malloc(sizeof(double) * (size_t)n * k);      /* (Minv U) Sinv */
+    if (!S || !Sinv || !MU || !VM || !X) {
+        free(S); free(Sinv); free(MU); free(VM); free(X); return OR_ERR_OOM;
+    }
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) S[a * k + b] = w->S[a * st + b];
+    int status = oracle_inverse(k, S, Sinv);
+    if (status == OR_OK) {
+        for (int i = 0; i < n; ++i)
+            for (int b = 0; b < k; ++b) {
+                double t = 0.0;
+                for (int l = 0; l < n; ++l) t += w->Minv[(size_t)i * n + l] * w->U[(size_t)l * KK + b];
+                MU[(size_t)i * k + b] = t;
+            }
+        for (int a = 0; a < k; ++a)
+            memcpy(VM + (size_t)a * n, w->Minv + (size_t)w->elec[a] * n, sizeof(double) * n);
+        for (int i = 0; i < n; ++i)
+            for (int b = 0; b < k; ++b) {
+                double t = 0.0;
+                for (int a = 0; a < k; ++a) t += MU[(size_t)i * k + a] * Sinv[a * k + b];
+                X[(size_t)i * k + b] = t;
+            }
+        for (int i = 0; i < n; ++i)
+            for (int l = 0; l < n; ++l) {
+                double t = 0.0;
+                for (int b = 0; b < k; ++b) t += X[(size_t)i * k + b] * VM[(size_t)b * n + l];
+                w->Minv[(size_t)i * n + l] -= t;
+            }
+        w->k = 0;
+        w->blk_logabs = 0.0; w->blk_sign = 1.0;
+    }
+    free(S); free(Sinv); free(MU); free(VM); free(X);
+    return status;
+}
+
+/* Accept the pending proposal. */
+static int walker_accept(walker *w)
+{
+    int n = w->n, j = w->prop_j;
+    double r = w->ratio;
+    if (!(r != 0.0) || !isfinite(r)) return OR_ERR_SINGULAR;
+    if (w->method == METHOD_SM) {
+        /* Eq. 2: Minv <- Minv - (Minv u)(1 + e_j' Minv u)^{-1}(e_j' Minv). */
+        double *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int l = 0; l < n; ++l) t += w->Minv[(size_t)i * n + l] * w->u[l];
+            x[i] = t;
+        }
+        memcpy(y, w->Minv + (size_t)j * n, sizeof(double) * n);
+        for (int i = 0; i < n; ++i)
+            for (int l = 0; l < n; ++l) w->Minv[(size_t)i * n + l] -= x[i] * y[l] / r;
+        free(x); free(y);
+    } else if (w->method == METHOD_DELAYED) {
+        int k = w->k;
+        for (int i = 0; i < n; ++i) w->U[(size_t)i * w->K + k] = w->u[i];
+        w->elec[k] = j;
+        w->blk_logabs = w->prop_logabs;
+        w->blk_sign = w->prop_sign;
+        w->k = k + 1;
+    }
+    for (int i = 0; i < n; ++i) w->M[(size_t)i * n + j] = w->prop_col[i];
+    w->logabs += log(fabs(r));
+    if (r < 0) w->sign = -w->sign;
+    if (w->method == METHOD_BRUTE) {
+        int st = oracle_inverse(n, w->M, w->Minv);
+        if (st) return st;
+    }
+    if (w->method == METHOD_DELAYED && w->k == w->K) return walker_flush(w);
+    return OR_OK;
+}
+
+static int in_queue(const walker *w, int j)
+{
+    for (int m = 0; m < w->k; ++m) if (w->elec[m] == j) return 1;
+    return 0;
+}
+
+static void walker_export(const walker *w, double *A_rows, double *Ainv_cm,
+                          double *logabs, int *sign)
+{
+    int n = w->n;
+    if (A_rows)
+        for (int k = 0; k < n; ++k)
+            for (int i = 0; i < n; ++i) A_rows[(size_t)k * n + i] = w->M[(size_t)i * n + k];
+    if (Ainv_cm) memcpy(Ainv_cm, w->Minv, sizeof(double) * (size_t)n * n);
+    if (logabs) *logabs = w->logabs;
+    if (sign) *sign = (int)w->sign;
+}
+
+static int decide(double r, double u, int override, long long *near_ties)
+{
+    double p = r * r;
+    if (p > 1.0) p = 1.0;
+    if (fabs(p - u) < NEAR_TIE) ++*near_ties;
+    if (override == 0) return 0;
+    if (override == 1) return 1;
+    return u < p;
+}
+
+/*
+ * One or more Metropolis sweeps. Electron j = 0..n-1 in order; the proposed
+ * row is v = a_j + sigma * g with a_j the CURRENT row j and g = G[s][j][:].
+ *   A0       n x n, row j = electron j (input)
+ *   G        nsweeps x n x n Gaussians, U nsweeps x n uniforms
+ *   override nsweeps x n (-1 decide, 0 reject, 1 accept) or NULL
+ * Outputs: ratios, accepted (nsweeps x n), final A rows, final inverse in the
+ * column-major layout of A^{-1}, running log|det| and sign, near-tie count.
+ * The delayed method flushes when k reaches K and at the end of every sweep.
+ */
+int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
+                  const double *A0, const double *G, const double *U,
+                  const signed char *override,
+                  double *ratios, unsigned char *accepted,
+                  double *A_out, double *Ainv_out, double *logabs, int *sign,
+                  long long *near_ties)
+{
+    if (n < 1 || nsweeps < 0 || (method == METHOD_DELAYED && K < 1)) return OR_ERR_ARG;
+    walker w;
+    int st = walker_init(&w, n, K, method, A0);
+    if (st) return st;
+    double *col = malloc(sizeof(double) * n);
+    *near_ties = 0;
+    for (int s = 0; s < nsweeps && st == OR_OK; ++s) {
+        for (int j = 0; j < n && st == OR_OK; ++j) {
+            const double *g = G + ((size_t)s * n + j) * n;
+            for (int i = 0; i < n; ++i) col[i] = w.M[(size_t)i * n + j] + sigma * g[i];
+            double r = walker_propose(&w, j, col);
+            size_t at = (size_t)s * n + j;
+            ratios[at] = r;
+            int ov = override ? override[at] : -1;
+            int acc = decide(r, U[at], ov, near_ties);
+            accepted[at] = (unsigned char)acc;
+            if (acc) st = walker_accept(&w);
+        }
+        if (st == OR_OK) st = walker_flush(&w);
+    }
+    if (st == OR_OK) walker_export(&w, A_out, Ainv_out, logabs, sign);
+    free(col);
+    walker_free(&w);
+    return st;
+}
+
+/*
+ * Explicit moves: move m proposes new row vrows[m] for electron elec[m]; the
+ * decision is given (decisions[m]: 1 accept, 0 reject). The delayed method
+ * flushes when k reaches K, before proposing an electron already queued, when
+ * flush_after[m] is set (may be NULL), and at the end.
+ */
+int oracle_moves(int method, int n, int K, int nmoves, const double *A0,
+                 const int *elec, const double *vrows,
+                 const unsigned char *decisions, const unsigned char *flush_after,
+                 double *ratios, double *A_out, double *Ainv_out,
+                 double *logabs, int *sign)
+{
+    if (n < 1 || nmoves < 0 || (method == METHOD_DELAYED && K < 1)) return OR_ERR_ARG;
+    walker w;
+    int st = walker_init(&w, n, K, method, A0);
+    if (st) return st;
+    for (int m = 0; m < nmoves && st == OR_OK; ++m) {
+        int j = elec[m];
+        if (j < 0 || j >= n) { st = OR_ERR_ARG; break; }
+        if (method == METHOD_DELAYED && in_queue(&w, j)) st = walker_flush(&w);
+        if (st) break;
+        ratios[m] = walker_propose(&w, j, vrows + (size_t)m * n);
+        if (decisions[m]) st = walker_accept(&w);
+        if (st == OR_OK && flush_after && flush_after[m]) st = walker_flush(&w);
+    }
+    if (st == OR_OK) st = walker_flush(&w);
+    if (st == OR_OK) walker_export(&w, A_out, Ainv_out, logabs, sign);
+    walker_free(&w);
+    return st;
+}
