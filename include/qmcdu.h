@@ -1,0 +1,192 @@
+/*
+ * qmcdu.h -- C ABI of libqmcdu: rank-K delayed Slater-determinant updates for
+ * quantum Monte Carlo on one NVIDIA B300 (sm_103a).
+ *
+ * Method: McDaniel, D'Azevedo, Li, Wong, Kent, "Delayed Slater determinant
+ * update algorithms for high efficiency quantum Monte Carlo".
+ *   - A single-electron move changes one row of the Slater matrix; its
+ *     acceptance probability is the squared determinant ratio, which the
+ *     matrix determinant lemma gives from the explicit inverse (Sec. I, Eq. 1).
+ *   - K = 1 applies every accepted move at once by Sherman-Morrison (Eq. 2).
+ *   - K > 1 delays accepted moves: ratios come from the generalised lemma
+ *     (Eq. 3) through N x k panels and a k x k inverse, and the queued moves
+ *     are applied en bloc by Sherman-Morrison-Woodbury (Eq. 4) when k reaches
+ *     K or the sweep ends (Sec. II). Rejected moves change nothing.
+ *   - The determinant is checked against direct calculation after a sweep
+ *     (Sec. III): qmcdu_recompute.
+ *
+ * Conventions (row form; the paper's matrix transposed, same determinant):
+ *   A       batch x N x N fp64, row-major; row j holds electron j's orbitals.
+ *   A^{-1}  kept in the working precision, COLUMN-major: column j of A^{-1}
+ *           is contiguous (it is the vector the ratio of electron j needs).
+ *   Every call is asynchronous on the handle's stream. A handle is bound to
+ *   one stream and one thread; it is not thread-safe.
+ *   "host or device" pointers: any pointer the CUDA runtime can copy from or
+ *   to with cudaMemcpyDefault (pinned or pageable host memory, device
+ *   memory). "device" pointers: device memory the caller owns, to be read or
+ *   written in stream order.
+ *   Errors found on the device (a singular or non-finite ratio on accept, a
+ *   zero pivot in the recompute, an exceeded spin-wait budget) are latched in a
+ *   device status word and returned by the next synchronising call
+ *   (qmcdu_sync, qmcdu_logdet, qmcdu_get_*); the handle must then be reloaded
+ *   with qmcdu_set_matrix.
+ */
+#ifndef QMCDU_H
+#define QMCDU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmcdu_ctx *qmcdu_t;
+
+/* Working precision of A^{-1}, the panels and the flush. */
+enum {
+    QMCDU_FP64 = 0,        /* everything fp64                                     */
+    QMCDU_FP32 = 1,        /* A^{-1}, panels, flush fp32; k x k inverse, ratios,  */
+                           /* log-det and the recompute fp64                      */
+    QMCDU_FP32_BF16X3 = 2  /* as FP32, flush on tensor cores with split-bf16 x3   */
+};
+
+enum {
+    QMCDU_OK = 0,
+    QMCDU_ERR_ARG = 1,      /* invalid argument; nothing was launched             */
+    QMCDU_ERR_STATE = 2,    /* call out of order (accept without ratio, ...)      */
+    QMCDU_ERR_SINGULAR = 3, /* zero / non-finite ratio accepted, or zero pivot    */
+    QMCDU_ERR_OOM = 4,      /* device allocation failed                           */
+    QMCDU_ERR_CUDA = 5,     /* CUDA runtime error (text in qmcdu_last_error)      */
+    QMCDU_ERR_TIMEOUT = 6   /* a device spin-wait exceeded its budget             */
+};
+
+/* Limits of one handle. */
+#define QMCDU_MAX_N 8192
+#define QMCDU_MAX_K 256
+
+/*
+ * Create a handle for `batch` independent walkers of N electrons with delay K
+ * (K = 1: Sherman-Morrison, Eq. 2; 1 < K <= min(N, QMCDU_MAX_K): delayed,
+ * Eq. 3-4). `stream` is a cudaStream_t (NULL: the legacy default stream).
+ * The library allocates and owns all walker state on the current device:
+ * A, A^{-1}, the N x K panels, the K x K inverse, the recompute workspace.
+ * On success *out receives the handle. Errors: ERR_ARG, ERR_OOM, ERR_CUDA.
+ */
+int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *out);
+
+/* Release the handle and its device memory (synchronises its stream). */
+int qmcdu_destroy(qmcdu_t h);
+
+/*
+ * Load the Slater matrices (host or device, batch x N x N fp64 row-major) and
+ * compute A^{-1} and log|det A| by the fp64 recompute (see qmcdu_recompute).
+ * Clears pending moves and the error latch. ERR_SINGULAR (at the next sync)
+ * if a matrix is singular.
+ */
+int qmcdu_set_matrix(qmcdu_t h, const double *A);
+
+/* Copy the current A (host or device, batch x N x N fp64 row-major). */
+int qmcdu_get_matrix(qmcdu_t h, double *A_out);
+
+/*
+ * Copy the current A^{-1} (host or device, batch x N x N fp64, column-major:
+ * element (i, c) of A^{-1} at [b][c][i]). Pending delayed moves are flushed
+ * first (Eq. 4), so this is the inverse of the current A. Synchronises.
+ */
+int qmcdu_get_inverse(qmcdu_t h, double *Ainv_out);
+
+/*
+ * Determinant ratio of one proposed move per walker (Eq. 1 for k = 0; the
+ * generalised lemma, Eq. 3, through the queued panels otherwise):
+ *   r_b = det(A_b with row elec[b] replaced by v_b) / det(A_b).
+ *   elec       host, [batch] electron indices in [0, N)
+ *   v          device, [batch][N] fp64 proposed rows (read during the call's
+ *              stream order; may be reused afterwards)
+ *   ratio_out  device, [batch] fp64
+ * If a walker's electron is already in its delay queue, that walker's queue is
+ * flushed first (the paper's queue holds distinct moves). Leaves one pending
+ * proposal per walker for qmcdu_accept.
+ */
+int qmcdu_ratio(qmcdu_t h, const int *elec, const double *v, double *ratio_out);
+
+/*
+ * Resolve the pending proposals: mask (host, [batch], 1 = accept, 0 = reject).
+ * Accepted moves are queued (K > 1: panel append and bordered k x k inverse
+ * update; a full queue is flushed at once, Eq. 4) or applied (K = 1, Eq. 2);
+ * A's row and the running log|det A| and sign are updated. Rejected moves
+ * leave the state untouched. ERR_STATE without a pending proposal.
+ */
+int qmcdu_accept(qmcdu_t h, const unsigned char *mask);
+
+/* Apply all queued moves now (Eq. 4). A no-op when the queues are empty. */
+int qmcdu_flush(qmcdu_t h);
+
+/*
+ * Recompute A^{-1} and log|det A| from A in fp64 (Sec. III's direct
+ * calculation): Gauss-Jordan elimination with partial pivoting, whose pivots
+ * are the diagonal of U in P A' = L U. Queued moves are flushed first.
+ * drift_out (host or device, [batch][2] fp64, or NULL): per walker
+ * |log|det|_running - log|det|_recomputed| and
+ * ||A^{-1}_running - A^{-1}_recomputed||_F / ||A^{-1}_recomputed||_F.
+ */
+int qmcdu_recompute(qmcdu_t h, double *drift_out);
+
+/* Running log|det A| (host or device, [batch] fp64) and sign (host or device,
+ * [batch] int, +1/-1). Synchronises. */
+int qmcdu_logdet(qmcdu_t h, double *logabs, int *sign);
+
+/*
+ * One Metropolis sweep per walker, entirely on the device: electrons
+ * j = 0..N-1 in order; proposal v = a_j + sigma * g (a_j the current row j,
+ * g ~ N(0,1)^N); accept iff u < min(1, r^2) (Sec. I); queued moves flushed at
+ * k = K and at the end of the sweep (Sec. II). g and u come from the
+ * Philox4x32-10 counter generator (Salmon et al., SC'11) with key
+ * base_seed + walker and counters (j, sweep_index, 1, block) for g and
+ * (j, sweep_index, 0, 0) for u; g pairs by Box-Muller.
+ *   override      host or device [batch][N] int8 (-1 decide, 0 reject,
+ *                 1 accept), or NULL
+ *   accepted_out  host or device [batch][N] uint8, or NULL
+ *   ratios_out    host or device [batch][N] fp64, or NULL
+ *   near_ties_out host or device [batch] int64 (count of
+ *                 |min(1, r^2) - u| < 1e-10), or NULL
+ * Outputs written to host memory are valid when the call returns; to device
+ * memory, in stream order.
+ */
+int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double sigma,
+                const signed char *override, unsigned char *accepted_out,
+                double *ratios_out, long long *near_ties_out);
+
+/* Wait for the handle's stream and return the latched device status. */
+int qmcdu_sync(qmcdu_t h);
+
+/* Text of the last error on this handle ("" if none). Valid until the next call. */
+const char *qmcdu_last_error(qmcdu_t h);
+
+/*
+ * Philox4x32-10 on the device (Salmon et al., SC'11): out[4 i + w] = word w of
+ * the generator at counter (c0[i], c1[i], c2[i], c3[i]) and key
+ * (seed & 0xffffffff, seed >> 32). All pointers device, n entries per counter
+ * word, 4 n outputs. Runs on `stream` (cudaStream_t, NULL = default).
+ */
+int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *c2,
+                        const unsigned *c3, int n, unsigned long long seed,
+                        unsigned *out, void *stream);
+
+/*
+ * Profiling. While enabled, the library records CUDA events on the handle's
+ * stream around every flush (Eq. 4) and every recompute, and counts its
+ * kernel launches. qmcdu_profile_enable(h, 1) resets the counters; 0 stops.
+ * qmcdu_profile_read synchronises and writes n <= 8 values to out (host):
+ *   [0] kernel launches  [1] flushes   [2] flush time (ms)
+ *   [3] recomputes       [4] recompute time (ms)   [5] stream syncs inside
+ *   sweeps  [6] ratio launches  [7] accept launches
+ */
+int qmcdu_profile_enable(qmcdu_t h, int enable);
+int qmcdu_profile_read(qmcdu_t h, double *out, int n);
+
+/* Library version string. */
+const char *qmcdu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMCDU_H */

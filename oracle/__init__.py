@@ -62,7 +62,7 @@ def _load():
         lib.oracle_inverse.argtypes = [ctypes.c_int, dp, dp]
         lib.oracle_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, dp, dp, dp, i8p, dp, u8p, dp, dp, dp, ip,
-                                      ctypes.POINTER(ctypes.c_longlong)]
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]
         lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                      ip, dp, u8p, u8p, dp, dp, dp, dp, ip]
         for f in (lib.oracle_slogdet, lib.oracle_inverse, lib.oracle_sweeps, lib.oracle_moves):
@@ -106,9 +106,10 @@ def inverse_colmajor(a):
     return np.ascontiguousarray(inverse(a).T)
 
 
-def sweeps(method, A0, G, U, sigma, K=1, override=None):
+def sweeps(method, A0, G, U, sigma, K=1, override=None, max_moves=-1):
     """Metropolis sweeps from A0 with Gaussians G[s, j, :] and uniforms U[s, j].
 
+    max_moves >= 0 stops after that many proposals (a bounded sample).
     Returns dict(ratios, accepted, A, Ainv (column-major layout), logabs, sign,
     near_ties)."""
     A0 = _f64(A0)
@@ -127,7 +128,7 @@ def sweeps(method, A0, G, U, sigma, K=1, override=None):
                                _p(ov, ctypes.c_int8), _p(ratios, ctypes.c_double),
                                _p(acc, ctypes.c_uint8), _p(A, ctypes.c_double),
                                _p(Ainv, ctypes.c_double), ctypes.byref(la), ctypes.byref(sg),
-                               ctypes.byref(nt))
+                               ctypes.byref(nt), int(max_moves))
     if st != OK:
         raise OracleError("oracle_sweeps status %d" % st)
     return dict(ratios=ratios, accepted=acc.astype(bool), A=A, Ainv=Ainv,

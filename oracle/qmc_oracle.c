@@ -377,13 +377,15 @@ static int decide(double r, double u, int override, long long *near_ties)
  * Outputs: ratios, accepted (nsweeps x n), final A rows, final inverse in the
  * column-major layout of A^{-1}, running log|det| and sign, near-tie count.
  * The delayed method flushes when k reaches K and at the end of every sweep.
+ * max_moves >= 0 stops after that many proposals (a bounded sample; the queue
+ * is flushed); -1 runs every sweep in full.
  */
 int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
                   const double *A0, const double *G, const double *U,
                   const signed char *override,
                   double *ratios, unsigned char *accepted,
                   double *A_out, double *Ainv_out, double *logabs, int *sign,
-                  long long *near_ties)
+                  long long *near_ties, long long max_moves)
 {
     if (n < 1 || nsweeps < 0 || (method == METHOD_DELAYED && K < 1)) return OR_ERR_ARG;
     walker w;
@@ -391,8 +393,11 @@ int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
     if (st) return st;
     double *col = malloc(sizeof(double) * n);
     *near_ties = 0;
+    long long done = 0;
     for (int s = 0; s < nsweeps && st == OR_OK; ++s) {
         for (int j = 0; j < n && st == OR_OK; ++j) {
+            if (max_moves >= 0 && done >= max_moves) break;
+            ++done;
             const double *g = G + ((size_t)s * n + j) * n;
             for (int i = 0; i < n; ++i) col[i] = w.M[(size_t)i * n + j] + sigma * g[i];
             double r = walker_propose(&w, j, col);

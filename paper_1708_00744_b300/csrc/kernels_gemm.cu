@@ -1,0 +1,193 @@
+// kernels_gemm.cu -- the rank-k flush of the delayed update (Sec. II, Eq. 4)
+// on SIMT cores, and the tile GEMM it shares with the recompute.
+//
+// Row-convention form of Eq. 4: with P = A^{-1}[:, idx] (N x k), V the queued
+// rows (N x k), Kinv = (V'P)^{-1} and E the selector of idx,
+//   A^{-1} <- A^{-1} - (P Kinv) (V' A^{-1} - E').
+// Three launches per flush, each a batched tile GEMM:
+//   T = V' A^{-1} - E'     (k x N, inner dimension N)
+//   W = P Kinv             (N x k, inner dimension k)
+//   A^{-1} -= W T          (N x N, inner dimension k)
+// 4 N^2 k flops per flush of k moves (the same 4 N^2 per accepted move as
+// Sherman-Morrison, now as matrix-matrix products).
+#include "qmcdu_internal.cuh"
+
+namespace qmcdu {
+
+template <typename TA, typename TB, typename TC>
+struct GemmArgs {
+    const TA *A; long long sAb, sAm, sAl;   // A(m, l) = A[b*sAb + m*sAm + l*sAl]
+    const TB *B; long long sBb, sBl, sBn;   // B(l, n)
+    TC *C; long long sCb, sCm, sCn;         // C(m, n)
+    int M, Nn, Kd;
+    const int *kdyn;    // per-walker k (device) or null
+    int dyn;            // bit 1: M = k_b, bit 2: Kd = k_b
+    int kthresh;        // walkers with k_b < kthresh are skipped (when kdyn)
+    double alpha;
+    int accumulate;     // C = alpha AB + (accumulate ? C : 0)
+    const int *fix_idx; // C(m, n) -= [n == fix_idx[b*fix_stride + m]]
+    int fix_stride;
+};
+
+constexpr int GTHREADS = 256;
+constexpr int GBK = 16;
+
+// C tile BM x BN per CTA, 256 threads in a 16 x 16 grid, each thread
+// (BM/16) x (BN/16) outputs spaced 16 apart. Operand tiles staged in shared
+// memory in the accumulation type; A_L_CONTIG / B_N_CONTIG pick which operand
+// dimension is contiguous so that global loads are coalesced.
+template <typename TA, typename TB, typename TC, typename Acc, int BM, int BN, bool A_L_CONTIG,
+          bool B_N_CONTIG>
+__global__ void __launch_bounds__(GTHREADS) gemm_tile_kernel(GemmArgs<TA, TB, TC> g)
+{
+    constexpr int TM = BM / 16, TN = BN / 16;
+    const int b = blockIdx.z;
+    int M = g.M, Kd = g.Kd;
+    if (g.kdyn) {
+        const int kb = g.kdyn[b];
+        if (kb < g.kthresh || kb <= 0) return;
+        if (g.dyn & 1) M = kb;
+        if (g.dyn & 2) Kd = kb;
+    }
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= M || n0 >= g.Nn) return;
+
+    __shared__ Acc As[GBK][BM + 1];
+    __shared__ Acc Bs[GBK][BN + 1];
+    const TA *Ab = g.A + b * g.sAb;
+    const TB *Bb = g.B + b * g.sBb;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    Acc acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = 0;
+
+    for (int l0 = 0; l0 < Kd; l0 += GBK) {
+#pragma unroll
+        for (int e = tid; e < BM * GBK; e += GTHREADS) {
+            int m, l;
+            if (A_L_CONTIG) { l = e % GBK; m = e / GBK; } else { m = e % BM; l = e / BM; }
+            const int gm = m0 + m, gl = l0 + l;
+            As[l][m] = (gm < M && gl < Kd) ? (Acc)Ab[gm * g.sAm + gl * g.sAl] : (Acc)0;
+        }
+#pragma unroll
+        for (int e = tid; e < BN * GBK; e += GTHREADS) {
+            int nn, l;
+            if (B_N_CONTIG) { nn = e % BN; l = e / BN; } else { l = e % GBK; nn = e / GBK; }
+            const int gn = n0 + nn, gl = l0 + l;
+            Bs[l][nn] = (gn < g.Nn && gl < Kd) ? (Acc)Bb[gl * g.sBl + gn * g.sBn] : (Acc)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < GBK; ++l) {
+            Acc ra[TM], rb[TN];
+#pragma unroll
+            for (int a = 0; a < TM; ++a) ra[a] = As[l][ty + 16 * a];
+#pragma unroll
+            for (int c = 0; c < TN; ++c) rb[c] = Bs[l][tx + 16 * c];
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[a][c] += ra[a] * rb[c];
+        }
+        __syncthreads();
+    }
+
+    TC *Cb = g.C + b * g.sCb;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+        const int gm = m0 + ty + 16 * a;
+        if (gm >= M) continue;
+        const int fix = g.fix_idx ? g.fix_idx[(size_t)b * g.fix_stride + gm] : -1;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int gn = n0 + tx + 16 * c;
+            if (gn >= g.Nn) continue;
+            TC *dst = Cb + gm * g.sCm + gn * g.sCn;
+            Acc v = (Acc)g.alpha * acc[a][c];
+            if (g.accumulate) v += (Acc)*dst;
+            if (gn == fix) v -= (Acc)1;
+            *dst = (TC)v;
+        }
+    }
+}
+
+__global__ void flush_reset_kernel(int batch, int *kcount, int kthresh)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < batch && kcount[b] >= kthresh && kcount[b] > 0) kcount[b] = 0;
+}
+
+template <typename T>
+static cudaError_t launch_flush_t(Ctx &c, int kthresh)
+{
+    const int N = c.N, K = c.K, ld = c.ld;
+    const long long wN = (long long)N * ld, wK = (long long)K * ld;
+    T *Ainv = (T *)c.Ainv;
+    T *Tb = (T *)c.Tbuf;
+    T *Wb = (T *)c.Wbuf;
+    // T = V' A^{-1} - E':  T(m, n) = sum_i V[m][i] A^{-1}[i][n] - [n == idx_m]
+    {
+        GemmArgs<T, T, T> g{};
+        g.A = (const T *)c.V; g.sAb = wK; g.sAm = ld; g.sAl = 1;
+        g.B = Ainv; g.sBb = wN; g.sBl = 1; g.sBn = ld;       // B(l=i, n=c) = Ainv[c*ld + i]
+        g.C = Tb; g.sCb = wK; g.sCm = ld; g.sCn = 1;
+        g.M = K; g.Nn = N; g.Kd = N;
+        g.kdyn = c.kcount; g.dyn = 1; g.kthresh = kthresh;
+        g.alpha = 1.0; g.accumulate = 0;
+        g.fix_idx = c.idx; g.fix_stride = K;
+        dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
+        gemm_tile_kernel<T, T, T, T, 32, 32, true, false><<<grid, GTHREADS, 0, c.stream>>>(g);
+    }
+    // W = P Kinv:  W(m, i) = sum_q Kinv[q][m] P[q][i]   (stored W[m][i])
+    {
+        GemmArgs<double, T, T> g{};
+        g.A = c.Kinv; g.sAb = (long long)K * K; g.sAm = 1; g.sAl = K;
+        g.B = (const T *)c.P; g.sBb = wK; g.sBl = ld; g.sBn = 1;
+        g.C = Wb; g.sCb = wK; g.sCm = ld; g.sCn = 1;
+        g.M = K; g.Nn = N; g.Kd = K;
+        g.kdyn = c.kcount; g.dyn = 3; g.kthresh = kthresh;
+        g.alpha = 1.0; g.accumulate = 0;
+        dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
+        gemm_tile_kernel<double, T, T, T, 32, 32, false, true><<<grid, GTHREADS, 0, c.stream>>>(g);
+    }
+    // A^{-1} -= W T:  stored Ainv[c][i] (column c) -= sum_m T[m][c] W[m][i]
+    {
+        GemmArgs<T, T, T> g{};
+        g.A = Tb; g.sAb = wK; g.sAm = 1; g.sAl = ld;          // A(row=c, l=m) = T[m][c]
+        g.B = Wb; g.sBb = wK; g.sBl = ld; g.sBn = 1;          // B(l=m, n=i) = W[m][i]
+        g.C = Ainv; g.sCb = wN; g.sCm = ld; g.sCn = 1;
+        g.M = N; g.Nn = N; g.Kd = K;
+        g.kdyn = c.kcount; g.dyn = 2; g.kthresh = kthresh;
+        g.alpha = -1.0; g.accumulate = 1;
+        dim3 grid((N + 63) / 64, (N + 63) / 64, c.batch);
+        gemm_tile_kernel<T, T, T, T, 64, 64, false, true><<<grid, GTHREADS, 0, c.stream>>>(g);
+    }
+    flush_reset_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.kcount, kthresh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flush(Ctx &c, int kthresh)
+{
+    if (c.K <= 1) return cudaSuccess;
+    return c.prec == QMCDU_FP64 ? launch_flush_t<double>(c, kthresh) : launch_flush_t<float>(c, kthresh);
+}
+
+// Rank-nb update of the Gauss-Jordan recompute: X += Lt' R (all fp64).
+cudaError_t launch_gj_update(Ctx &c, int nbe)
+{
+    const int N = c.N, ld = c.ld;
+    GemmArgs<double, double, double> g{};
+    g.A = c.Lt; g.sAb = (long long)c.nb * ld; g.sAm = 1; g.sAl = ld;
+    g.B = c.R; g.sBb = (long long)c.nb * ld; g.sBl = ld; g.sBn = 1;
+    g.C = c.work; g.sCb = (long long)N * ld; g.sCm = ld; g.sCn = 1;
+    g.M = N; g.Nn = N; g.Kd = nbe;
+    g.alpha = 1.0; g.accumulate = 1;
+    dim3 grid((N + 63) / 64, (N + 63) / 64, c.batch);
+    gemm_tile_kernel<double, double, double, double, 64, 64, false, true>
+        <<<grid, GTHREADS, 0, c.stream>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace qmcdu

@@ -1,0 +1,286 @@
+// kernels_recompute.cu -- fp64 recompute of A^{-1} and log|det A| from A.
+//
+// The paper checks the running determinants against direct calculation after
+// a sweep (Sec. III). Here the direct calculation is blocked Gauss-Jordan
+// elimination with partial pivoting on X = A' (the transposed copy, so that the
+// result lands in the column-major layout of A^{-1} without a transpose):
+//   * the pivots are the diagonal of U in P X = L U, so
+//     log|det A| = sum log|pivot| and sign = prod sign(pivot) * (-1)^swaps;
+//   * eliminating above and below every pivot leaves (S X)^{-1} = X^{-1} S^{-1}
+//     in place (S the row interchanges), and X^{-1} = (S X)^{-1} S is a column
+//     permutation of it; X^{-1} = A^{-T} stored row-major is A^{-1} stored
+//     column-major.
+// Blocking: for a panel of nb columns, one CTA per walker eliminates the panel
+// (all N rows, panel staged in shared memory), then every other column gets
+// the panel's transformation as one rank-nb update, X += (Mp - E) X_p, with
+// Mp the eliminated panel and X_p the panel's pivot rows. 2 N^3 flops in all.
+#include <math.h>
+
+#include "qmcdu_internal.cuh"
+
+namespace qmcdu {
+
+cudaError_t launch_gj_update(Ctx &c, int nbe);
+
+constexpr int PTHREADS = 1024;
+
+int choose_panel_width(int N)
+{
+    const size_t budget = 192 * 1024;
+    int nb = 16;
+    while (nb > 1 && (size_t)N * nb * sizeof(double) > budget) nb >>= 1;
+    return nb;
+}
+
+// work[b][i][x] = A[b][x][i]  (X = A'); padding stays zero.
+__global__ void transpose_kernel(int N, int ld, const double *A, double *work)
+{
+    __shared__ double tile[32][33];
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const double *Ab = A + (size_t)b * N * ld;
+    double *Wb = work + (size_t)b * N * ld;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int row = i0 + r, col = x0 + threadIdx.x;   // read A[row][col]
+        if (row < N && col < N) tile[r][threadIdx.x] = Ab[(size_t)row * ld + col];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int row = x0 + r, col = i0 + threadIdx.x;   // write work[row][col] = A[col][row]
+        if (row < N && col < N) Wb[(size_t)row * ld + col] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void lu_init_kernel(int batch, double *lu_logabs, int *lu_sign, double *drift)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    lu_logabs[b] = 0.0;
+    lu_sign[b] = 1;
+    drift[4 * b + 0] = drift[4 * b + 1] = drift[4 * b + 2] = drift[4 * b + 3] = 0.0;
+}
+
+// One CTA per walker: Gauss-Jordan on columns [c0, c0 + nbe) of X over all
+// rows, pivot among rows >= c (largest |x|, first index on ties, as LU with
+// partial pivoting), whole-row interchanges applied to X in global memory
+// at once. Outputs: the eliminated panel written back into X, Lt = (Mp - E)'
+// and R = X_p with the panel columns zeroed (the operands of the rank-nb
+// update of all other columns).
+__global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int nb, int c0, int nbe,
+                                                            double *work, int *piv, double *Lt,
+                                                            double *R, double *lu_logabs,
+                                                            int *lu_sign, int *status)
+{
+    extern __shared__ double S[];          // N x nb, row i at S + i*nb
+    __shared__ double wval[32];
+    __shared__ int widx[32];
+    __shared__ double prow[16];
+    __shared__ int pivot_row;
+    __shared__ int singular;
+    const int b = blockIdx.x;
+    double *X = work + (size_t)b * N * ld;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < N * nbe; e += blockDim.x) {
+        const int i = e / nbe, q = e - i * nbe;
+        S[i * nb + q] = X[(size_t)i * ld + c0 + q];
+    }
+    if (tid == 0) singular = 0;
+    __syncthreads();
+    double la = 0.0;
+    int sg = 1;
+    for (int q = 0; q < nbe; ++q) {
+        const int c = c0 + q;
+        // pivot search
+        double best = -1.0;
+        int bi = N;
+        for (int i = c + tid; i < N; i += blockDim.x) {
+            const double v = fabs(S[i * nb + q]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < (blockDim.x >> 5) ? wval[lane] : -1.0;
+            bi = lane < (blockDim.x >> 5) ? widx[lane] : N;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) {
+                pivot_row = bi < N ? bi : c;
+                piv[(size_t)b * N + c] = pivot_row;
+            }
+        }
+        __syncthreads();
+        const int p = pivot_row;
+        if (p != c) {
+            for (int t = tid; t < nbe; t += blockDim.x) {
+                const double s = S[c * nb + t];
+                S[c * nb + t] = S[p * nb + t];
+                S[p * nb + t] = s;
+            }
+            for (int x = tid; x < N; x += blockDim.x) {
+                if (x >= c0 && x < c0 + nbe) continue;
+                const double s = X[(size_t)c * ld + x];
+                X[(size_t)c * ld + x] = X[(size_t)p * ld + x];
+                X[(size_t)p * ld + x] = s;
+            }
+            sg = -sg;
+        }
+        __syncthreads();
+        const double pv = S[c * nb + q];
+        if (pv == 0.0) {
+            if (tid == 0) singular = 1;
+            __syncthreads();
+            continue;
+        }
+        la += log(fabs(pv));
+        if (pv < 0.0) sg = -sg;
+        if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : S[c * nb + tid] / pv;
+        __syncthreads();
+        for (int i = tid; i < N; i += blockDim.x) {
+            double *row = S + i * nb;
+            if (i == c) {
+                for (int t = 0; t < nbe; ++t) row[t] = prow[t];
+            } else {
+                const double f = row[q];
+                row[q] = 0.0;
+                for (int t = 0; t < nbe; ++t) row[t] -= f * prow[t];
+            }
+        }
+        __syncthreads();
+    }
+    // write back the panel, and the rank-nb update operands
+    double *Ltb = Lt + (size_t)b * nb * ld;
+    double *Rb = R + (size_t)b * nb * ld;
+    for (int e = tid; e < N * nbe; e += blockDim.x) {
+        const int i = e / nbe, q = e - i * nbe;
+        const double v = S[i * nb + q];
+        X[(size_t)i * ld + c0 + q] = v;
+        Ltb[(size_t)q * ld + i] = v - (i == c0 + q ? 1.0 : 0.0);
+    }
+    for (int q = 0; q < nbe; ++q)
+        for (int x = tid; x < N; x += blockDim.x)
+            Rb[(size_t)q * ld + x] = (x >= c0 && x < c0 + nbe) ? 0.0 : X[(size_t)(c0 + q) * ld + x];
+    if (tid == 0) {
+        if (singular) {
+            atomicOr(status, ST_SINGULAR);
+            lu_logabs[b] = -INFINITY;
+            lu_sign[b] = 0;
+        } else if (lu_sign[b] != 0) {
+            lu_logabs[b] += la;
+            lu_sign[b] *= sg;
+        }
+    }
+}
+
+// Column permutation of the result: X^{-1} = M S, i.e. column x of X^{-1} is
+// column colperm[x] of M, with the interchanges undone in reverse order.
+__global__ void colperm_kernel(int N, int batch, const int *piv, int *colperm)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    int *cp = colperm + (size_t)b * N;
+    const int *pv = piv + (size_t)b * N;
+    for (int x = 0; x < N; ++x) cp[x] = x;
+    for (int c = N - 1; c >= 0; --c) {
+        const int p = pv[c];
+        const int t = cp[c];
+        cp[c] = cp[p];
+        cp[p] = t;
+    }
+}
+
+// A^{-1} (working precision) from the eliminated matrix, with drift sums.
+template <typename T>
+__global__ void gather_kernel(int N, int ld, const double *work, const int *colperm, T *Ainv,
+                              double *drift, int have_old)
+{
+    const int b = blockIdx.z, r = blockIdx.y;
+    const double *src = work + ((size_t)b * N + r) * ld;
+    const int *cp = colperm + (size_t)b * N;
+    T *dst = Ainv + ((size_t)b * N + r) * ld;
+    double dsq = 0.0, nsq = 0.0;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const double v = src[cp[x]];
+        if (have_old) {
+            const double o = (double)dst[x];
+            dsq += (o - v) * (o - v);
+        }
+        nsq += v * v;
+        dst[x] = (T)v;
+    }
+    if (!have_old) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dsq += __shfl_xor_sync(0xffffffffu, dsq, o);
+        nsq += __shfl_xor_sync(0xffffffffu, nsq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(drift + 4 * b + 0, dsq);
+        atomicAdd(drift + 4 * b + 1, nsq);
+    }
+}
+
+// Replace the running log-det by the recomputed one; keep the drift report.
+__global__ void lu_finish_kernel(int batch, double *logabs, int *sign, const double *lu_logabs,
+                                 const int *lu_sign, double *drift, int have_old)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    drift[4 * b + 2] = have_old ? fabs(logabs[b] - lu_logabs[b]) : 0.0;
+    drift[4 * b + 3] = have_old ? sqrt(drift[4 * b + 0] / fmax(drift[4 * b + 1], 1e-300)) : 0.0;
+    logabs[b] = lu_logabs[b];
+    sign[b] = lu_sign[b];
+}
+
+cudaError_t launch_recompute(Ctx &c, int have_old)
+{
+    const int N = c.N, ld = c.ld;
+    {
+        dim3 grid((N + 31) / 32, (N + 31) / 32, c.batch);
+        transpose_kernel<<<grid, dim3(32, 8), 0, c.stream>>>(N, ld, c.A, c.work);
+    }
+    lu_init_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.lu_logabs, c.lu_sign, c.drift);
+    const size_t smem = (size_t)N * c.nb * sizeof(double);
+    {
+        cudaError_t e = cudaFuncSetAttribute(gj_panel_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    for (int c0 = 0; c0 < N; c0 += c.nb) {
+        const int nbe = N - c0 < c.nb ? N - c0 : c.nb;
+        gj_panel_kernel<<<c.batch, PTHREADS, smem, c.stream>>>(N, ld, c.nb, c0, nbe, c.work, c.piv,
+                                                              c.Lt, c.R, c.lu_logabs, c.lu_sign,
+                                                              c.status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_gj_update(c, nbe);
+        if (e != cudaSuccess) return e;
+    }
+    colperm_kernel<<<(c.batch + 127) / 128, 128, 0, c.stream>>>(N, c.batch, c.piv, c.colperm);
+    {
+        dim3 grid((N + 255) / 256, N, c.batch);
+        if (c.prec == QMCDU_FP64)
+            gather_kernel<double><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm,
+                                                             (double *)c.Ainv, c.drift, have_old);
+        else
+            gather_kernel<float><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm,
+                                                            (float *)c.Ainv, c.drift, have_old);
+    }
+    lu_finish_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.logabs, c.sign,
+                                                                  c.lu_logabs, c.lu_sign, c.drift,
+                                                                  have_old);
+    return cudaGetLastError();
+}
+
+}  // namespace qmcdu

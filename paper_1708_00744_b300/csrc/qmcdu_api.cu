@@ -1,0 +1,530 @@
+// qmcdu_api.cu -- the extern "C" entry points of libqmcdu (declared in
+// include/qmcdu.h): handle life cycle, argument checks, host-side delay-queue
+// bookkeeping, and the order of kernel launches.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "qmcdu_internal.cuh"
+
+using qmcdu::Ctx;
+
+namespace qmcdu {
+
+size_t elem_size(int prec) { return prec == QMCDU_FP64 ? sizeof(double) : sizeof(float); }
+
+static int fail(Ctx *c, int code, const char *fmt, const char *detail = "")
+{
+    if (c) {
+        char buf[512];
+        snprintf(buf, sizeof buf, fmt, detail);
+        c->err = buf;
+    }
+    return code;
+}
+
+static int cuda_fail(Ctx *c, cudaError_t e, const char *where)
+{
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? QMCDU_ERR_OOM : QMCDU_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+template <typename P>
+static cudaError_t dalloc(P **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    return e;
+}
+
+static void release(Ctx *c)
+{
+    void *ptrs[] = {c->A, c->Ainv, c->P, c->V, c->vstash, c->Kinv, c->idx, c->kcount, c->logabs,
+                    c->sign, c->rs, c->partial, c->arrive, c->acc, c->elec_d, c->mask_d,
+                    c->status, c->Tbuf, c->Wbuf, c->work, c->piv, c->colperm, c->Lt, c->R,
+                    c->lu_logabs, c->lu_sign, c->drift, c->sw_acc, c->sw_ratio, c->sw_ties,
+                    c->sw_override};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Read the latched device status (after a stream sync).
+static int read_status(Ctx *c)
+{
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st & ST_TIMEOUT) return fail(c, QMCDU_ERR_TIMEOUT, "device spin-wait budget exceeded%s");
+    if (st & ST_SINGULAR)
+        return fail(c, QMCDU_ERR_SINGULAR, "singular or non-finite ratio / zero pivot%s");
+    if (st & ST_BADARG) return fail(c, QMCDU_ERR_ARG, "electron index out of range on device%s");
+    return QMCDU_OK;
+}
+
+static void clear_queues(Ctx *c)
+{
+    for (int b = 0; b < c->batch; ++b) {
+        c->h_k[b] = 0;
+        std::fill(c->h_inq[b].begin(), c->h_inq[b].end(), 0);
+    }
+}
+
+static cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
+{
+    if (!c->prof) return cudaSuccess;
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) v.emplace_back(a, b);
+    return e;
+}
+
+static cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
+{
+    if (!c->prof || v.empty()) return cudaSuccess;
+    return cudaEventRecord(v.back().second, c->stream);
+}
+
+// Flush every walker with k_b >= kthresh (Eq. 4): four kernel launches.
+static int do_flush(Ctx *c, int kthresh)
+{
+    CK(prof_begin(c, c->ev_flush));
+    CK(launch_flush(*c, kthresh));
+    CK(prof_end(c, c->ev_flush));
+    c->n_launch += 4;
+    c->n_flush += 1;
+    return QMCDU_OK;
+}
+
+static int do_recompute(Ctx *c, int have_old)
+{
+    CK(prof_begin(c, c->ev_recompute));
+    CK(launch_recompute(*c, have_old));
+    CK(prof_end(c, c->ev_recompute));
+    c->n_launch += 5 + 2 * ((c->N + c->nb - 1) / c->nb);
+    c->n_recompute += 1;
+    return QMCDU_OK;
+}
+
+static int do_ratio(Ctx *c, const RatioLaunch &L)
+{
+    CK(launch_ratio(*c, L));
+    c->n_launch += 1;
+    c->n_ratio += 1;
+    return QMCDU_OK;
+}
+
+static int do_accept(Ctx *c, const AcceptLaunch &L)
+{
+    CK(launch_accept(*c, L));
+    c->n_launch += 1;
+    c->n_accept += 1;
+    if (c->K == 1) {
+        CK(launch_sm_update(*c));
+        c->n_launch += 1;
+    }
+    return QMCDU_OK;
+}
+
+static void drop_events(Ctx *c)
+{
+    for (auto *v : {&c->ev_flush, &c->ev_recompute}) {
+        for (auto &p : *v) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+        v->clear();
+    }
+}
+
+static int flush_all(Ctx *c)
+{
+    if (c->K > 1) {
+        bool any = false;
+        for (int b = 0; b < c->batch; ++b) any |= c->h_k[b] > 0;
+        if (any) {
+            int st = do_flush(c, 1);
+            if (st) return st;
+        }
+    }
+    clear_queues(c);
+    return QMCDU_OK;
+}
+
+}  // namespace qmcdu
+
+using namespace qmcdu;
+
+extern "C" {
+
+const char *qmcdu_version(void) { return "qmcdu 0.1 (sm_103a)"; }
+
+const char *qmcdu_last_error(qmcdu_t h) { return h ? reinterpret_cast<Ctx *>(h)->err.c_str() : ""; }
+
+int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *out)
+{
+    if (!out) return QMCDU_ERR_ARG;
+    *out = nullptr;
+    if (N < 1 || N > QMCDU_MAX_N || K < 1 || K > QMCDU_MAX_K || K > N || batch < 1 ||
+        batch > 65535 || precision < QMCDU_FP64 || precision > QMCDU_FP32)
+        return QMCDU_ERR_ARG;
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return QMCDU_ERR_OOM;
+    c->N = N; c->K = K; c->prec = precision; c->batch = batch; c->ld = padded_ld(N);
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->nsplit = (N + 255) / 256;
+    c->nb = choose_panel_width(N);
+    const size_t es = elem_size(precision);
+    const size_t B = batch, ld = c->ld, NN = (size_t)N * ld, KN = (size_t)K * ld;
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, bytes) if (e == cudaSuccess) e = dalloc(&(ptr), (bytes))
+    AL(c->A, B * NN * sizeof(double));
+    AL(c->Ainv, B * NN * es);
+    AL(c->P, B * KN * es);
+    AL(c->V, B * KN * es);
+    AL(c->vstash, B * ld * sizeof(double));
+    AL(c->Kinv, B * K * K * sizeof(double));
+    AL(c->idx, B * K * sizeof(int));
+    AL(c->kcount, B * sizeof(int));
+    AL(c->logabs, B * sizeof(double));
+    AL(c->sign, B * sizeof(int));
+    AL(c->rs, B * rs_stride(K) * sizeof(double));
+    AL(c->partial, B * c->nsplit * (2 * K + 1) * sizeof(double));
+    AL(c->arrive, B * sizeof(unsigned));
+    AL(c->acc, B);
+    AL(c->elec_d, B * sizeof(int));
+    AL(c->mask_d, B);
+    AL(c->status, sizeof(int));
+    if (K > 1) {
+        AL(c->Tbuf, B * KN * es);
+        AL(c->Wbuf, B * KN * es);
+    }
+    AL(c->work, B * NN * sizeof(double));
+    AL(c->piv, B * N * sizeof(int));
+    AL(c->colperm, B * N * sizeof(int));
+    AL(c->Lt, B * c->nb * ld * sizeof(double));
+    AL(c->R, B * c->nb * ld * sizeof(double));
+    AL(c->lu_logabs, B * sizeof(double));
+    AL(c->lu_sign, B * sizeof(int));
+    AL(c->drift, B * 4 * sizeof(double));
+    AL(c->sw_acc, B * N);
+    AL(c->sw_ratio, B * N * sizeof(double));
+    AL(c->sw_ties, B * sizeof(long long));
+    AL(c->sw_override, B * N);
+#undef AL
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? QMCDU_ERR_OOM : QMCDU_ERR_CUDA;
+    }
+    c->h_k.assign(batch, 0);
+    c->h_inq.assign(batch, std::vector<unsigned char>(N, 0));
+    c->h_elec.assign(batch, 0);
+    *out = reinterpret_cast<qmcdu_t>(c);
+    return QMCDU_OK;
+}
+
+int qmcdu_destroy(qmcdu_t h)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    cudaStreamSynchronize(c->stream);
+    drop_events(c);
+    release(c);
+    delete c;
+    return QMCDU_OK;
+}
+
+int qmcdu_set_matrix(qmcdu_t h, const double *A)
+{
+    if (!h || !A) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    const size_t N = c->N;
+    CK(cudaMemcpy2DAsync(c->A, c->ld * sizeof(double), A, N * sizeof(double), N * sizeof(double),
+                         N * c->batch, cudaMemcpyDefault, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->arrive, 0, c->batch * sizeof(unsigned), c->stream));
+    clear_queues(c);
+    c->pending = false;
+    return do_recompute(c, 0);
+}
+
+int qmcdu_get_matrix(qmcdu_t h, double *A_out)
+{
+    if (!h || !A_out) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    const size_t N = c->N;
+    CK(cudaMemcpy2DAsync(A_out, N * sizeof(double), c->A, c->ld * sizeof(double),
+                         N * sizeof(double), N * c->batch, cudaMemcpyDefault, c->stream));
+    return read_status(c);
+}
+
+int qmcdu_get_inverse(qmcdu_t h, double *Ainv_out)
+{
+    if (!h || !Ainv_out) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    int st = flush_all(c);
+    if (st) return st;
+    const size_t N = c->N;
+    if (c->prec == QMCDU_FP64) {
+        CK(cudaMemcpy2DAsync(Ainv_out, N * sizeof(double), c->Ainv, c->ld * sizeof(double),
+                             N * sizeof(double), N * c->batch, cudaMemcpyDefault, c->stream));
+    } else {
+        double *tmp = nullptr;
+        CK(cudaMalloc(&tmp, (size_t)c->batch * N * N * sizeof(double)));
+        cudaError_t e = launch_inverse_export(*c, tmp);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(Ainv_out, tmp, (size_t)c->batch * N * N * sizeof(double),
+                                cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_inverse");
+    }
+    return read_status(c);
+}
+
+int qmcdu_ratio(qmcdu_t h, const int *elec, const double *v, double *ratio_out)
+{
+    if (!h || !elec || !v || !ratio_out) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    bool need_flush = false;
+    for (int b = 0; b < c->batch; ++b) {
+        if (elec[b] < 0 || elec[b] >= c->N)
+            return fail(c, QMCDU_ERR_ARG, "electron index out of range%s");
+        need_flush |= c->h_inq[b][elec[b]] != 0;
+    }
+    if (need_flush) {
+        int st = flush_all(c);
+        if (st) return st;
+    }
+    CK(cudaMemcpyAsync(c->elec_d, elec, c->batch * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    RatioLaunch L{};
+    L.v_in = v;
+    L.elec = c->elec_d;
+    L.ratio_out = ratio_out;
+    int st = do_ratio(c, L);
+    if (st) return st;
+    std::copy(elec, elec + c->batch, c->h_elec.begin());
+    c->pending = true;
+    return QMCDU_OK;
+}
+
+int qmcdu_accept(qmcdu_t h, const unsigned char *mask)
+{
+    if (!h || !mask) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c->pending) return fail(c, QMCDU_ERR_STATE, "accept without a pending ratio%s");
+    CK(cudaMemcpyAsync(c->mask_d, mask, c->batch, cudaMemcpyHostToDevice, c->stream));
+    AcceptLaunch L{};
+    L.mode = 0;
+    L.mask = c->mask_d;
+    int st = do_accept(c, L);
+    if (st) return st;
+    c->pending = false;
+    if (c->K == 1) return QMCDU_OK;
+    bool full = false;
+    for (int b = 0; b < c->batch; ++b) {
+        if (!mask[b]) continue;
+        c->h_k[b] += 1;
+        c->h_inq[b][c->h_elec[b]] = 1;
+        full |= c->h_k[b] == c->K;
+    }
+    if (full) {
+        st = do_flush(c, c->K);
+        if (st) return st;
+        for (int b = 0; b < c->batch; ++b)
+            if (c->h_k[b] == c->K) {
+                c->h_k[b] = 0;
+                std::fill(c->h_inq[b].begin(), c->h_inq[b].end(), 0);
+            }
+    }
+    return QMCDU_OK;
+}
+
+int qmcdu_flush(qmcdu_t h)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    return flush_all(reinterpret_cast<Ctx *>(h));
+}
+
+int qmcdu_recompute(qmcdu_t h, double *drift_out)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    st = do_recompute(c, 1);
+    if (st) return st;
+    if (drift_out) {
+        // drift sums are [b][4]: report entries 2 (log-det) and 3 (inverse)
+        CK(cudaMemcpy2DAsync(drift_out, 2 * sizeof(double), c->drift + 2, 4 * sizeof(double),
+                             2 * sizeof(double), c->batch, cudaMemcpyDefault, c->stream));
+        if (!is_device_ptr(drift_out)) return read_status(c);
+    }
+    return QMCDU_OK;
+}
+
+int qmcdu_logdet(qmcdu_t h, double *logabs, int *sign)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (logabs)
+        CK(cudaMemcpyAsync(logabs, c->logabs, c->batch * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (sign)
+        CK(cudaMemcpyAsync(sign, c->sign, c->batch * sizeof(int), cudaMemcpyDefault, c->stream));
+    return read_status(c);
+}
+
+int qmcdu_sync(qmcdu_t h)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    return read_status(reinterpret_cast<Ctx *>(h));
+}
+
+int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double sigma,
+                const signed char *override, unsigned char *accepted_out, double *ratios_out,
+                long long *near_ties_out)
+{
+    if (!h || sweep_index < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    const int N = c->N, K = c->K;
+    const signed char *ov = nullptr;
+    if (override) {
+        CK(cudaMemcpyAsync(c->sw_override, override, (size_t)c->batch * N, cudaMemcpyDefault,
+                           c->stream));
+        ov = c->sw_override;
+    }
+    CK(cudaMemsetAsync(c->sw_ties, 0, c->batch * sizeof(long long), c->stream));
+    int kub = 0;                      // upper bound on max_b k_b
+    std::vector<int> hk(c->batch);
+    for (int j = 0; j < N; ++j) {
+        RatioLaunch R{};
+        R.uniform_elec = j;
+        R.generate = 1;
+        R.seed = base_seed;
+        R.sweep = sweep_index;
+        R.sigma = sigma;
+        st = do_ratio(c, R);
+        if (st) return st;
+        AcceptLaunch L{};
+        L.mode = 1;
+        L.seed = base_seed;
+        L.sweep = sweep_index;
+        L.override = ov;
+        L.acc_out = c->sw_acc;
+        L.ratio_out = c->sw_ratio;
+        L.ties = c->sw_ties;
+        st = do_accept(c, L);
+        if (st) return st;
+        if (K == 1) continue;
+        if (++kub < K) continue;
+        // Some walker may have reached K: look, and flush every non-empty
+        // queue if one has (a grouped flush keeps all walkers in step).
+        CK(cudaMemcpyAsync(hk.data(), c->kcount, c->batch * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->n_sync += 1;
+        const int kmax = *std::max_element(hk.begin(), hk.end());
+        if (kmax >= K) {
+            st = do_flush(c, 1);
+            if (st) return st;
+            kub = 0;
+        } else {
+            kub = kmax;
+        }
+    }
+    if (K > 1) {
+        st = do_flush(c, 1);
+        if (st) return st;
+    }
+    clear_queues(c);
+    bool host_out = false;
+    if (accepted_out) {
+        CK(cudaMemcpyAsync(accepted_out, c->sw_acc, (size_t)c->batch * N, cudaMemcpyDefault, c->stream));
+        host_out |= !is_device_ptr(accepted_out);
+    }
+    if (ratios_out) {
+        CK(cudaMemcpyAsync(ratios_out, c->sw_ratio, (size_t)c->batch * N * sizeof(double),
+                           cudaMemcpyDefault, c->stream));
+        host_out |= !is_device_ptr(ratios_out);
+    }
+    if (near_ties_out) {
+        CK(cudaMemcpyAsync(near_ties_out, c->sw_ties, c->batch * sizeof(long long), cudaMemcpyDefault,
+                           c->stream));
+        host_out |= !is_device_ptr(near_ties_out);
+    }
+    if (host_out) return read_status(c);
+    return QMCDU_OK;
+}
+
+int qmcdu_profile_enable(qmcdu_t h, int enable)
+{
+    if (!h) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    CK(cudaStreamSynchronize(c->stream));
+    drop_events(c);
+    c->prof = enable != 0;
+    c->n_launch = c->n_flush = c->n_recompute = c->n_sync = c->n_ratio = c->n_accept = 0;
+    return QMCDU_OK;
+}
+
+int qmcdu_profile_read(qmcdu_t h, double *out, int n)
+{
+    if (!h || !out || n < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    CK(cudaStreamSynchronize(c->stream));
+    double ms_flush = 0.0, ms_rec = 0.0;
+    for (auto &p : c->ev_flush) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.first, p.second));
+        ms_flush += ms;
+    }
+    for (auto &p : c->ev_recompute) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.first, p.second));
+        ms_rec += ms;
+    }
+    const double vals[8] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
+                            (double)c->n_recompute, ms_rec, (double)c->n_sync,
+                            (double)c->n_ratio, (double)c->n_accept};
+    for (int i = 0; i < n && i < 8; ++i) out[i] = vals[i];
+    return QMCDU_OK;
+}
+
+int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *c2,
+                        const unsigned *c3, int n, unsigned long long seed, unsigned *out,
+                        void *stream)
+{
+    if (n < 0 || (n > 0 && (!c0 || !c1 || !c2 || !c3 || !out))) return QMCDU_ERR_ARG;
+    cudaError_t e = launch_philox_fill(c0, c1, c2, c3, n, seed, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? QMCDU_OK : QMCDU_ERR_CUDA;
+}
+
+}  // extern "C"

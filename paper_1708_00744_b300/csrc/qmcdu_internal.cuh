@@ -1,0 +1,125 @@
+// qmcdu_internal.cuh -- shared definitions of libqmcdu's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qmcdu.h"
+
+namespace qmcdu {
+
+// Leading dimension of every per-walker N-vector and N x N matrix: rows start
+// on 128-byte boundaries for fp64 (16 elements) so vector loads stay aligned.
+__host__ __device__ static inline int padded_ld(int N) { return (N + 15) / 16 * 16; }
+
+// Device status word bits (latched; cleared by set_matrix).
+enum : int {
+    ST_SINGULAR = 1,   // zero / non-finite ratio accepted, or zero pivot
+    ST_TIMEOUT = 2,    // spin-wait budget exceeded
+    ST_BADARG = 4,     // electron index out of range seen on the device
+};
+
+// Per-proposal scratch record (fp64) for walker b at rs + b * rs_stride:
+//   [0] d = v . A^{-1}[:, j]     [1] r (the ratio)       [2] k at proposal
+//   [3] electron j               [4..4+K) x = Kinv c     [4+K..4+2K) y = Kinv' b
+__host__ __device__ static inline int rs_stride(int K) { return 4 + 2 * K; }
+
+struct Ctx {
+    int N, K, prec, batch, ld;
+    cudaStream_t stream;
+    int device;
+    // walker state
+    double *A = nullptr;        // batch x N x ld, row-major
+    void *Ainv = nullptr;       // batch x N x ld, column-major (working precision)
+    void *P = nullptr;          // batch x K x ld  (P[m] = A^{-1}[:, idx_m])
+    void *V = nullptr;          // batch x K x ld  (V[m] = proposed row of move m)
+    double *vstash = nullptr;   // batch x ld fp64 copy of the pending proposed row
+    double *Kinv = nullptr;     // batch x K x K, row-major
+    int *idx = nullptr;         // batch x K
+    int *kcount = nullptr;      // batch
+    double *logabs = nullptr;   // batch
+    int *sign = nullptr;        // batch
+    double *rs = nullptr;       // batch x rs_stride(K)
+    double *partial = nullptr;  // batch x nsplit x (2K+1)
+    unsigned *arrive = nullptr; // batch
+    unsigned char *acc = nullptr; // batch: decision of the last resolved proposal
+    int *elec_d = nullptr;      // batch
+    unsigned char *mask_d = nullptr; // batch
+    int *status = nullptr;      // 1 int
+    // flush workspace
+    void *Tbuf = nullptr;       // batch x K x ld  (T = V^t A^{-1} - E^t, row m)
+    void *Wbuf = nullptr;       // batch x K x ld  (W = P Kinv, column m)
+    // recompute workspace
+    double *work = nullptr;     // batch x N x ld fp64
+    int *piv = nullptr;         // batch x N
+    int *colperm = nullptr;     // batch x N
+    double *Lt = nullptr;       // batch x nb x ld
+    double *R = nullptr;        // batch x nb x ld
+    double *lu_logabs = nullptr; // batch
+    int *lu_sign = nullptr;     // batch
+    double *drift = nullptr;    // batch x 4 (sums for the drift report)
+    // sweep outputs (device staging)
+    unsigned char *sw_acc = nullptr; // batch x N
+    double *sw_ratio = nullptr;      // batch x N
+    long long *sw_ties = nullptr;    // batch
+    signed char *sw_override = nullptr; // batch x N
+    // host mirror of the delay queues (exact for the per-call API)
+    std::vector<int> h_k;
+    std::vector<std::vector<unsigned char>> h_inq;  // batch x N membership
+    std::vector<int> h_elec;
+    bool pending = false;
+    int nsplit = 1;
+    int nb = 16;
+    std::string err;
+    // profiling (qmcdu_profile_*)
+    bool prof = false;
+    long long n_launch = 0, n_flush = 0, n_recompute = 0, n_sync = 0, n_ratio = 0, n_accept = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_flush, ev_recompute;
+};
+
+size_t elem_size(int prec);
+
+// ---- launchers (kernels_move.cu) ----
+struct RatioLaunch {
+    const double *v_in;         // [batch][N] or null when generating
+    const int *elec;            // device [batch] or null (uniform electron)
+    int uniform_elec;
+    int generate;               // 1: v = a_j + sigma g (Philox)
+    unsigned long long seed;
+    int sweep;
+    double sigma;
+    double *ratio_out;          // device [batch] or null
+};
+cudaError_t launch_ratio(Ctx &c, const RatioLaunch &L);
+
+struct AcceptLaunch {
+    int mode;                   // 0: mask (device), 1: Metropolis with Philox u
+    const unsigned char *mask;  // mode 0
+    unsigned long long seed;    // mode 1
+    int sweep;
+    const signed char *override; // mode 1, [batch][N] or null
+    unsigned char *acc_out;     // [batch][N] or null (mode 1)
+    double *ratio_out;          // [batch][N] or null (mode 1)
+    long long *ties;            // [batch] or null (mode 1)
+};
+cudaError_t launch_accept(Ctx &c, const AcceptLaunch &L);
+cudaError_t launch_sm_update(Ctx &c);
+
+// ---- flush (kernels_gemm.cu) ----
+cudaError_t launch_flush(Ctx &c, int kthresh);
+
+// ---- recompute (kernels_recompute.cu) ----
+cudaError_t launch_recompute(Ctx &c, int have_old_inverse);
+cudaError_t launch_gj_update(Ctx &c, int nbe);
+int choose_panel_width(int N);
+
+// ---- utilities (kernels_move.cu) ----
+cudaError_t launch_philox_fill(const unsigned *c0, const unsigned *c1, const unsigned *c2,
+                               const unsigned *c3, int n, unsigned long long seed,
+                               unsigned *out, cudaStream_t s);
+cudaError_t launch_inverse_export(Ctx &c, double *dst);
+
+}  // namespace qmcdu

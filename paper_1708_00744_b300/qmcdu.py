@@ -1,0 +1,294 @@
+"""Thin ctypes binding of libqmcdu (include/qmcdu.h): same names, argument
+marshalling only. Every step of the delayed update runs in the library's CUDA
+kernels; PyTorch only supplies device memory and streams here.
+
+Array arguments may be torch tensors (CPU or CUDA) or numpy arrays; the C
+functions are told only their addresses. Arrays that the header calls
+"device" must be CUDA tensors; "host or device" arrays may be either.
+Any non-zero status raises QmcduError with the library's error text.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "libqmcdu.so")
+
+QMCDU_FP64, QMCDU_FP32, QMCDU_FP32_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": QMCDU_FP64, "fp32": QMCDU_FP32, "bf16x3": QMCDU_FP32_BF16X3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_SINGULAR", 4: "ERR_OOM",
+          5: "ERR_CUDA", 6: "ERR_TIMEOUT"}
+QMCDU_MAX_N, QMCDU_MAX_K = 8192, 256
+
+# Every function the header declares, with its ctypes signature.
+_VP, _I, _D, _ULL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong
+SIGNATURES = {
+    "qmcdu_create": (_I, [_I, _I, _I, _I, _VP, ctypes.POINTER(_VP)]),
+    "qmcdu_destroy": (_I, [_VP]),
+    "qmcdu_set_matrix": (_I, [_VP, _VP]),
+    "qmcdu_get_matrix": (_I, [_VP, _VP]),
+    "qmcdu_get_inverse": (_I, [_VP, _VP]),
+    "qmcdu_ratio": (_I, [_VP, _VP, _VP, _VP]),
+    "qmcdu_accept": (_I, [_VP, _VP]),
+    "qmcdu_flush": (_I, [_VP]),
+    "qmcdu_recompute": (_I, [_VP, _VP]),
+    "qmcdu_logdet": (_I, [_VP, _VP, _VP]),
+    "qmcdu_sweep": (_I, [_VP, _ULL, _I, _D, _VP, _VP, _VP, _VP]),
+    "qmcdu_sync": (_I, [_VP]),
+    "qmcdu_last_error": (ctypes.c_char_p, [_VP]),
+    "qmcdu_philox4x32_10": (_I, [_VP, _VP, _VP, _VP, _I, _ULL, _VP, _VP]),
+    "qmcdu_profile_enable": (_I, [_VP, _I]),
+    "qmcdu_profile_read": (_I, [_VP, _VP, _I]),
+    "qmcdu_version": (ctypes.c_char_p, []),
+}
+
+
+class QmcduError(RuntimeError):
+    def __init__(self, fn, status, text):
+        super().__init__("%s -> %s (%d): %s" % (fn, STATUS.get(status, "?"), status, text))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libqmcdu.so. Raises if the CUDA library has not been built: there is
+    no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBRARY_PATH):
+            raise RuntimeError("libqmcdu.so is missing at %s; build it with "
+                               "`python -m paper_1708_00744_b300.build`" % LIBRARY_PATH)
+        lib = ctypes.CDLL(LIBRARY_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError("expected a torch tensor, numpy array or address, got %r" % type(x))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(name, status, h=None):
+    if status != 0:
+        text = load().qmcdu_last_error(h).decode() if h else ""
+        raise QmcduError(name, status, text)
+
+
+def _is_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _need(x, n, kind, name, device):
+    if x is None:
+        return
+    size = x.numel() if hasattr(x, "numel") else x.size
+    if size < n:
+        raise ValueError("%s: need %d elements, got %d" % (name, n, size))
+    dt = str(x.dtype).replace("torch.", "")
+    if dt != kind:
+        raise TypeError("%s: dtype %s, expected %s" % (name, dt, kind))
+    if device and not _is_cuda(x):
+        raise ValueError("%s must be a CUDA tensor" % name)
+
+
+# ---------------------------------------------------------------- C functions
+def qmcdu_version():
+    return load().qmcdu_version().decode()
+
+
+def qmcdu_create(N, K, precision, batch, stream=None):
+    h = ctypes.c_void_p()
+    prec = PRECISIONS.get(precision, precision)
+    _check("qmcdu_create", load().qmcdu_create(N, K, prec, batch, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qmcdu_destroy(h):
+    _check("qmcdu_destroy", load().qmcdu_destroy(h))
+
+
+def qmcdu_set_matrix(h, A, N, batch):
+    _need(A, batch * N * N, "float64", "A", False)
+    _check("qmcdu_set_matrix", load().qmcdu_set_matrix(h, _ptr(A)), h)
+
+
+def qmcdu_get_matrix(h, A_out, N, batch):
+    _need(A_out, batch * N * N, "float64", "A_out", False)
+    _check("qmcdu_get_matrix", load().qmcdu_get_matrix(h, _ptr(A_out)), h)
+
+
+def qmcdu_get_inverse(h, Ainv_out, N, batch):
+    _need(Ainv_out, batch * N * N, "float64", "Ainv_out", False)
+    _check("qmcdu_get_inverse", load().qmcdu_get_inverse(h, _ptr(Ainv_out)), h)
+
+
+def qmcdu_ratio(h, elec, v, ratio_out, N, batch):
+    elec = np.ascontiguousarray(elec, dtype=np.int32)
+    if elec.size != batch:
+        raise ValueError("elec: need %d entries" % batch)
+    _need(v, batch * N, "float64", "v", True)
+    _need(ratio_out, batch, "float64", "ratio_out", True)
+    _check("qmcdu_ratio", load().qmcdu_ratio(h, _ptr(elec), _ptr(v), _ptr(ratio_out)), h)
+
+
+def qmcdu_accept(h, mask, batch):
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    if mask.size != batch:
+        raise ValueError("mask: need %d entries" % batch)
+    _check("qmcdu_accept", load().qmcdu_accept(h, _ptr(mask)), h)
+
+
+def qmcdu_flush(h):
+    _check("qmcdu_flush", load().qmcdu_flush(h), h)
+
+
+def qmcdu_recompute(h, drift_out=None, batch=None):
+    if drift_out is not None:
+        _need(drift_out, 2 * batch, "float64", "drift_out", False)
+    _check("qmcdu_recompute", load().qmcdu_recompute(h, _ptr(drift_out)), h)
+
+
+def qmcdu_logdet(h, logabs, sign, batch):
+    _need(logabs, batch, "float64", "logabs", False)
+    _need(sign, batch, "int32", "sign", False)
+    _check("qmcdu_logdet", load().qmcdu_logdet(h, _ptr(logabs), _ptr(sign)), h)
+
+
+def qmcdu_sweep(h, base_seed, sweep_index, sigma, N, batch, override=None, accepted_out=None,
+                ratios_out=None, near_ties_out=None):
+    _need(override, batch * N, "int8", "override", False)
+    _need(accepted_out, batch * N, "uint8", "accepted_out", False)
+    _need(ratios_out, batch * N, "float64", "ratios_out", False)
+    _need(near_ties_out, batch, "int64", "near_ties_out", False)
+    _check("qmcdu_sweep", load().qmcdu_sweep(h, base_seed, sweep_index, sigma, _ptr(override),
+                                             _ptr(accepted_out), _ptr(ratios_out),
+                                             _ptr(near_ties_out)), h)
+
+
+def qmcdu_sync(h):
+    _check("qmcdu_sync", load().qmcdu_sync(h), h)
+
+
+def qmcdu_last_error(h):
+    return load().qmcdu_last_error(h).decode()
+
+
+def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
+    n = c0.numel()
+    for name, x in (("c0", c0), ("c1", c1), ("c2", c2), ("c3", c3)):
+        _need(x, n, "int32", name, True)
+    _need(out, 4 * n, "int32", "out", True)
+    _check("qmcdu_philox4x32_10", load().qmcdu_philox4x32_10(
+        _ptr(c0), _ptr(c1), _ptr(c2), _ptr(c3), n, seed, _ptr(out), _stream_ptr(stream)))
+
+
+PROFILE_FIELDS = ("launches", "flushes", "flush_ms", "recomputes", "recompute_ms", "sweep_syncs",
+                  "ratio_launches", "accept_launches")
+
+
+def qmcdu_profile_enable(h, enable=True):
+    _check("qmcdu_profile_enable", load().qmcdu_profile_enable(h, 1 if enable else 0), h)
+
+
+def qmcdu_profile_read(h):
+    out = np.zeros(len(PROFILE_FIELDS))
+    _check("qmcdu_profile_read", load().qmcdu_profile_read(h, _ptr(out), out.size), h)
+    return dict(zip(PROFILE_FIELDS, out.tolist()))
+
+
+# ---------------------------------------------------------------- handle object
+class Walkers:
+    """A qmcdu handle: `batch` walkers of N electrons with delay K.
+
+    Methods forward to the C functions of the same name (without the prefix).
+    """
+
+    def __init__(self, N, K, precision="fp64", batch=1, stream=None):
+        self.N, self.K, self.batch = int(N), int(K), int(batch)
+        self.precision = precision
+        self.h = qmcdu_create(self.N, self.K, precision, self.batch, stream)
+
+    def close(self):
+        if self.h:
+            qmcdu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_matrix(self, A):
+        qmcdu_set_matrix(self.h, A, self.N, self.batch)
+
+    def get_matrix(self, out):
+        qmcdu_get_matrix(self.h, out, self.N, self.batch)
+        return out
+
+    def get_inverse(self, out):
+        qmcdu_get_inverse(self.h, out, self.N, self.batch)
+        return out
+
+    def ratio(self, elec, v, ratio_out):
+        qmcdu_ratio(self.h, elec, v, ratio_out, self.N, self.batch)
+
+    def accept(self, mask):
+        qmcdu_accept(self.h, mask, self.batch)
+
+    def flush(self):
+        qmcdu_flush(self.h)
+
+    def recompute(self, drift_out=None):
+        qmcdu_recompute(self.h, drift_out, self.batch)
+
+    def logdet(self, logabs, sign):
+        qmcdu_logdet(self.h, logabs, sign, self.batch)
+
+    def sweep(self, base_seed, sweep_index, sigma, override=None, accepted_out=None,
+              ratios_out=None, near_ties_out=None):
+        qmcdu_sweep(self.h, base_seed, sweep_index, sigma, self.N, self.batch, override,
+                    accepted_out, ratios_out, near_ties_out)
+
+    def sync(self):
+        qmcdu_sync(self.h)
+
+    def profile_enable(self, enable=True):
+        qmcdu_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        return qmcdu_profile_read(self.h)

@@ -1,0 +1,50 @@
+"""Shared helpers of the GPU parity tests (CUDA path vs the CPU oracle)."""
+import numpy as np
+import pytest
+
+from paper_1708_00744_b300 import inputs
+
+torch = pytest.importorskip("torch")
+
+# Tolerances for the fp64 path (the spec bar): per-element relative
+# error of ratios, norm-wise relative error of A^{-1}, absolute log|det| error
+# scaled by max(1, |log|det||).
+RTOL_RATIO = 1e-10
+RTOL_INV = 1e-10
+RTOL_LOGDET = 1e-10
+NEAR_TIE = 1e-10
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def walker_inputs(base_seed, batch, N, nsweeps):
+    A = np.stack([inputs.initial_matrix(inputs.walker_seed(base_seed, b), N) for b in range(batch)])
+    G = [np.stack([inputs.proposal_gaussians(inputs.walker_seed(base_seed, b), s, N)
+                   for s in range(nsweeps)]) for b in range(batch)]
+    U = [np.stack([inputs.metropolis_uniforms(inputs.walker_seed(base_seed, b), s, N)
+                   for s in range(nsweeps)]) for b in range(batch)]
+    return A, G, U
+
+
+def tie_override(ref_ratios, U):
+    """Replay the oracle's decision only where it was a near tie."""
+    p = np.minimum(1.0, ref_ratios ** 2)
+    ties = np.abs(p - U) < NEAR_TIE
+    ov = np.full(U.shape, -1, dtype=np.int8)
+    ov[ties] = (U[ties] < p[ties]).astype(np.int8)
+    return ov, int(ties.sum())
+
+
+def rel_ratio_err(x, ref):
+    return float(np.max(np.abs(x - ref) / np.maximum(np.abs(ref), 1e-300))) if x.size else 0.0
+
+
+def rel_norm_err(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def logdet_err(x, ref):
+    return abs(x - ref) / max(1.0, abs(ref))

@@ -1,0 +1,236 @@
+"""Parity of the CUDA path with the CPU oracle (fp64), through the C ABI.
+
+Every case runs the same seeded inputs through libqmcdu and through the oracle
+and compares element by element: accept decisions exactly (near ties, where
+|min(1, r^2) - u| < 1e-10, replay the oracle's decision and are counted),
+ratios, A^{-1} and log|det A| within the fp64 tolerances of tests/gpu_common.py.
+Sizes span one and several 256-element chunks with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_00744_b300 import inputs
+from paper_1708_00744_b300.qmcdu import QmcduError, Walkers
+
+from gpu_common import (RTOL_INV, RTOL_LOGDET, RTOL_RATIO, logdet_err, need_gpu, rel_norm_err,
+                        rel_ratio_err, tie_override, torch, walker_inputs)
+
+pytestmark = pytest.mark.gpu
+
+
+def run_sweeps(N, K, sigma, batch, nsweeps, base_seed, precision="fp64", override=None):
+    W = Walkers(N, K, precision, batch)
+    A, G, U = walker_inputs(base_seed, batch, N, nsweeps)
+    W.set_matrix(A)
+    acc = np.zeros((nsweeps, batch, N), dtype=np.uint8)
+    rat = np.zeros((nsweeps, batch, N))
+    ties = np.zeros((nsweeps, batch), dtype=np.int64)
+    for s in range(nsweeps):
+        ov = None if override is None else np.ascontiguousarray(override[s])
+        W.sweep(base_seed, s, sigma, override=ov, accepted_out=acc[s], ratios_out=rat[s],
+                near_ties_out=ties[s])
+    Af = np.zeros((batch, N, N))
+    Ai = np.zeros((batch, N, N))
+    la = np.zeros(batch)
+    sg = np.zeros(batch, dtype=np.int32)
+    W.get_matrix(Af)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.close()
+    return dict(A0=A, G=G, U=U, acc=acc, rat=rat, ties=ties, A=Af, Ainv=Ai, logabs=la, sign=sg)
+
+
+def oracle_reference(A0, G, U, sigma):
+    return oracle.sweeps(oracle.SM, A0, G, U, sigma)
+
+
+@pytest.mark.parametrize("N,K,sigma", [(1, 1, 0.5), (2, 2, 1.0), (3, 2, 0.1), (7, 3, 1.0),
+                                       (64, 1, 0.1), (64, 8, 0.1), (65, 16, 1.0), (200, 1, 1.0),
+                                       (257, 32, 0.1), (511, 64, 1.0), (300, 300, 0.1)])
+def test_sweeps_match_oracle(N, K, sigma):
+    need_gpu()
+    batch, nsweeps, base = 2, 2, 100 + N
+    A, G, U = walker_inputs(base, batch, N, nsweeps)
+    refs = [oracle_reference(A[b], G[b], U[b], sigma) for b in range(batch)]
+    override = np.full((nsweeps, batch, N), -1, dtype=np.int8)
+    nties = 0
+    for b in range(batch):
+        ov, t = tie_override(refs[b]["ratios"], U[b])
+        override[:, b, :] = ov
+        nties += t
+    out = run_sweeps(N, K, sigma, batch, nsweeps, base, override=override if nties else None)
+    for b, ref in enumerate(refs):
+        assert np.array_equal(out["acc"][:, b, :].astype(bool), ref["accepted"]), (b, nties)
+        assert rel_ratio_err(out["rat"][:, b, :], ref["ratios"]) < RTOL_RATIO
+        assert np.array_equal(out["A"][b], ref["A"])
+        assert rel_norm_err(out["Ainv"][b], ref["Ainv"]) < RTOL_INV
+        assert logdet_err(out["logabs"][b], ref["logabs"]) < RTOL_LOGDET
+        assert out["sign"][b] == ref["sign"]
+    assert out["ties"].sum() == nties
+
+
+def test_sweep_n64_matches_golden_fixture():
+    """One sweep of the 64-electron walker from seed 0 (tests/golden)."""
+    import json
+    import os
+    need_gpu()
+    doc = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sweep_n64_seed0.json")))
+    for case in doc["cases"]:
+        out = run_sweeps(case["n"], case["K"], case["sigma"], 1, case["nsweeps"], case["seed"])
+        got = "".join("1" if x else "0" for x in out["acc"][0, 0])
+        assert got == case["accepted"][0]
+        assert rel_ratio_err(out["rat"][0, 0], np.array(case["ratios"][0])) < RTOL_RATIO
+        assert logdet_err(out["logabs"][0], case["final_logabs"]) < RTOL_LOGDET
+
+
+@pytest.mark.parametrize("N,K", [(5, 1), (5, 3), (64, 8), (130, 1), (130, 7), (300, 32)])
+def test_per_call_moves_match_oracle(N, K):
+    """qmcdu_ratio / qmcdu_accept with caller-made rows, repeated electrons
+    (which force a flush) and explicit flushes."""
+    need_gpu()
+    rng = np.random.default_rng(N * 10 + K)
+    batch, nmoves = 3, 3 * N // 2 + 5
+    A0 = np.stack([inputs.initial_matrix(7 + b, N) for b in range(batch)])
+    cur = A0.copy()
+    W = Walkers(N, K, "fp64", batch)
+    W.set_matrix(A0)
+    elec = rng.integers(0, N, size=(nmoves, batch))
+    vrows = np.zeros((nmoves, batch, N))
+    masks = (rng.random((nmoves, batch)) < 0.75).astype(np.uint8)
+    flush_after = rng.random(nmoves) < 0.05
+    ratios = np.zeros((nmoves, batch))
+    v_dev = torch.zeros(batch, N, dtype=torch.float64, device="cuda")
+    r_dev = torch.zeros(batch, dtype=torch.float64, device="cuda")
+    for m in range(nmoves):
+        for b in range(batch):
+            vrows[m, b] = cur[b, elec[m, b]] + 0.3 * rng.standard_normal(N)
+        v_dev.copy_(torch.from_numpy(vrows[m]))
+        W.ratio(elec[m], v_dev, r_dev)
+        ratios[m] = r_dev.cpu().numpy()
+        W.accept(masks[m])
+        for b in range(batch):
+            if masks[m, b]:
+                cur[b, elec[m, b]] = vrows[m, b]
+        if flush_after[m]:
+            W.flush()
+    Af = np.zeros((batch, N, N))
+    Ai = np.zeros((batch, N, N))
+    la = np.zeros(batch)
+    sg = np.zeros(batch, dtype=np.int32)
+    W.get_matrix(Af)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.close()
+    for b in range(batch):
+        ref = oracle.moves(oracle.DELAYED if K > 1 else oracle.SM, A0[b], elec[:, b], vrows[:, b],
+                           masks[:, b], K=K, flush_after=flush_after.astype(np.uint8))
+        assert rel_ratio_err(ratios[:, b], ref["ratios"]) < RTOL_RATIO
+        assert np.array_equal(Af[b], ref["A"])
+        assert rel_norm_err(Ai[b], ref["Ainv"]) < RTOL_INV
+        assert logdet_err(la[b], ref["logabs"]) < RTOL_LOGDET and sg[b] == ref["sign"]
+
+
+@pytest.mark.parametrize("N,batch", [(1, 3), (7, 2), (64, 4), (100, 1), (513, 2)])
+def test_recompute_matches_oracle_lu(N, batch):
+    """Sec. III's direct calculation: A^{-1} and log|det A| from A alone."""
+    need_gpu()
+    A = np.stack([inputs.initial_matrix(50 + b, N) for b in range(batch)])
+    W = Walkers(N, 4 if N >= 4 else 1, "fp64", batch)
+    W.set_matrix(A)
+    Ai = np.zeros((batch, N, N))
+    la = np.zeros(batch)
+    sg = np.zeros(batch, dtype=np.int32)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.sweep(50, 0, 0.1)
+    drift = np.zeros((batch, 2))
+    W.recompute(drift)
+    W.close()
+    for b in range(batch):
+        s, l = oracle.slogdet(A[b])
+        assert sg[b] == s and logdet_err(la[b], l) < RTOL_LOGDET
+        assert rel_norm_err(Ai[b], oracle.inverse_colmajor(A[b])) < RTOL_INV
+    assert np.all(drift[:, 0] < 1e-10) and np.all(drift[:, 1] < 1e-10)
+
+
+def test_recompute_special_matrices():
+    """Closed forms: permutation (sign = parity, log|det| = 0), diagonal."""
+    need_gpu()
+    N = 37
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(N)
+    Pm = np.zeros((N, N))
+    Pm[np.arange(N), perm] = 1.0
+    inv_count = sum(1 for i in range(N) for j in range(i + 1, N) if perm[i] > perm[j])
+    d = rng.uniform(0.5, 2.0, N) * rng.choice([-1.0, 1.0], N)
+    A = np.stack([Pm, np.diag(d)])
+    W = Walkers(N, 1, "fp64", 2)
+    W.set_matrix(A)
+    Ai = np.zeros((2, N, N))
+    la = np.zeros(2)
+    sg = np.zeros(2, dtype=np.int32)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.close()
+    assert sg[0] == (-1 if inv_count % 2 else 1) and la[0] == 0.0
+    assert np.array_equal(Ai[0], Pm)                 # colmajor(P^{-1}) = (P^T)^T = P
+    assert sg[1] == int(np.prod(np.sign(d))) and abs(la[1] - np.sum(np.log(np.abs(d)))) < 1e-13
+    assert np.allclose(np.diag(Ai[1]), 1.0 / d, rtol=1e-15, atol=0)
+
+
+def test_forced_accept_matches_oracle_forced_mode():
+    """100% acceptance, the paper's test condition (Sec. III)."""
+    need_gpu()
+    N, K, batch = 96, 16, 1
+    A, G, U = walker_inputs(9, batch, N, 1)
+    ov = np.ones((1, batch, N), dtype=np.int8)
+    ref = oracle.sweeps(oracle.SM, A[0], G[0], U[0], 0.1, override=ov[:, 0])
+    out = run_sweeps(N, K, 0.1, batch, 1, 9, override=ov)
+    assert out["acc"].all()
+    assert rel_ratio_err(out["rat"][:, 0], ref["ratios"]) < RTOL_RATIO
+    assert rel_norm_err(out["Ainv"][0], ref["Ainv"]) < RTOL_INV
+
+
+def test_error_paths():
+    need_gpu()
+    N = 8
+    W = Walkers(N, 4, "fp64", 1)
+    W.set_matrix(np.eye(N)[None])
+    with pytest.raises(QmcduError) as e:
+        W.accept(np.ones(1, dtype=np.uint8))         # no pending ratio
+    assert e.value.status == 2
+    v = torch.zeros(1, N, dtype=torch.float64, device="cuda")
+    r = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(QmcduError) as e:
+        W.ratio(np.array([N]), v, r)                  # electron out of range
+    assert e.value.status == 1
+    W.ratio(np.array([3]), v, r)                      # v = 0: r = 0
+    assert r.item() == 0.0
+    W.accept(np.ones(1, dtype=np.uint8))              # accepting r = 0 is singular
+    with pytest.raises(QmcduError) as e:
+        W.sync()
+    assert e.value.status == 3
+    W.set_matrix(np.eye(N)[None])                     # reload clears the latch
+    W.sync()
+    with pytest.raises(QmcduError) as e:
+        W.set_matrix(np.zeros((1, N, N)))             # singular matrix
+        W.sync()
+    assert e.value.status == 3
+    W.close()
+
+
+@pytest.mark.parametrize("K", [1, 64])
+def test_full_size_sweep_n2048(K):
+    """The benchmark's walker (N = 2048, sigma = 0.1, fp64): one full sweep
+    compared with the oracle's Sherman-Morrison trajectory."""
+    need_gpu()
+    N, sigma, base = 2048, 0.1, 0
+    A, G, U = walker_inputs(base, 1, N, 1)
+    ref = oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma)
+    ov, nties = tie_override(ref["ratios"], U[0])
+    out = run_sweeps(N, K, sigma, 1, 1, base, override=ov[:, None, :] if nties else None)
+    assert np.array_equal(out["acc"][:, 0].astype(bool), ref["accepted"])
+    assert rel_ratio_err(out["rat"][:, 0], ref["ratios"]) < RTOL_RATIO
+    assert rel_norm_err(out["Ainv"][0], ref["Ainv"]) < RTOL_INV
+    assert logdet_err(out["logabs"][0], ref["logabs"]) < RTOL_LOGDET

@@ -1,0 +1,53 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every symbol include/qmcdu.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1708_00744_b300 import build as qbuild
+from paper_1708_00744_b300 import qmcdu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qmcdu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qmcdu_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    qbuild.build()
+    return ctypes.CDLL(qbuild.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    assert set(declared_functions()) == set(qmcdu.SIGNATURES)
+
+
+def test_version_and_argument_errors_without_gpu(lib):
+    lib.qmcdu_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.qmcdu_version()
+    h = ctypes.c_void_p()
+    # invalid arguments are rejected before any CUDA call
+    assert lib.qmcdu_create(0, 1, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.qmcdu_create(64, 65, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.qmcdu_create(64, 8, 7, 1, None, ctypes.byref(h)) == 1
+    assert lib.qmcdu_create(64, 300, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.qmcdu_create(9000, 8, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.qmcdu_destroy(None) == 1
+    assert lib.qmcdu_flush(None) == 1
+
+
+def test_library_is_built_for_sm_103a():
+    assert "arch=compute_103a,code=sm_103a" in qbuild.ARCH
