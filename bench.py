@@ -374,6 +374,11 @@ def main():
                    "d2h_bytes_per_step": a.sweeps_per_step * a.batch * a.N + a.batch * 12}
     prof = res["prof"] or {}
     line["gpu_launches"] = int(prof.get("launches", 0))
+    line["breakdown_ms_per_step"] = {
+        "flush": prof.get("flush_ms", 0.0) / a.steps,
+        "recompute": prof.get("recompute_ms", 0.0) / a.steps,
+        "moves (ratio + accept + sync)": (res["total_ms"] - prof.get("flush_ms", 0.0)
+                                          - prof.get("recompute_ms", 0.0)) / a.steps}
     line["clocks"] = res["clocks"]
     if a.gpus == 1:
         nm = cpu_sample_size(a)

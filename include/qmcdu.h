@@ -182,6 +182,35 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
 int qmcdu_profile_enable(qmcdu_t h, int enable);
 int qmcdu_profile_read(qmcdu_t h, double *out, int n);
 
+/*
+ * Options of a handle (value semantics in brackets; 0 restores the default):
+ *   QMCDU_OPT_SWEEP_PERSISTENT  [1] qmcdu_sweep runs as one persistent
+ *       cooperative kernel per sweep; 0 drives the per-proposal kernels from
+ *       the host (same results, for comparison and debugging)
+ *   QMCDU_OPT_RATIO_CTAS   [auto] CTAs per walker that compute the ratios
+ *   QMCDU_OPT_FLUSH_CTAS   [auto] CTAs per walker that apply the flush
+ *   QMCDU_OPT_WAIT_BUDGET_NS [2e9] time budget of every device spin-wait;
+ *       on expiry the call fails with ERR_TIMEOUT at the next sync
+ *   QMCDU_OPT_TEST_STALL   [0] test hook: the next persistent sweep waits for
+ *       one arrival that never comes, so that its wait runs out of budget
+ * Returns ERR_ARG for an unknown option or a negative value.
+ */
+enum {
+    QMCDU_OPT_SWEEP_PERSISTENT = 1,
+    QMCDU_OPT_RATIO_CTAS = 2,
+    QMCDU_OPT_FLUSH_CTAS = 3,
+    QMCDU_OPT_WAIT_BUDGET_NS = 4,
+    QMCDU_OPT_TEST_STALL = 5
+};
+int qmcdu_set_option(qmcdu_t h, int option, long long value);
+
+/*
+ * Shape of the last persistent sweep launch (host, 5 ints): CTAs per walker
+ * group (flush), ratio CTAs per group, walker groups, rows per ratio CTA,
+ * flush column tile.
+ */
+int qmcdu_sweep_shape(qmcdu_t h, int *shape5);
+
 /* Library version string. */
 const char *qmcdu_version(void);
 

@@ -52,7 +52,7 @@ static void release(Ctx *c)
                     c->sign, c->rs, c->partial, c->arrive, c->acc, c->elec_d, c->mask_d,
                     c->status, c->Tbuf, c->Wbuf, c->work, c->piv, c->colperm, c->Lt, c->R,
                     c->lu_logabs, c->lu_sign, c->drift, c->sw_acc, c->sw_ratio, c->sw_ties,
-                    c->sw_override};
+                    c->sw_override, c->sw_partial, c->sw_sync};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -157,6 +157,9 @@ static void drop_events(Ctx *c)
     }
 }
 
+int copy_sweep_outputs(Ctx *c, unsigned char *accepted_out, double *ratios_out,
+                       long long *near_ties_out);
+
 static int flush_all(Ctx *c)
 {
     if (c->K > 1) {
@@ -193,6 +196,8 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
     c->N = N; c->K = K; c->prec = precision; c->batch = batch; c->ld = padded_ld(N);
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->num_sms = 148;
     c->nsplit = (N + 255) / 256;
     c->nb = choose_panel_width(N);
     const size_t es = elem_size(precision);
@@ -232,6 +237,13 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
     AL(c->sw_ratio, B * N * sizeof(double));
     AL(c->sw_ties, B * sizeof(long long));
     AL(c->sw_override, B * N);
+    {
+        const size_t cap = (size_t)c->num_sms * 8;   // 256-thread CTAs resident per GPU, at most
+        c->sw_partial_len = cap * 2 * (2 * K + 1);
+        c->sync_words = (int)(cap * 4);
+        AL(c->sw_partial, c->sw_partial_len * sizeof(double));
+        AL(c->sw_sync, cap * 4 * sizeof(unsigned));
+    }
 #undef AL
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -422,6 +434,21 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         ov = c->sw_override;
     }
     CK(cudaMemsetAsync(c->sw_ties, 0, c->batch * sizeof(long long), c->stream));
+    if (c->opt_persistent) {
+        SweepLaunch S{};
+        S.seed = base_seed;
+        S.sweep = sweep_index;
+        S.sigma = sigma;
+        S.override = ov;
+        S.acc_out = c->sw_acc;
+        S.ratio_out = c->sw_ratio;
+        S.ties = c->sw_ties;
+        CK(launch_sweep(*c, S));
+        c->n_launch += 1;
+        c->opt_stall = 0;
+        CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
+        return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out);
+    }
     int kub = 0;                      // upper bound on max_b k_b
     std::vector<int> hk(c->batch);
     for (int j = 0; j < N; ++j) {
@@ -465,6 +492,39 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         if (st) return st;
     }
     clear_queues(c);
+    return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out);
+}
+
+int qmcdu_set_option(qmcdu_t h, int option, long long value)
+{
+    if (!h || value < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    switch (option) {
+    case QMCDU_OPT_SWEEP_PERSISTENT: c->opt_persistent = value ? 1 : 0; break;
+    case QMCDU_OPT_RATIO_CTAS: c->opt_ratio_ctas = (int)std::min(value, 1LL << 20); break;
+    case QMCDU_OPT_FLUSH_CTAS: c->opt_flush_ctas = (int)std::min(value, 1LL << 20); break;
+    case QMCDU_OPT_WAIT_BUDGET_NS: c->opt_budget_ns = value ? value : 2000000000LL; break;
+    case QMCDU_OPT_TEST_STALL: c->opt_stall = value ? 1 : 0; break;
+    default: return fail(c, QMCDU_ERR_ARG, "unknown option%s");
+    }
+    return QMCDU_OK;
+}
+
+int qmcdu_sweep_shape(qmcdu_t h, int *shape5)
+{
+    if (!h || !shape5) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    for (int i = 0; i < 5; ++i) shape5[i] = c->last_sweep_shape[i];
+    return QMCDU_OK;
+}
+
+}  // extern "C"
+
+namespace qmcdu {
+int copy_sweep_outputs(Ctx *c, unsigned char *accepted_out, double *ratios_out,
+                       long long *near_ties_out)
+{
+    const int N = c->N;
     bool host_out = false;
     if (accepted_out) {
         CK(cudaMemcpyAsync(accepted_out, c->sw_acc, (size_t)c->batch * N, cudaMemcpyDefault, c->stream));
@@ -483,6 +543,9 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
     if (host_out) return read_status(c);
     return QMCDU_OK;
 }
+}  // namespace qmcdu
+
+extern "C" {
 
 int qmcdu_profile_enable(qmcdu_t h, int enable)
 {

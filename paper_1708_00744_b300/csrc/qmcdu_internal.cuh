@@ -78,7 +78,31 @@ struct Ctx {
     bool prof = false;
     long long n_launch = 0, n_flush = 0, n_recompute = 0, n_sync = 0, n_ratio = 0, n_accept = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_flush, ev_recompute;
+    // persistent sweep (kernels_sweep.cu)
+    int num_sms = 148;
+    double *sw_partial = nullptr;   // capacity x 2 x (2K+1)
+    size_t sw_partial_len = 0;
+    unsigned *sw_sync = nullptr;    // capacity x 4
+    int sync_words = 0;
+    int last_sweep_shape[5] = {0, 0, 0, 0, 0};   // Gf, Gr, groups, chunk, cb
+    // options (qmcdu_set_option)
+    int opt_persistent = 1;
+    int opt_ratio_ctas = 0;
+    int opt_flush_ctas = 0;
+    long long opt_budget_ns = 2000000000LL;
+    int opt_stall = 0;
 };
+
+struct SweepLaunch {
+    unsigned long long seed;
+    int sweep;
+    double sigma;
+    const signed char *override;
+    unsigned char *acc_out;
+    double *ratio_out;
+    long long *ties;
+};
+cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L);
 
 size_t elem_size(int prec);
 

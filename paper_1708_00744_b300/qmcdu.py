@@ -40,6 +40,8 @@ SIGNATURES = {
     "qmcdu_sync": (_I, [_VP]),
     "qmcdu_last_error": (ctypes.c_char_p, [_VP]),
     "qmcdu_philox4x32_10": (_I, [_VP, _VP, _VP, _VP, _I, _ULL, _VP, _VP]),
+    "qmcdu_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
+    "qmcdu_sweep_shape": (_I, [_VP, _VP]),
     "qmcdu_profile_enable": (_I, [_VP, _I]),
     "qmcdu_profile_read": (_I, [_VP, _VP, _I]),
     "qmcdu_version": (ctypes.c_char_p, []),
@@ -210,6 +212,20 @@ def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
         _ptr(c0), _ptr(c1), _ptr(c2), _ptr(c3), n, seed, _ptr(out), _stream_ptr(stream)))
 
 
+OPTIONS = {"sweep_persistent": 1, "ratio_ctas": 2, "flush_ctas": 3, "wait_budget_ns": 4,
+           "test_stall": 5}
+
+
+def qmcdu_set_option(h, option, value):
+    _check("qmcdu_set_option", load().qmcdu_set_option(h, OPTIONS.get(option, option), int(value)), h)
+
+
+def qmcdu_sweep_shape(h):
+    out = np.zeros(5, dtype=np.int32)
+    _check("qmcdu_sweep_shape", load().qmcdu_sweep_shape(h, _ptr(out)), h)
+    return dict(zip(("flush_ctas", "ratio_ctas", "groups", "chunk", "col_tile"), out.tolist()))
+
+
 PROFILE_FIELDS = ("launches", "flushes", "flush_ms", "recomputes", "recompute_ms", "sweep_syncs",
                   "ratio_launches", "accept_launches")
 
@@ -286,6 +302,12 @@ class Walkers:
 
     def sync(self):
         qmcdu_sync(self.h)
+
+    def set_option(self, option, value):
+        qmcdu_set_option(self.h, option, value)
+
+    def sweep_shape(self):
+        return qmcdu_sweep_shape(self.h)
 
     def profile_enable(self, enable=True):
         qmcdu_profile_enable(self.h, enable)
