@@ -30,9 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP64 peak (B300): the nominal 1.25 TFLOP/s of the dense FP64 rate; see the
-# roofline notes of the design document for the unit-count derivation.
-FP64_PEAK_TFLOPS = 1.25
+# ALU peaks of one B300 (148 SMs at the 2032 MHz maximum SM clock): 2 FP64 FMA
+# per SM per clock (a DFMA loop measures 1.127 TFLOP/s at the clock it ran at),
+# 128 FP32 FMA per SM per clock.
+SMS, SM_MHZ = 148, 2032.0
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.203
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 77.0
 HBM_PEAK_FALLBACK_GBS = 6400.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the flush kernels,
@@ -73,21 +76,26 @@ def config(a, world):
 
 # ------------------------------------------------------------------ CPU oracle
 def cpu_oracle_sample(a, max_moves):
-    """The fp64 CPU oracle (delayed look-ahead + Woodbury, same K) on the first
-    `max_moves` proposals of sweep 0 of one walker. Returns (accepted, seconds)."""
+    """The fp64 CPU oracle (delayed look-ahead + Woodbury with the same K; K = 1:
+    Sherman-Morrison) on the first `max_moves` proposals of sweep 0 of one
+    walker. The oracle's setup (an O(N^3) LU inverse of the starting matrix) is
+    timed by a zero-proposal run and subtracted, so that the figure is the update
+    throughput. Returns (accepted, seconds of update work, seconds of setup)."""
     import oracle
     from paper_1708_00744_b300 import inputs
     A = inputs.initial_matrix(a.seed, a.N)
-    nsw = 1
     G = inputs.proposal_gaussians(a.seed, 0, a.N)[None]
     U = inputs.metropolis_uniforms(a.seed, 0, a.N)[None]
     method = oracle.SM if a.K == 1 else oracle.DELAYED
     oracle.build()
     t0 = time.perf_counter()
+    oracle.sweeps(method, A, G, U, a.sigma, K=a.K, max_moves=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
     out = oracle.sweeps(method, A, G, U, a.sigma, K=a.K, max_moves=max_moves)
-    dt = time.perf_counter() - t0
-    acc = int(out["accepted"][:nsw].sum())
-    return acc, dt
+    dt = time.perf_counter() - t0 - t_setup
+    acc = int(out["accepted"][0, :max_moves].sum())
+    return acc, max(dt, 1e-9), t_setup
 
 
 def cpu_sample_size(a, seconds=15.0):
@@ -284,34 +292,32 @@ def run_ours(a, rank, world, local_rank):
 
 
 def roofline_for(a, res):
-    prof = res["prof"]
+    """Dominant kernel: the persistent sweep kernel (one launch per sweep). Its
+    algorithmic work is the Eq. 4 flush, 4 N^2 flops per accepted move, plus
+    the ratio dot products, 2 (2k + 2) N flops per proposal with k the mean
+    queue length (about K/2 at high acceptance), and the W-panel append,
+    4 k N flops per accepted move."""
+    prof = res["prof"] or {}
     N, K = a.N, a.K
-    peaks = measured_peaks()
     acc_per_gpu = res["accepted"] / max(1, a.gpus)
-    if K > 1 and prof and prof["flushes"] > 0:
-        # Eq. 4 flush: 4 N^2 flops per queued accepted move (T = V'A^{-1} and
-        # A^{-1} -= W T) plus 2 N k^2 for W = P Kinv; per launch = per flush.
-        flops = 4.0 * N * N * acc_per_gpu
-        ms = prof["flush_ms"]
-        per_launch = flops / prof["flushes"]
-        achieved = per_launch / (ms / prof["flushes"] * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS if a.precision == "fp64" else None
-        key = source_hash("kernels_gemm.cu")
-        traffic = NCU_TRAFFIC.get(key)
-        return {"kernel": "flush (Eq. 4): T = V'A^-1, W = P Kinv, A^-1 -= W T",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": traffic,
-                "peak_source": "nominal B300 fp64 rate (not in MEASURED_PEAKS.json)",
-                "flops_per_launch": per_launch, "launches": prof["flushes"],
-                "avg_launch_ms": ms / prof["flushes"],
-                "share_of_step": ms / res["total_ms"] if res["total_ms"] else None}
-    # K = 1: the Sherman-Morrison pass moves 2 N^2 elements per accepted move
-    es = 8 if a.precision == "fp64" else 4
-    peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK_GBS)
-    byts = 2.0 * N * N * es * acc_per_gpu
-    achieved = byts / (res["total_ms"] * 1e-3) / 1e9
-    return {"kernel": "sm_update (Eq. 2)", "bound": "hbm", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None}
+    prop_per_gpu = a.steps * a.sweeps_per_step * a.N * a.batch
+    kbar = 0.0 if K == 1 else (K - 1) / 2.0
+    flops = 4.0 * N * N * acc_per_gpu + 2.0 * (2 * kbar + 2) * N * prop_per_gpu + 4.0 * kbar * N * acc_per_gpu
+    launches = prof.get("sweep_kernels", 0)
+    ms = prof.get("sweep_kernel_ms", 0.0)
+    if not launches or ms <= 0:
+        return None
+    achieved = flops / launches / (ms / launches * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS if a.precision == "fp64" else FP32_PEAK_TFLOPS
+    key = source_hash("kernels_sweep.cu")
+    return {"kernel": "sweep_kernel (persistent fused sweep: Eq. 3 ratios, bordered append, Eq. 4 flush)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(key),
+            "peak_source": "derived: 148 SMs x %s FMA/clk x 2 x 2032 MHz"
+                           % ("2 FP64" if a.precision == "fp64" else "128 FP32"),
+            "flops_per_launch": flops / launches, "launches": launches,
+            "avg_launch_ms": ms / launches,
+            "share_of_step": ms / res["total_ms"] if res["total_ms"] else None}
 
 
 def main():
@@ -328,7 +334,7 @@ def main():
         nm = cpu_sample_size(a, seconds=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
         vals = []
         for it in range(a.warmup + a.steps):
-            acc, dt = cpu_oracle_sample(a, nm)
+            acc, dt, _ = cpu_oracle_sample(a, nm)
             if it >= a.warmup:
                 vals.append(acc / dt)
         v = float(np.median(vals))
@@ -337,7 +343,8 @@ def main():
                 "higher_is_better": True, "dtype": "f64", "data": "synthetic",
                 "config": config(a, 1),
                 "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                                 "sample": "first %d proposals of sweep 0, one walker" % nm},
+                                 "sample": "first %d proposals of sweep 0, one walker "
+                                           "(setup inverse timed apart and excluded)" % nm},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -374,19 +381,25 @@ def main():
                    "d2h_bytes_per_step": a.sweeps_per_step * a.batch * a.N + a.batch * 12}
     prof = res["prof"] or {}
     line["gpu_launches"] = int(prof.get("launches", 0))
+    sweep_ms = prof.get("sweep_kernel_ms", 0.0)
+    rec_ms = prof.get("recompute_ms", 0.0)
     line["breakdown_ms_per_step"] = {
-        "flush": prof.get("flush_ms", 0.0) / a.steps,
-        "recompute": prof.get("recompute_ms", 0.0) / a.steps,
-        "moves (ratio + accept + sync)": (res["total_ms"] - prof.get("flush_ms", 0.0)
-                                          - prof.get("recompute_ms", 0.0)) / a.steps}
+        "sweep kernel": sweep_ms / a.steps,
+        "recompute (fp64 Gauss-Jordan)": rec_ms / a.steps,
+        "proposal draws + log-det + launches": (res["total_ms"] - sweep_ms - rec_ms) / a.steps}
+    nprop = a.steps * a.sweeps_per_step * a.N
+    line["sweep_phases_us_per_proposal"] = {
+        k[6:-3]: v * 1000.0 / nprop for k, v in prof.items()
+        if k.startswith("sweep_") and k.endswith("_ms") and k != "sweep_kernel_ms"}
     line["clocks"] = res["clocks"]
     if a.gpus == 1:
         nm = cpu_sample_size(a)
-        acc, dt = cpu_oracle_sample(a, nm)
+        acc, dt, t_setup = cpu_oracle_sample(a, nm)
         line["cpu_baseline"] = {"value": acc / dt, "unit": "updates/s", "cores": 1,
                                 "kind": "oracle",
-                                "sample": "first %d proposals of sweep 0 of one walker (N=%d, K=%d), "
-                                          "%.1f s" % (nm, a.N, a.K, dt)}
+                                "sample": "first %d proposals of sweep 0 of one walker (N=%d, K=%d): "
+                                          "%.1f s of updates; the %.1f s setup inverse excluded"
+                                          % (nm, a.N, a.K, dt, t_setup)}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -174,10 +174,15 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
  * Profiling. While enabled, the library records CUDA events on the handle's
  * stream around every flush (Eq. 4) and every recompute, and counts its
  * kernel launches. qmcdu_profile_enable(h, 1) resets the counters; 0 stops.
- * qmcdu_profile_read synchronises and writes n <= 8 values to out (host):
+ * qmcdu_profile_read synchronises and writes n <= 18 values to out (host):
  *   [0] kernel launches  [1] flushes   [2] flush time (ms)
  *   [3] recomputes       [4] recompute time (ms)   [5] stream syncs inside
  *   sweeps  [6] ratio launches  [7] accept launches
+ *   [8..15] persistent sweeps, walker 0's lead CTA, time (ms) in: partial
+ *   dot products, staging the next proposal, the group barrier, reduction and
+ *   decision, accept, the flush's first barrier, the flush arithmetic, the
+ *   flush's second barrier (host-driven sweeps time [2] instead)
+ *   [16] persistent sweep kernel launches  [17] their total time (ms)
  */
 int qmcdu_profile_enable(qmcdu_t h, int enable);
 int qmcdu_profile_read(qmcdu_t h, double *out, int n);

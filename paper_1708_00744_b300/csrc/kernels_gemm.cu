@@ -30,14 +30,13 @@ struct GemmArgs {
 };
 
 constexpr int GTHREADS = 256;
-constexpr int GBK = 16;
 
 // C tile BM x BN per CTA, 256 threads in a 16 x 16 grid, each thread
 // (BM/16) x (BN/16) outputs spaced 16 apart. Operand tiles staged in shared
 // memory in the accumulation type; A_L_CONTIG / B_N_CONTIG pick which operand
 // dimension is contiguous so that global loads are coalesced.
 template <typename TA, typename TB, typename TC, typename Acc, int BM, int BN, bool A_L_CONTIG,
-          bool B_N_CONTIG>
+          bool B_N_CONTIG, int GBK = 16>
 __global__ void __launch_bounds__(GTHREADS) gemm_tile_kernel(GemmArgs<TA, TB, TC> g)
 {
     constexpr int TM = BM / 16, TN = BN / 16;
@@ -185,8 +184,12 @@ cudaError_t launch_gj_update(Ctx &c, int nbe)
     g.M = N; g.Nn = N; g.Kd = nbe;
     g.alpha = 1.0; g.accumulate = 1;
     dim3 grid((N + 63) / 64, (N + 63) / 64, c.batch);
-    gemm_tile_kernel<double, double, double, double, 64, 64, false, true>
-        <<<grid, GTHREADS, 0, c.stream>>>(g);
+    if (nbe <= 8)   // the inner dimension is the panel width: no zero padding to 16
+        gemm_tile_kernel<double, double, double, double, 64, 64, false, true, 8>
+            <<<grid, GTHREADS, 0, c.stream>>>(g);
+    else
+        gemm_tile_kernel<double, double, double, double, 64, 64, false, true, 16>
+            <<<grid, GTHREADS, 0, c.stream>>>(g);
     return cudaGetLastError();
 }
 

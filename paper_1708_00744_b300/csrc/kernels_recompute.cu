@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
             __syncthreads();
             continue;
         }
-        la += log(fabs(pv));
+        if (tid == 0) la += log(fabs(pv));   // one thread: fp64 log is costly on this part
         if (pv < 0.0) sg = -sg;
         if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : S[c * nb + tid] / pv;
         __syncthreads();

@@ -1,5 +1,5 @@
 // kernels_sweep.cu -- one Metropolis sweep per walker in a single persistent,
-// cooperative kernel launch (proposal, ratio, decision, accept and flush fused).
+// cooperative kernel launch (ratio, decision, accept and flush fused).
 //
 // Each walker is served by a group of Gf CTAs. The first Gr of them (the ratio
 // CTAs) each own a chunk of rows of the N-vectors and advance the proposals in
@@ -14,10 +14,19 @@
 //   r  = d - y.c                            (ratio of the proposal, Eq. 3)
 //   z  = a - W c,   W <- [W - z y'/r, z/r]   (append on accept)
 // so every step is an N-parallel dot product or axpy over the row chunks, with
-// no k x k work on the critical path.
+// no k x k work on the critical path. When a ratio CTA's rows of W and V fit,
+// they stay in its shared memory for the whole sweep (RES) and are written to
+// global memory only for a flush.
 //
 // Flush (column c of the column-major A^{-1}, T = V'A^{-1} - E'):
 //   t_m = V[m] . A^{-1}[:, c] - [idx_m == c],   A^{-1}[:, c] -= sum_m t_m W[m].
+// Column tiles are brought into shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier).
+//
+// The proposal Gaussians and Metropolis uniforms of the sweep are drawn up
+// front by a fully parallel kernel (sweep_draw_kernel), and the running
+// log|det A| is brought up to date after the sweep from the recorded ratios,
+// so that neither costs time on the sequential chain of proposals.
 //
 // Every spin-wait has a time budget (globaltimer); on expiry the kernel sets
 // ST_TIMEOUT in the status word and returns. Data written by other CTAs is read
@@ -35,6 +44,7 @@ namespace qmcdu {
 constexpr int STHREADS = 256;
 constexpr int SWARPS = STHREADS / 32;
 constexpr int MAX_CB = 8;
+constexpr int SYNC_STRIDE = 96;   // unsigned words per walker group: three 128-byte lines
 
 template <typename T>
 struct SweepParams {
@@ -43,13 +53,12 @@ struct SweepParams {
     double *A;
     T *Ainv, *W, *V;
     int *idx, *kglob;
-    double *logabs;
-    int *sign;
+    const double *gauss;    // [batch][N][ld] proposal Gaussians of this sweep
+    const double *unif;     // [batch][N] Metropolis uniforms of this sweep
     double *partial;        // [ngroups][2][Gr][2K+1]
-    unsigned *sync;         // [ngroups][4]: ratio barrier, flush barrier, flush command
+    unsigned *sync;         // [ngroups][SYNC_STRIDE]: ratio barrier, flush barrier, flush command,
+                            // each on its own 128-byte line
     int *status;
-    unsigned long long seed;
-    int sweep;
     double sigma;
     const signed char *override_;
     unsigned char *acc_out;
@@ -57,7 +66,8 @@ struct SweepParams {
     long long *ties;
     long long budget_ns;    // per wait
     int stall;              // test hook: the first ratio barrier waits for one CTA too many
-    int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm;   // shared memory (bytes)
+    int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm, off_bar;
+    unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -74,21 +84,29 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Arrive (optionally) on a group counter, then wait until it reaches `target`.
-// Returns false, uniformly for the CTA, when the budget runs out or another
-// CTA has reported a timeout.
-__device__ bool group_wait(unsigned *ctr, unsigned target, bool arrive, int *status,
-                           long long budget_ns)
+// Arrival on a group counter (after all of this CTA's prior writes).
+__device__ __forceinline__ void group_arrive(unsigned *ctr)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+    }
+}
+
+// Wait until a group counter reaches `target`. Returns false, uniformly for
+// the CTA, when the budget runs out or another CTA has reported a timeout.
+__device__ bool group_wait_for(unsigned *ctr, unsigned target, int *status, long long budget_ns,
+                               unsigned backoff_ns = 0)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (arrive) atomicAdd(ctr, 1u);
         int ok = 1;
         const unsigned long long t0 = globaltimer();
         unsigned spins = 0;
         while (ld_acquire(ctr) < target) {
+            if (backoff_ns) __nanosleep(backoff_ns);
             if ((++spins & 63u) == 0) {
                 if ((long long)(globaltimer() - t0) > budget_ns) {
                     atomicOr(status, ST_TIMEOUT);
@@ -108,6 +126,13 @@ __device__ bool group_wait(unsigned *ctr, unsigned target, bool arrive, int *sta
     return ok_s != 0;
 }
 
+__device__ __forceinline__ bool group_barrier(unsigned *ctr, unsigned target, int *status,
+                                              long long budget_ns)
+{
+    group_arrive(ctr);
+    return group_wait_for(ctr, target, status, budget_ns);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_allsum(T v)
 {
@@ -116,15 +141,107 @@ __device__ __forceinline__ T warp_allsum(T v)
     return v;
 }
 
-// Flush of walker w on columns [c_begin, c_end): tiles of cb columns staged in
-// shared memory; V and W rows streamed from L2 once per tile.
+// ---- bulk asynchronous copy global -> shared, completion on an mbarrier
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *status,
+                                          long long budget_ns)
+{
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if ((long long)(globaltimer() - t0) > budget_ns) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Flush for a short queue (k < SMALL_K, including Sherman-Morrison at K = 1):
+// one warp per column, a dot-product pass and an update pass over the column
+// in global memory (no staging).
+constexpr int SMALL_K = 4;
+
 template <typename T>
-__device__ void flush_columns(const SweepParams<T> &p, int w, int k, int c_begin, int c_end,
-                              unsigned char *smem)
+__device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c_begin, int c_end)
+{
+    const int N = p.N, ld = p.ld, K = p.K;
+    const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
+    T *Ab = p.Ainv + (size_t)w * wN;
+    const T *Vb = p.V + (size_t)w * wK;
+    const T *Wb = p.W + (size_t)w * wK;
+    const int *idxw = p.idx + (size_t)w * K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = c_begin + warp; c < c_end; c += SWARPS) {
+        T *xc = Ab + (size_t)c * ld;
+        T t[SMALL_K];
+#pragma unroll
+        for (int m = 0; m < SMALL_K; ++m) t[m] = 0;
+#pragma unroll 4
+        for (int i = lane; i < N; i += 32) {
+            const T x = __ldcg(xc + i);
+#pragma unroll
+            for (int m = 0; m < SMALL_K; ++m)
+                if (m < k) t[m] += __ldcg(Vb + (size_t)m * ld + i) * x;
+        }
+#pragma unroll
+        for (int m = 0; m < SMALL_K; ++m) {
+            t[m] = warp_allsum(t[m]);
+            if (m < k && __ldcg(idxw + m) == c) t[m] -= (T)1;
+        }
+#pragma unroll 4
+        for (int i = lane; i < N; i += 32) {
+            T acc = 0;
+#pragma unroll
+            for (int m = 0; m < SMALL_K; ++m)
+                if (m < k) acc += t[m] * __ldcg(Wb + (size_t)m * ld + i);
+            xc[i] = __ldcg(xc + i) - acc;
+        }
+    }
+    __syncthreads();
+}
+
+// Flush of walker w on columns [c_begin, c_end): tiles of nc <= cb columns.
+// Each column is one bulk copy of ld elements (ld is a multiple of 16, so
+// every copy is 16-byte aligned and a multiple of 16 bytes long).
+template <typename T>
+__device__ bool flush_columns(const SweepParams<T> &p, int w, int k, int c_begin, int c_end,
+                              unsigned char *smem, unsigned &bar_phase)
 {
     const int N = p.N, ld = p.ld, K = p.K, cb = p.cb;
     T *xs = (T *)(smem + p.off_xs);
     T *ts = (T *)(smem + p.off_ts);
+    unsigned long long *bar = (unsigned long long *)(smem + p.off_bar);
+    __shared__ int ok_s;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     T *Ab = p.Ainv + (size_t)w * wN;
     const T *Vb = p.V + (size_t)w * wK;
@@ -134,82 +251,145 @@ __device__ void flush_columns(const SweepParams<T> &p, int w, int k, int c_begin
     for (int c0 = c_begin; c0 < c_end; c0 += cb) {
         const int nc = min(cb, c_end - c0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nc * N; e += STHREADS) {
-            const int cc = e / N, i = e - cc * N;
-            xs[(size_t)cc * N + i] = __ldcg(Ab + (size_t)(c0 + cc) * ld + i);
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async;" ::: "memory");
+            const unsigned bytes = (unsigned)(ld * sizeof(T));
+            mbar_expect(bar, bytes * nc);
+            for (int cc = 0; cc < nc; ++cc)
+                bulk_g2s(xs + (size_t)cc * ld, Ab + (size_t)(c0 + cc) * ld, bytes, bar);
+            ok_s = mbar_wait(bar, bar_phase, p.status, p.budget_ns) ? 1 : 0;
         }
+        bar_phase ^= 1u;
         __syncthreads();
-        for (int pr = warp; pr < k * nc; pr += SWARPS) {
-            const int m = pr / nc, cc = pr - m * nc;
-            const T *vr = Vb + (size_t)m * ld;
-            const T *xc = xs + (size_t)cc * N;
-            T acc = 0;
-            for (int i = lane; i < N; i += 32) acc += __ldcg(vr + i) * xc[i];
-            acc = warp_allsum(acc);
-            if (lane == 0) ts[m * cb + cc] = acc - (__ldcg(idxw + m) == c0 + cc ? (T)1 : (T)0);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < N; i += STHREADS) {
-            T acc[MAX_CB];
+        if (!ok_s) return false;
+        // T tile: t[m][cc] = V[m] . A^{-1}[:, c0 + cc] - [idx_m == c0 + cc], four rows per warp
+        for (int mb = warp * 4; mb < k; mb += SWARPS * 4) {
+            T acc[4][MAX_CB];
 #pragma unroll
-            for (int cc = 0; cc < MAX_CB; ++cc) acc[cc] = 0;
-            for (int m = 0; m < k; ++m) {
-                const T wv = __ldcg(Wb + (size_t)m * ld + i);
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int cc = 0; cc < MAX_CB; ++cc)
-                    if (cc < nc) acc[cc] += ts[m * cb + cc] * wv;
+                for (int cc = 0; cc < MAX_CB; ++cc) acc[r][cc] = 0;
+            const T *v0 = Vb + (size_t)mb * ld;
+            if (mb + 4 <= k) {
+#pragma unroll 2
+                for (int i = lane; i < N; i += 32) {
+                    T vv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vv[r] = __ldcg(v0 + (size_t)r * ld + i);
+#pragma unroll
+                    for (int cc = 0; cc < MAX_CB; ++cc) {
+                        if (cc < nc) {
+                            const T x = xs[(size_t)cc * ld + i];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) acc[r][cc] += vv[r] * x;
+                        }
+                    }
+                }
+            } else {
+                // tail rows one at a time (compile-time indices only)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    if (mb + r < k) {
+                        for (int i = lane; i < N; i += 32) {
+                            const T vv = __ldcg(v0 + (size_t)r * ld + i);
+#pragma unroll
+                            for (int cc = 0; cc < MAX_CB; ++cc)
+                                if (cc < nc) acc[r][cc] += vv * xs[(size_t)cc * ld + i];
+                        }
+                    }
+                }
             }
 #pragma unroll
-            for (int cc = 0; cc < MAX_CB; ++cc)
-                if (cc < nc) Ab[(size_t)(c0 + cc) * ld + i] = xs[(size_t)cc * N + i] - acc[cc];
+            for (int r = 0; r < 4; ++r) {
+                const int m = mb + r;
+                const int im = m < k ? __ldcg(idxw + m) : -1;
+#pragma unroll
+                for (int cc = 0; cc < MAX_CB; ++cc) {
+                    const T v = warp_allsum(acc[r][cc]);
+                    if (lane == 0 && cc < nc && m < k)
+                        ts[m * cb + cc] = v - (im == c0 + cc ? (T)1 : (T)0);
+                }
+            }
+        }
+        __syncthreads();
+        // update: A^{-1}[:, c0 + cc] -= sum_m t[m][cc] W[m], two rows per thread
+        for (int i = threadIdx.x; i < N; i += 2 * STHREADS) {
+            const int i2 = i + STHREADS;
+            const bool two = i2 < N;
+            T a0[MAX_CB], a1[MAX_CB];
+#pragma unroll
+            for (int cc = 0; cc < MAX_CB; ++cc) a0[cc] = a1[cc] = 0;
+#pragma unroll 2
+            for (int m = 0; m < k; ++m) {
+                const T w0 = __ldcg(Wb + (size_t)m * ld + i);
+                const T w1 = two ? __ldcg(Wb + (size_t)m * ld + i2) : (T)0;
+#pragma unroll
+                for (int cc = 0; cc < MAX_CB; ++cc) {
+                    if (cc < nc) {
+                        const T t = ts[m * cb + cc];
+                        a0[cc] += t * w0;
+                        a1[cc] += t * w1;
+                    }
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < MAX_CB; ++cc) {
+                if (cc < nc) {
+                    Ab[(size_t)(c0 + cc) * ld + i] = xs[(size_t)cc * ld + i] - a0[cc];
+                    if (two) Ab[(size_t)(c0 + cc) * ld + i2] = xs[(size_t)cc * ld + i2] - a1[cc];
+                }
+            }
         }
     }
     __syncthreads();
+    return true;
 }
 
 template <typename T, bool RES>
-__global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
+__global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
     if (grp >= p.ngroups) return;
     const int N = p.N, K = p.K, ld = p.ld, Gf = p.Gf, Gr = p.Gr;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
-    unsigned *ratio_ctr = p.sync + 4 * grp + 0;
-    unsigned *flush_ctr = p.sync + 4 * grp + 1;
-    unsigned *cmd = p.sync + 4 * grp + 2;
-    unsigned n_ratio = 0, n_flush = 0, n_event = 0;
+    unsigned *ratio_ctr = p.sync + SYNC_STRIDE * grp + 0;
+    unsigned *flush_ctr = p.sync + SYNC_STRIDE * grp + 32;
+    unsigned *cmd = p.sync + SYNC_STRIDE * grp + 64;
+    unsigned n_ratio = 0, n_flush = 0, n_event = 0, bar_phase = 0;
     const int cpc = (N + Gf - 1) / Gf;                 // columns per CTA in the flush
     const int fc0 = min(N, rank * cpc), fc1 = min(N, fc0 + cpc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) mbar_init((unsigned long long *)(smem + p.off_bar));
+    __syncthreads();
 
     if (rank >= Gr) {
         // Helper CTA: take part in every flush of every walker of the group.
         for (int w = grp; w < p.batch; w += p.ngroups) {
             for (;;) {
-                if (!group_wait(cmd, 2u * (n_event + 1), false, p.status, p.budget_ns)) return;
+                if (!group_wait_for(cmd, 2u * (n_event + 1), p.status, p.budget_ns, 128)) return;
                 const bool last = (ld_acquire(cmd) & 1u) != 0;
                 ++n_event;
-                if (!group_wait(flush_ctr, (++n_flush) * Gf, true, p.status, p.budget_ns)) return;
+                if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
                 const int k = __ldcg(p.kglob + w);
-                if (k > 0) flush_columns(p, w, k, fc0, fc1, smem);
-                if (!group_wait(flush_ctr, (++n_flush) * Gf, true, p.status, p.budget_ns)) return;
+                if (k > 0 && k < SMALL_K) flush_columns_small(p, w, k, fc0, fc1);
+                else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) return;
+                if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
                 if (last) break;
             }
         }
         return;
     }
 
-    // Ratio CTA: rows [i0, i0 + L) of every N-vector. RES: this CTA's rows of
-    // the queue panels W and V stay in shared memory for the whole sweep and
-    // are written to global memory only for a flush.
+    // Ratio CTA: rows [i0, i0 + L) of every N-vector.
     T *vs = (T *)(smem + p.off_vs);                    // [2][chunk] proposed row (working prec.)
     T *as = (T *)(smem + p.off_as);                    // [2][chunk] column j of A^{-1}
     double *vd = (double *)(smem + p.off_vd);          // [2][chunk] proposed row (fp64)
     double *red = (double *)(smem + p.off_red);        // [2K+1] reduced dots
+    T *coef = (T *)(smem + p.off_ts);                  // accept: [0,K) c_m, [K,2K) y_m/r, [2K,..) z
     T *Wsm = (T *)(smem + p.off_wsm);                  // RES: [K][LP]
     T *Vsm = (T *)(smem + p.off_vsm);                  // RES: [K][LP]
-    __shared__ double rr_s;
+    __shared__ double rr_s, u_s[2];
     __shared__ int acc_s;
     const int chunk = p.chunk, LP = chunk + 1;
     const int i0 = rank * chunk;
@@ -217,28 +397,24 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
     const int nj = 2 * K + 1;
 
     for (int w = grp; w < p.batch; w += p.ngroups) {
-        const unsigned long long wseed = p.seed + (unsigned long long)w;
         double *Aw = p.A + (size_t)w * wN;
         const T *Ainv = p.Ainv + (size_t)w * wN;
+        const double *Gw = p.gauss + (size_t)w * wN;
+        const double *Uw = p.unif + (size_t)w * N;
         T *Ww = p.W + (size_t)w * wK;
         T *Vw = p.V + (size_t)w * wK;
 
-        // proposal row of electron jj into buffer bb; column jj of A^{-1} too
+        // proposed row of electron jj (v = a_jj + sigma g) and column jj of A^{-1}
         auto stage = [&](int jj, int bb, bool row, bool col) {
             if (row) {
-                const double *arow = Aw + (size_t)jj * ld;
-                for (int q = threadIdx.x; 2 * q < L; q += STHREADS) {
-                    const int i = i0 + 2 * q;
-                    const double2 g = proposal_gaussian_pair(wseed, jj, p.sweep, i >> 1);
-                    const double v0 = arow[i] + p.sigma * g.x;
-                    vs[bb * chunk + 2 * q] = (T)v0;
-                    vd[bb * chunk + 2 * q] = v0;
-                    if (2 * q + 1 < L) {
-                        const double v1 = arow[i + 1] + p.sigma * g.y;
-                        vs[bb * chunk + 2 * q + 1] = (T)v1;
-                        vd[bb * chunk + 2 * q + 1] = v1;
-                    }
+                const double *arow = Aw + (size_t)jj * ld + i0;
+                const double *grow = Gw + (size_t)jj * ld + i0;
+                for (int t = threadIdx.x; t < L; t += STHREADS) {
+                    const double v = arow[t] + p.sigma * __ldcg(grow + t);
+                    vs[bb * chunk + t] = (T)v;
+                    vd[bb * chunk + t] = v;
                 }
+                if (threadIdx.x == 0) u_s[bb] = __ldcg(Uw + jj);
             }
             if (col) {
                 const T *acol = Ainv + (size_t)jj * ld + i0;
@@ -249,6 +425,15 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
         int k = 0;
         __syncthreads();
         stage(0, 0, true, true);
+        const bool timed = p.phase_ns && grp == 0 && rank == 0 && threadIdx.x == 0;
+        unsigned long long tp = timed ? globaltimer() : 0ull, ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        auto tick = [&](int slot) {
+            if (timed) {
+                const unsigned long long t = globaltimer();
+                ph[slot] += t - tp;
+                tp = t;
+            }
+        };
         for (int j = 0; j < N; ++j) {
             const int b = j & 1;
             const T *vsb = vs + b * chunk, *asb = as + b * chunk;
@@ -259,11 +444,16 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
             if (RES) {
                 for (int job = threadIdx.x; job < 2 * k + 1; job += STHREADS) {
                     const T *src = job == 0 ? asb : (job <= k ? Wsm + (job - 1) * LP : Vsm + (job - 1 - k) * LP);
-                    const T *with = (job >= 1 && job <= k) ? vsb : (job == 0 ? vsb : asb);
-                    T acc = 0;
-#pragma unroll 8
-                    for (int t = 0; t < L; ++t) acc += src[t] * with[t];
-                    part[job] = (double)acc;
+                    const T *with = job <= k ? vsb : asb;
+                    T acc0 = 0, acc1 = 0;
+                    int t = 0;
+#pragma unroll 4
+                    for (; t + 1 < L; t += 2) {
+                        acc0 += src[t] * with[t];
+                        acc1 += src[t + 1] * with[t + 1];
+                    }
+                    if (t < L) acc0 += src[t] * with[t];
+                    part[job] = (double)acc0 + (double)acc1;
                 }
             } else {
                 for (int job = warp; job < 2 * k + 1; job += SWARPS) {
@@ -278,16 +468,27 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
                     if (lane == 0) part[job] = (double)acc;
                 }
             }
-            // ---- next proposal's row, and (speculatively) its column of A^{-1}
-            if (j + 1 < N) stage(j + 1, b ^ 1, true, true);
-            // ---- group barrier, then every ratio CTA sums the partials in order
+            tick(0);
+            // ---- arrive, stage the next proposal (its column speculatively), wait
             const unsigned extra = (p.stall && n_ratio == 0) ? 1u : 0u;
-            if (!group_wait(ratio_ctr, (++n_ratio) * Gr + extra, true, p.status, p.budget_ns)) return;
+            group_arrive(ratio_ctr);
+            if (j + 1 < N) stage(j + 1, b ^ 1, true, true);
+            tick(1);
+            if (!group_wait_for(ratio_ctr, (++n_ratio) * Gr + extra, p.status, p.budget_ns)) return;
+            tick(2);
+            // ---- every ratio CTA sums the partials in the same order
             const double *pb = p.partial + ((size_t)grp * 2 + b) * Gr * nj;
             for (int job = threadIdx.x; job < 2 * k + 1; job += STHREADS) {
                 double s = 0.0;
-#pragma unroll 8
-                for (int q = 0; q < Gr; ++q) s += __ldcg(pb + (size_t)q * nj + job);
+                int q = 0;
+                for (; q + 8 <= Gr; q += 8) {
+                    double x[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e) * nj + job);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) s += x[e];
+                }
+                for (; q < Gr; ++q) s += __ldcg(pb + (size_t)q * nj + job);
                 red[job] = s;
             }
             __syncthreads();
@@ -297,7 +498,7 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
                 s = warp_allsum(s);
                 if (lane == 0) {
                     const double r = red[0] - s;
-                    const double u = metropolis_uniform(wseed, j, p.sweep);
+                    const double u = u_s[b];
                     const double prob = fmin(1.0, r * r);
                     const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
                     int a = ov == 0 ? 0 : (ov == 1 ? 1 : (u < prob ? 1 : 0));
@@ -308,52 +509,61 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
                     rr_s = r;
                     acc_s = a;
                     if (rank == 0) {
-                        if (p.acc_out) p.acc_out[(size_t)w * N + j] = (unsigned char)a;
-                        if (p.ratio_out) p.ratio_out[(size_t)w * N + j] = r;
-                        if (p.ties && fabs(prob - u) < 1e-10) p.ties[w] += 1;
-                        if (a) {
-                            p.logabs[w] += log(fabs(r));
-                            if (r < 0.0) p.sign[w] = -p.sign[w];
-                            p.idx[(size_t)w * K + k] = j;
-                        }
+                        p.acc_out[(size_t)w * N + j] = (unsigned char)a;
+                        p.ratio_out[(size_t)w * N + j] = r;
+                        if (fabs(prob - u) < 1e-10) p.ties[w] += 1;
+                        if (a) p.idx[(size_t)w * K + k] = j;
                     }
                 }
             }
             __syncthreads();
+            tick(3);
             if (acc_s) {
                 // ---- accept: z = a - W c, W <- [W - z y'/r, z/r], V[k] = v, A[j] = v
                 const double rinv = 1.0 / rr_s;
-                const double *yv = red + 1, *cv = red + 1 + k;
+                T *cT = coef, *yT = coef + K, *zs = coef + 2 * K;
+                for (int m = threadIdx.x; m < k; m += STHREADS) {
+                    cT[m] = (T)red[1 + k + m];
+                    yT[m] = (T)(red[1 + m] * rinv);
+                }
+                __syncthreads();
                 double *arow_w = Aw + (size_t)j * ld;
                 if (RES) {
-                    T *zs = (T *)(smem + p.off_ts);        // the flush tile is idle here
                     for (int t = threadIdx.x; t < L; t += STHREADS) {
-                        T z = asb[t];
-#pragma unroll 8
-                        for (int m = 0; m < k; ++m) z -= (T)cv[m] * Wsm[m * LP + t];
-                        zs[t] = z;
+                        T z0 = asb[t], z1 = 0;
+                        int m = 0;
+#pragma unroll 4
+                        for (; m + 1 < k; m += 2) {
+                            z0 -= cT[m] * Wsm[m * LP + t];
+                            z1 -= cT[m + 1] * Wsm[(m + 1) * LP + t];
+                        }
+                        if (m < k) z0 -= cT[m] * Wsm[m * LP + t];
+                        zs[t] = z0 + z1;
                         Vsm[k * LP + t] = vsb[t];
                         arow_w[i0 + t] = vdb[t];
                     }
                     __syncthreads();
+                    const T rT = (T)rinv;
                     for (int e = threadIdx.x; e < (k + 1) * L; e += STHREADS) {
                         const int m = e / L, t = e - m * L;
-                        if (m < k) Wsm[m * LP + t] -= zs[t] * (T)(yv[m] * rinv);
-                        else Wsm[k * LP + t] = zs[t] * (T)rinv;
+                        if (m < k) Wsm[m * LP + t] -= zs[t] * yT[m];
+                        else Wsm[k * LP + t] = zs[t] * rT;
                     }
                 } else {
+                    const T rT = (T)rinv;
                     for (int t = threadIdx.x; t < L; t += STHREADS) {
                         const int i = i0 + t;
                         T z = asb[t];
-                        for (int m = 0; m < k; ++m) z -= (T)cv[m] * Ww[(size_t)m * ld + i];
-                        for (int m = 0; m < k; ++m) Ww[(size_t)m * ld + i] -= z * (T)(yv[m] * rinv);
-                        Ww[(size_t)k * ld + i] = z * (T)rinv;
+                        for (int m = 0; m < k; ++m) z -= cT[m] * Ww[(size_t)m * ld + i];
+                        for (int m = 0; m < k; ++m) Ww[(size_t)m * ld + i] -= z * yT[m];
+                        Ww[(size_t)k * ld + i] = z * rT;
                         Vw[(size_t)k * ld + i] = vsb[t];
                         arow_w[i] = vdb[t];
                     }
                 }
                 ++k;
             }
+            tick(4);
             const bool last = (j == N - 1);
             if (k < K && !last) continue;
             // ---- flush event: queue full, or end of the walker's sweep
@@ -371,12 +581,73 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
                 atomicExch(cmd, 2u * (n_event + 1) + (last ? 1u : 0u));
             }
             ++n_event;
-            if (!group_wait(flush_ctr, (++n_flush) * Gf, true, p.status, p.budget_ns)) return;
-            if (k > 0) flush_columns(p, w, k, fc0, fc1, smem);
-            if (!group_wait(flush_ctr, (++n_flush) * Gf, true, p.status, p.budget_ns)) return;
+            if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
+            tick(5);
+            if (k > 0 && k < SMALL_K) flush_columns_small(p, w, k, fc0, fc1);
+            else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) return;
+            tick(6);
+            if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
             if (k > 0 && j + 1 < N) stage(j + 1, b ^ 1, false, true);   // the column changed
             k = 0;
+            tick(7);
         }
+        if (timed)
+            for (int q = 0; q < 8; ++q) p.phase_ns[q] += ph[q];
+    }
+}
+
+// Gaussians (Box-Muller pairs) and Metropolis uniforms of one sweep for every
+// walker, from the Philox counters of qmcdu_sweep.
+__global__ void sweep_draw_kernel(int N, int ld, int batch, unsigned long long seed, int sweep,
+                                  double *gauss, double *unif)
+{
+    const int npair = (N + 1) / 2;
+    const long long per_w = (long long)N * npair;
+    const long long total = per_w * batch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e / per_w);
+        const long long r = e - (long long)w * per_w;
+        const int j = (int)(r / npair), q = (int)(r - (long long)j * npair);
+        const unsigned long long ws = seed + (unsigned long long)w;
+        const double2 g = proposal_gaussian_pair(ws, j, sweep, q);
+        double *row = gauss + ((size_t)w * N + j) * ld;
+        row[2 * q] = g.x;
+        if (2 * q + 1 < N) row[2 * q + 1] = g.y;
+        if (q == 0) unif[(size_t)w * N + j] = metropolis_uniform(ws, j, sweep);
+    }
+}
+
+// log|det A| and sign after the sweep: one CTA per walker sums log|r| over the
+// accepted proposals in a fixed order.
+__global__ void sweep_logdet_kernel(int N, const unsigned char *acc, const double *ratio,
+                                    double *logabs, int *sign)
+{
+    const int w = blockIdx.x;
+    __shared__ double sred[STHREADS];
+    __shared__ int sneg[STHREADS];
+    double s = 0.0;
+    int neg = 0;
+    for (int j = threadIdx.x; j < N; j += STHREADS) {
+        if (acc[(size_t)w * N + j]) {
+            const double r = ratio[(size_t)w * N + j];
+            s += log(fabs(r));
+            neg += r < 0.0;
+        }
+    }
+    sred[threadIdx.x] = s;
+    sneg[threadIdx.x] = neg;
+    __syncthreads();
+    for (int o = STHREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sred[threadIdx.x] += sred[threadIdx.x + o];
+            sneg[threadIdx.x] += sneg[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        logabs[w] += sred[0];
+        if (sneg[0] & 1) sign[w] = -sign[w];
     }
 }
 
@@ -384,15 +655,16 @@ __global__ void __launch_bounds__(STHREADS) sweep_kernel(SweepParams<T> p)
 static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 template <typename T>
-static size_t sweep_smem(int N, int K, int chunk, int cb, bool res, int *offs)
+static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int *offs)
 {
     size_t o = 0;
+    offs[8] = (int)o; o = align16(o + 16);                                   // mbarrier
     offs[0] = (int)o; o = align16(o + (size_t)2 * chunk * sizeof(T));        // vs
     offs[1] = (int)o; o = align16(o + (size_t)2 * chunk * sizeof(T));        // as
     offs[2] = (int)o; o = align16(o + (size_t)2 * chunk * sizeof(double));   // vd
     offs[3] = (int)o; o = align16(o + (size_t)(2 * K + 1) * sizeof(double)); // red
-    offs[4] = (int)o; o = align16(o + (size_t)std::max(K * cb, chunk) * sizeof(T));  // ts / z
-    offs[5] = (int)o; o = align16(o + (size_t)cb * N * sizeof(T));           // xs
+    offs[4] = (int)o; o = align16(o + (size_t)std::max(K * cb, 2 * K + chunk) * sizeof(T));  // ts
+    offs[5] = (int)o; o = align16(o + (size_t)cb * ld * sizeof(T));          // xs
     offs[6] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Wsm
     offs[7] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Vsm
     return o;
@@ -404,13 +676,13 @@ static const size_t RES_BUDGET = 128 * 1024;
 template <typename T, bool RES>
 static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, int chunk)
 {
-    const int N = c.N, K = c.K;
-    int offs[8];
+    const int K = c.K;
+    int offs[9];
     int cb = MAX_CB;
-    size_t smem = sweep_smem<T>(N, K, chunk, cb, RES, offs);
+    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, offs);
     while (cb > 1 && smem > SMEM_BUDGET) {
         cb >>= 1;
-        smem = sweep_smem<T>(N, K, chunk, cb, RES, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, offs);
     }
     if (smem > SMEM_BUDGET) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES>,
@@ -422,21 +694,24 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     const int capacity = per_sm * c.num_sms;
     if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
     const int ngroups = std::min(c.batch, std::max(1, capacity / Gf));
-    if (ngroups * 4 > c.sync_words) return cudaErrorInvalidConfiguration;
+    if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
     if ((size_t)ngroups * 2 * Gr * (2 * K + 1) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
 
     SweepParams<T> p;
-    p.N = N; p.K = K; p.ld = c.ld; p.batch = c.batch;
+    p.N = c.N; p.K = K; p.ld = c.ld; p.batch = c.batch;
     p.Gf = Gf; p.Gr = Gr; p.ngroups = ngroups; p.chunk = chunk; p.cb = cb;
     p.A = c.A; p.Ainv = (T *)c.Ainv; p.W = (T *)c.P; p.V = (T *)c.V;
-    p.idx = c.idx; p.kglob = c.kcount; p.logabs = c.logabs; p.sign = c.sign;
+    p.idx = c.idx; p.kglob = c.kcount;
+    p.gauss = c.sw_gauss; p.unif = c.sw_unif;
     p.partial = c.sw_partial; p.sync = c.sw_sync; p.status = c.status;
-    p.seed = L.seed; p.sweep = L.sweep; p.sigma = L.sigma; p.override_ = L.override;
+    p.sigma = L.sigma; p.override_ = L.override;
     p.acc_out = L.acc_out; p.ratio_out = L.ratio_out; p.ties = L.ties;
     p.budget_ns = c.opt_budget_ns; p.stall = c.opt_stall;
     p.off_vs = offs[0]; p.off_as = offs[1]; p.off_vd = offs[2]; p.off_red = offs[3];
     p.off_ts = offs[4]; p.off_xs = offs[5]; p.off_wsm = offs[6]; p.off_vsm = offs[7];
-    e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * 4 * sizeof(unsigned), c.stream);
+    p.off_bar = offs[8];
+    p.phase_ns = c.prof ? c.sw_phase : nullptr;
+    e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {&p};
     e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES>, dim3(ngroups * Gf),
@@ -473,7 +748,20 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
 
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)
 {
-    return c.prec == QMCDU_FP64 ? launch_sweep_t<double>(c, L) : launch_sweep_t<float>(c, L);
+    // the sweep's proposal draws, then the sweep, then the running log-det
+    sweep_draw_kernel<<<c.num_sms * 8, 256, 0, c.stream>>>(c.N, c.ld, c.batch, L.seed, L.sweep,
+                                                           c.sw_gauss, c.sw_unif);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = prof_begin(&c, c.ev_sweep);
+    if (e != cudaSuccess) return e;
+    e = c.prec == QMCDU_FP64 ? launch_sweep_t<double>(c, L) : launch_sweep_t<float>(c, L);
+    if (e != cudaSuccess) return e;
+    e = prof_end(&c, c.ev_sweep);
+    if (e != cudaSuccess) return e;
+    sweep_logdet_kernel<<<c.batch, STHREADS, 0, c.stream>>>(c.N, L.acc_out, L.ratio_out, c.logabs,
+                                                            c.sign);
+    return cudaGetLastError();
 }
 
 }  // namespace qmcdu

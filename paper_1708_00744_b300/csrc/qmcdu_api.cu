@@ -52,7 +52,8 @@ static void release(Ctx *c)
                     c->sign, c->rs, c->partial, c->arrive, c->acc, c->elec_d, c->mask_d,
                     c->status, c->Tbuf, c->Wbuf, c->work, c->piv, c->colperm, c->Lt, c->R,
                     c->lu_logabs, c->lu_sign, c->drift, c->sw_acc, c->sw_ratio, c->sw_ties,
-                    c->sw_override, c->sw_partial, c->sw_sync};
+                    c->sw_override, c->sw_partial, c->sw_sync, c->sw_phase, c->sw_gauss,
+                    c->sw_unif};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -88,7 +89,7 @@ static void clear_queues(Ctx *c)
     }
 }
 
-static cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
+cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
 {
     if (!c->prof) return cudaSuccess;
     cudaEvent_t a, b;
@@ -99,7 +100,7 @@ static cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEve
     return e;
 }
 
-static cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
+cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v)
 {
     if (!c->prof || v.empty()) return cudaSuccess;
     return cudaEventRecord(v.back().second, c->stream);
@@ -148,7 +149,7 @@ static int do_accept(Ctx *c, const AcceptLaunch &L)
 
 static void drop_events(Ctx *c)
 {
-    for (auto *v : {&c->ev_flush, &c->ev_recompute}) {
+    for (auto *v : {&c->ev_flush, &c->ev_recompute, &c->ev_sweep}) {
         for (auto &p : *v) {
             cudaEventDestroy(p.first);
             cudaEventDestroy(p.second);
@@ -240,9 +241,12 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
     {
         const size_t cap = (size_t)c->num_sms * 8;   // 256-thread CTAs resident per GPU, at most
         c->sw_partial_len = cap * 2 * (2 * K + 1);
-        c->sync_words = (int)(cap * 4);
+        c->sync_words = (int)(cap * 96);
         AL(c->sw_partial, c->sw_partial_len * sizeof(double));
-        AL(c->sw_sync, cap * 4 * sizeof(unsigned));
+        AL(c->sw_sync, cap * 96 * sizeof(unsigned));
+        AL(c->sw_phase, 8 * sizeof(unsigned long long));
+        AL(c->sw_gauss, B * NN * sizeof(double));
+        AL(c->sw_unif, B * N * sizeof(double));
     }
 #undef AL
     if (e != cudaSuccess) {
@@ -444,7 +448,7 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         S.ratio_out = c->sw_ratio;
         S.ties = c->sw_ties;
         CK(launch_sweep(*c, S));
-        c->n_launch += 1;
+        c->n_launch += 3;
         c->opt_stall = 0;
         CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
         return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out);
@@ -555,6 +559,7 @@ int qmcdu_profile_enable(qmcdu_t h, int enable)
     drop_events(c);
     c->prof = enable != 0;
     c->n_launch = c->n_flush = c->n_recompute = c->n_sync = c->n_ratio = c->n_accept = 0;
+    CK(cudaMemset(c->sw_phase, 0, 8 * sizeof(unsigned long long)));
     return QMCDU_OK;
 }
 
@@ -563,7 +568,12 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n)
     if (!h || !out || n < 0) return QMCDU_ERR_ARG;
     Ctx *c = reinterpret_cast<Ctx *>(h);
     CK(cudaStreamSynchronize(c->stream));
-    double ms_flush = 0.0, ms_rec = 0.0;
+    double ms_flush = 0.0, ms_rec = 0.0, ms_sweep = 0.0;
+    for (auto &p : c->ev_sweep) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.first, p.second));
+        ms_sweep += ms;
+    }
     for (auto &p : c->ev_flush) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, p.first, p.second));
@@ -574,10 +584,15 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n)
         CK(cudaEventElapsedTime(&ms, p.first, p.second));
         ms_rec += ms;
     }
-    const double vals[8] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
-                            (double)c->n_recompute, ms_rec, (double)c->n_sync,
-                            (double)c->n_ratio, (double)c->n_accept};
-    for (int i = 0; i < n && i < 8; ++i) out[i] = vals[i];
+    unsigned long long ph[8];
+    CK(cudaMemcpy(ph, c->sw_phase, sizeof ph, cudaMemcpyDeviceToHost));
+    const double vals[18] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
+                             (double)c->n_recompute, ms_rec, (double)c->n_sync,
+                             (double)c->n_ratio, (double)c->n_accept,
+                             ph[0] * 1e-6, ph[1] * 1e-6, ph[2] * 1e-6, ph[3] * 1e-6,
+                             ph[4] * 1e-6, ph[5] * 1e-6, ph[6] * 1e-6, ph[7] * 1e-6,
+                             (double)c->ev_sweep.size(), ms_sweep};
+    for (int i = 0; i < n && i < 18; ++i) out[i] = vals[i];
     return QMCDU_OK;
 }
 

@@ -77,12 +77,15 @@ struct Ctx {
     // profiling (qmcdu_profile_*)
     bool prof = false;
     long long n_launch = 0, n_flush = 0, n_recompute = 0, n_sync = 0, n_ratio = 0, n_accept = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_flush, ev_recompute;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_flush, ev_recompute, ev_sweep;
     // persistent sweep (kernels_sweep.cu)
     int num_sms = 148;
     double *sw_partial = nullptr;   // capacity x 2 x (2K+1)
     size_t sw_partial_len = 0;
     unsigned *sw_sync = nullptr;    // capacity x 4
+    unsigned long long *sw_phase = nullptr;  // 8 phase timers of the persistent sweep
+    double *sw_gauss = nullptr;     // batch x N x ld proposal Gaussians of the current sweep
+    double *sw_unif = nullptr;      // batch x N Metropolis uniforms of the current sweep
     int sync_words = 0;
     int last_sweep_shape[5] = {0, 0, 0, 0, 0};   // Gf, Gr, groups, chunk, cb
     // options (qmcdu_set_option)
@@ -103,6 +106,8 @@ struct SweepLaunch {
     long long *ties;
 };
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L);
+cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
+cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
 
 size_t elem_size(int prec);
 

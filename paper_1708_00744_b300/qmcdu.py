@@ -227,7 +227,9 @@ def qmcdu_sweep_shape(h):
 
 
 PROFILE_FIELDS = ("launches", "flushes", "flush_ms", "recomputes", "recompute_ms", "sweep_syncs",
-                  "ratio_launches", "accept_launches")
+                  "ratio_launches", "accept_launches", "sweep_dots_ms", "sweep_stage_ms",
+                  "sweep_barrier_ms", "sweep_decide_ms", "sweep_accept_ms", "sweep_flushbar1_ms",
+                  "sweep_flush_ms", "sweep_flushbar2_ms", "sweep_kernels", "sweep_kernel_ms")
 
 
 def qmcdu_profile_enable(h, enable=True):
