@@ -157,7 +157,8 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
 /* Wait for the handle's stream and return the latched device status. */
 int qmcdu_sync(qmcdu_t h);
 
-/* Text of the last error on this handle ("" if none). Valid until the next call. */
+/* Text of the last error on this handle ("" if none). Valid until the next call.
+ * With h == NULL: the last error of a call without a handle on this thread. */
 const char *qmcdu_last_error(qmcdu_t h);
 
 /*
@@ -215,6 +216,39 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value);
  * flush column tile.
  */
 int qmcdu_sweep_shape(qmcdu_t h, int *shape5);
+
+/*
+ * Determinant ratio of one proposed move for callers that cannot allocate
+ * device memory. The paper has no counterpart to this entry point; it serves
+ * callers for whom cudaMalloc is not an option: code that must not
+ * synchronise the device (cudaMalloc can), or code running where another
+ * allocator (a framework's caching allocator, a pool reserved up front) owns
+ * the device's memory. It computes exactly what qmcdu_ratio computes for one
+ * walker, from a delay queue the caller holds, and allocates nothing: its
+ * scratch (the CTAs' partial sums and their arrival counter, 131,584 bytes) is
+ * a fixed array in the library's device memory, which every GPU that loads
+ * the library holds until the process exits.
+ *   N          1..8192 electrons;  k  0..min(N, 256) queued moves
+ *   ainv_col   device [N]     column j of A^{-1} as of the last flush (j is
+ *                             the moving electron, not among the queued ones)
+ *   v          device [N]     proposed new row j of A
+ *   P          device [k][N]  row m: column idx_m of A^{-1} as of the last flush
+ *   V          device [k][N]  row m: the new row of queued move m
+ *   Kinv       device [k][k]  (V P')^{-1}, row-major (P, V, Kinv may be NULL if k = 0)
+ *   ratio_out  device [1]     r = v.a - (P v)' Kinv (V a)
+ *   stream     cudaStream_t (NULL: the legacy default stream)
+ * Asynchronous on `stream`. Every call on a device shares the one scratch
+ * array, which keeps the last call's contents; each call clears what must
+ * start at zero. Calls whose executions overlap on the GPU (concurrent
+ * streams, or several host threads) race on the scratch and give wrong
+ * results: serialise them. The first call on a device looks up the scratch's
+ * device address (once per device, with that device current); make that first
+ * call before any stream capture. Errors: ERR_ARG for sizes beyond the limits
+ * above or null pointers, ERR_CUDA; the text is at qmcdu_last_error(NULL).
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v, const double *P,
+                        const double *V, const double *Kinv, double *ratio_out, void *stream);
 
 /* Library version string. */
 const char *qmcdu_version(void);

@@ -15,6 +15,10 @@ namespace qmcdu {
 
 size_t elem_size(int prec) { return prec == QMCDU_FP64 ? sizeof(double) : sizeof(float); }
 
+static thread_local std::string handleless_error;
+
+void set_handleless_error(const std::string &msg) { handleless_error = msg; }
+
 static int fail(Ctx *c, int code, const char *fmt, const char *detail = "")
 {
     if (c) {
@@ -183,7 +187,10 @@ extern "C" {
 
 const char *qmcdu_version(void) { return "qmcdu 0.1 (sm_103a)"; }
 
-const char *qmcdu_last_error(qmcdu_t h) { return h ? reinterpret_cast<Ctx *>(h)->err.c_str() : ""; }
+const char *qmcdu_last_error(qmcdu_t h)
+{
+    return h ? reinterpret_cast<Ctx *>(h)->err.c_str() : handleless_error.c_str();
+}
 
 int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *out)
 {

@@ -111,6 +111,9 @@ cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v
 
 size_t elem_size(int prec);
 
+// Error text of the last failed call that has no handle (qmcdu_last_error(NULL)).
+void set_handleless_error(const std::string &msg);
+
 // ---- launchers (kernels_move.cu) ----
 struct RatioLaunch {
     const double *v_in;         // [batch][N] or null when generating

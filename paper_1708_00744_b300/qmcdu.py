@@ -44,6 +44,7 @@ SIGNATURES = {
     "qmcdu_sweep_shape": (_I, [_VP, _VP]),
     "qmcdu_profile_enable": (_I, [_VP, _I]),
     "qmcdu_profile_read": (_I, [_VP, _VP, _I]),
+    "qmcdu_ratio_noalloc": (_I, [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "qmcdu_version": (ctypes.c_char_p, []),
 }
 
@@ -193,6 +194,21 @@ def qmcdu_sweep(h, base_seed, sweep_index, sigma, N, batch, override=None, accep
     _check("qmcdu_sweep", load().qmcdu_sweep(h, base_seed, sweep_index, sigma, _ptr(override),
                                              _ptr(accepted_out), _ptr(ratios_out),
                                              _ptr(near_ties_out)), h)
+
+
+def qmcdu_ratio_noalloc(N, k, ainv_col, v, P, V, Kinv, ratio_out, stream=None):
+    """Ratio of one proposal through a caller-held queue, with no device
+    allocation (see include/qmcdu.h)."""
+    for name, x, n in (("ainv_col", ainv_col, N), ("v", v, N), ("ratio_out", ratio_out, 1)):
+        _need(x, n, "float64", name, True)
+    if k > 0:
+        for name, x, n in (("P", P, k * N), ("V", V, k * N), ("Kinv", Kinv, k * k)):
+            _need(x, n, "float64", name, True)
+    st = load().qmcdu_ratio_noalloc(N, k, _ptr(ainv_col), _ptr(v), _ptr(P if k else None),
+                                    _ptr(V if k else None), _ptr(Kinv if k else None),
+                                    _ptr(ratio_out), _stream_ptr(stream))
+    if st != 0:
+        raise QmcduError("qmcdu_ratio_noalloc", st, load().qmcdu_last_error(None).decode())
 
 
 def qmcdu_sync(h):
