@@ -46,6 +46,8 @@ enum {
     QMCDU_FP32 = 1,        /* A^{-1}, panels, flush fp32; k x k inverse, ratios,  */
                            /* log-det and the recompute fp64                      */
     QMCDU_FP32_BF16X3 = 2  /* as FP32, flush on tensor cores with split-bf16 x3   */
+                           /* (tcgen05); sweeps of such a handle run as        */
+                           /* per-proposal launches around the tensor-core flush */
 };
 
 enum {
@@ -249,6 +251,22 @@ int qmcdu_sweep_shape(qmcdu_t h, int *shape5);
  */
 int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v, const double *P,
                         const double *V, const double *Kinv, double *ratio_out, void *stream);
+
+/*
+ * The tensor-core contraction of the fp32 flush (Eq. 4), exposed for direct use
+ * and testing: C = alpha * A B' + beta * C with fp32 operands split as
+ * x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and hi*hi + hi*lo + lo*hi
+ * accumulated in fp32 tensor memory by tcgen05.mma (relative error about
+ * 2^-16 of sum |a||b|, coarser than fp32 arithmetic).
+ *   A  device, M x K, A(m, k) at A[m*lda + k]
+ *   B  device, N x K with B(n, k) at B[n*ldb + k]; or, b_trans = 1, K x N with
+ *      B(n, k) at B[k*ldb + n]
+ *   C  device, M x N, C(m, n) at C[m*ldc + n]
+ * Asynchronous on `stream`. ERR_ARG for negative sizes, short leading
+ * dimensions or null pointers (text at qmcdu_last_error(NULL)).
+ */
+int qmcdu_gemm_bf16x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
+                      int b_trans, float *C, int ldc, float alpha, float beta, void *stream);
 
 /* Library version string. */
 const char *qmcdu_version(void);

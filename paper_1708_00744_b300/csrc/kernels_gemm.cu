@@ -167,9 +167,47 @@ static cudaError_t launch_flush_t(Ctx &c, int kthresh)
     return cudaGetLastError();
 }
 
+// Tensor-core flush (precision QMCDU_FP32_BF16X3): the two N x N x k
+// contractions run in split-bf16 x3 on tcgen05 (kernels_tc.cu); the small
+// W = P Kinv stays on SIMT cores.
+static cudaError_t launch_flush_tc(Ctx &c, int kthresh)
+{
+    const int N = c.N, K = c.K, ld = c.ld;
+    const long long wN = (long long)N * ld, wK = (long long)K * ld;
+    float *Ainv = (float *)c.Ainv;
+    float *Tt = (float *)c.Tbuf;     // T' stored [c][m] (N x K, row length K)
+    float *Wb = (float *)c.Wbuf;
+    // T'(c, m) = A^{-1}[:, c] . V[m] - [idx_m == c]
+    cudaError_t e = launch_gemm_bf16x3(N, K, N, Ainv, ld, wN, (const float *)c.V, ld, wK, 0, Tt, K,
+                                       wK, 1.f, 0.f, c.batch, c.kcount, 1, kthresh, c.idx, K,
+                                       c.status, c.opt_budget_ns, c.stream);
+    if (e != cudaSuccess) return e;
+    {
+        GemmArgs<double, float, float> g{};
+        g.A = c.Kinv; g.sAb = (long long)K * K; g.sAm = 1; g.sAl = K;
+        g.B = (const float *)c.P; g.sBb = wK; g.sBl = ld; g.sBn = 1;
+        g.C = Wb; g.sCb = wK; g.sCm = ld; g.sCn = 1;
+        g.M = K; g.Nn = N; g.Kd = K;
+        g.kdyn = c.kcount; g.dyn = 3; g.kthresh = kthresh;
+        g.alpha = 1.0; g.accumulate = 0;
+        dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
+        gemm_tile_kernel<double, float, float, float, 32, 32, false, true>
+            <<<grid, GTHREADS, 0, c.stream>>>(g);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // A^{-1}[:, c] -= sum_m T'(c, m) W[m]   (B operand W read as K x N)
+    e = launch_gemm_bf16x3(N, N, K, Tt, K, wK, Wb, ld, wK, 1, Ainv, ld, wN, -1.f, 1.f, c.batch,
+                           c.kcount, 0, kthresh, nullptr, 0, c.status, c.opt_budget_ns, c.stream);
+    if (e != cudaSuccess) return e;
+    flush_reset_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.kcount, kthresh);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flush(Ctx &c, int kthresh)
 {
     if (c.K <= 1) return cudaSuccess;
+    if (c.prec == QMCDU_FP32_BF16X3) return launch_flush_tc(c, kthresh);
     return c.prec == QMCDU_FP64 ? launch_flush_t<double>(c, kthresh) : launch_flush_t<float>(c, kthresh);
 }
 

@@ -197,7 +197,7 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
     if (!out) return QMCDU_ERR_ARG;
     *out = nullptr;
     if (N < 1 || N > QMCDU_MAX_N || K < 1 || K > QMCDU_MAX_K || K > N || batch < 1 ||
-        batch > 65535 || precision < QMCDU_FP64 || precision > QMCDU_FP32)
+        batch > 65535 || precision < QMCDU_FP64 || precision > QMCDU_FP32_BF16X3)
         return QMCDU_ERR_ARG;
     Ctx *c = new (std::nothrow) Ctx();
     if (!c) return QMCDU_ERR_OOM;
@@ -445,7 +445,7 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         ov = c->sw_override;
     }
     CK(cudaMemsetAsync(c->sw_ties, 0, c->batch * sizeof(long long), c->stream));
-    if (c->opt_persistent) {
+    if (c->opt_persistent && c->prec != QMCDU_FP32_BF16X3) {
         SweepLaunch S{};
         S.seed = base_seed;
         S.sweep = sweep_index;
@@ -557,6 +557,24 @@ int copy_sweep_outputs(Ctx *c, unsigned char *accepted_out, double *ratios_out,
 }  // namespace qmcdu
 
 extern "C" {
+
+int qmcdu_gemm_bf16x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
+                      int b_trans, float *C, int ldc, float alpha, float beta, void *stream)
+{
+    if (M < 0 || N < 0 || K < 0 || (M && N && (!C || (K && (!A || !B)))) || lda < K ||
+        ldb < (b_trans ? N : K) || ldc < N) {
+        set_handleless_error("qmcdu_gemm_bf16x3: invalid sizes, strides or null pointer");
+        return QMCDU_ERR_ARG;
+    }
+    cudaError_t e = launch_gemm_bf16x3(M, N, K, A, lda, 0, B, ldb, 0, b_trans, C, ldc, 0, alpha,
+                                       beta, 1, nullptr, 0, 0, nullptr, 0, nullptr, 2000000000LL,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_handleless_error(std::string("qmcdu_gemm_bf16x3: ") + cudaGetErrorString(e));
+        return QMCDU_ERR_CUDA;
+    }
+    return QMCDU_OK;
+}
 
 int qmcdu_profile_enable(qmcdu_t h, int enable)
 {

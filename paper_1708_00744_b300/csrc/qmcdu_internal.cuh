@@ -148,6 +148,13 @@ cudaError_t launch_recompute(Ctx &c, int have_old_inverse);
 cudaError_t launch_gj_update(Ctx &c, int nbe);
 int choose_panel_width(int N);
 
+// ---- tensor-core contraction (kernels_tc.cu) ----
+cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long lda, long long sA,
+                               const float *B, long long ldb, long long sB, int b_trans, float *C,
+                               long long ldc, long long sC, float alpha, float beta, int batch,
+                               const int *kdyn, int kdyn_is_n, int kthresh, const int *fix_idx,
+                               int fix_stride, int *status, long long budget_ns, cudaStream_t s);
+
 // ---- utilities (kernels_move.cu) ----
 cudaError_t launch_philox_fill(const unsigned *c0, const unsigned *c1, const unsigned *c2,
                                const unsigned *c3, int n, unsigned long long seed,

@@ -45,6 +45,8 @@ SIGNATURES = {
     "qmcdu_profile_enable": (_I, [_VP, _I]),
     "qmcdu_profile_read": (_I, [_VP, _VP, _I]),
     "qmcdu_ratio_noalloc": (_I, [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "qmcdu_gemm_bf16x3": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _I, _VP, _I, ctypes.c_float,
+                               ctypes.c_float, _VP]),
     "qmcdu_version": (ctypes.c_char_p, []),
 }
 
@@ -209,6 +211,20 @@ def qmcdu_ratio_noalloc(N, k, ainv_col, v, P, V, Kinv, ratio_out, stream=None):
                                     _ptr(ratio_out), _stream_ptr(stream))
     if st != 0:
         raise QmcduError("qmcdu_ratio_noalloc", st, load().qmcdu_last_error(None).decode())
+
+
+def qmcdu_gemm_bf16x3(A, B, C, alpha=1.0, beta=0.0, b_trans=False, stream=None):
+    """C = alpha A B' + beta C on the tensor cores (split-bf16 x3); fp32 CUDA
+    tensors, A: M x K, B: N x K (or K x N with b_trans), C: M x N, row-major."""
+    M, K = A.shape
+    N = B.shape[1] if b_trans else B.shape[0]
+    for name, x in (("A", A), ("B", B), ("C", C)):
+        _need(x, x.numel(), "float32", name, True)
+    st = load().qmcdu_gemm_bf16x3(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                  1 if b_trans else 0, _ptr(C), C.stride(0), float(alpha),
+                                  float(beta), _stream_ptr(stream))
+    if st != 0:
+        raise QmcduError("qmcdu_gemm_bf16x3", st, load().qmcdu_last_error(None).decode())
 
 
 def qmcdu_sync(h):

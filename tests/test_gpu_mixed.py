@@ -1,0 +1,57 @@
+"""Mixed precision: A^{-1}, the panels and the flush in fp32 (SIMT or
+split-bf16 x3 on the tensor cores), with the k x k inverse, ratios, log-det and
+the recompute in fp64, against the fp64 oracle on the same trajectory (the
+oracle's decisions are replayed so that both walk the same path).
+
+Stated bound: a running inverse kept in working precision u_w differs from the
+exact one by about N u_w kappa_1(A) (the forward error of a linear solve), so
+ratios (|r - r_ref| / max(1, |r_ref|)), A^{-1} (norm-wise) and log|det| must
+agree within 8 N u_w kappa_1 with u_w = 2^-24 (fp32) or 2^-16 (split bf16)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_00744_b300.qmcdu import Walkers
+
+from gpu_common import logdet_err, need_gpu, rel_norm_err, rel_ratio_err, walker_inputs
+
+pytestmark = pytest.mark.gpu
+
+U_W = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("N,K,sigma", [(128, 16, 0.1), (300, 32, 1.0), (640, 64, 0.1)])
+def test_mixed_precision_within_stated_bound(precision, N, K, sigma):
+    need_gpu()
+    batch, nsweeps, base = 2, 2, 900 + N
+    A, G, U = walker_inputs(base, batch, N, nsweeps)
+    refs = [oracle.sweeps(oracle.SM, A[b], G[b], U[b], sigma) for b in range(batch)]
+    override = np.stack([r["accepted"].astype(np.int8) for r in refs], axis=1)   # [s][b][N]
+    W = Walkers(N, K, precision, batch)
+    W.set_matrix(A)
+    acc = np.zeros((nsweeps, batch, N), dtype=np.uint8)
+    rat = np.zeros((nsweeps, batch, N))
+    for s in range(nsweeps):
+        W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s]), accepted_out=acc[s],
+                ratios_out=rat[s])
+    Ai = np.zeros((batch, N, N))
+    la = np.zeros(batch)
+    sg = np.zeros(batch, dtype=np.int32)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    drift = np.zeros((batch, 2))
+    W.recompute(drift)
+    W.close()
+    for b, ref in enumerate(refs):
+        kappa = max(np.linalg.cond(A[b], 1), np.linalg.cond(ref["A"], 1))
+        bound = 8 * N * U_W[precision] * kappa
+        errs = (rel_ratio_err(rat[:, b], ref["ratios"]), rel_norm_err(Ai[b], ref["Ainv"]),
+                logdet_err(la[b], ref["logabs"]))
+        flips = int(np.sum(np.abs(np.minimum(1, ref["ratios"] ** 2) - U[b]) < 2 * errs[0]))
+        print("%s N=%d K=%d sigma=%g walker %d: bound %.1e ratio %.1e inverse %.1e logdet %.1e "
+              "drift %.1e/%.1e decisions within error of a tie %d"
+              % ((precision, N, K, sigma, b, bound) + errs + tuple(drift[b]) + (flips,)))
+        assert np.array_equal(acc[:, b].astype(bool), ref["accepted"])
+        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
+        assert sg[b] == ref["sign"]
