@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct qmcdu_ctx *qmcdu_t;
+typedef struct qmcdu_group_ctx *qmcdu_group_t;
 
 /* Working precision of A^{-1}, the panels and the flush. */
 enum {
@@ -156,6 +157,45 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
                 const signed char *override, unsigned char *accepted_out,
                 double *ratios_out, long long *near_ties_out);
 
+/*
+ * A step of the benchmark's and the paper's measurement protocol (Sec. III:
+ * complete sweeps, then the determinant checked against direct calculation):
+ * `nsweeps` sweeps numbered first_sweep.. (as qmcdu_sweep, no override), then,
+ * if `recompute`, the fp64 recompute (qmcdu_recompute). With use_graph = 1 the
+ * kernels of the step are captured into a CUDA graph on first use and replayed
+ * by later calls with the same (nsweeps, recompute, sigma); the seed and first
+ * sweep index are read from device memory, so they may change between calls.
+ * Graph capture needs a handle on a non-default stream (ERR_ARG otherwise).
+ *   accepted_out  host or device [nsweeps][batch][N] uint8, or NULL
+ *   drift_out     host or device [batch][2] (as qmcdu_recompute), or NULL
+ * Handles of precision QMCDU_FP32_BF16X3, or with persistent sweeps switched
+ * off, run the sweeps call by call without a graph.
+ */
+int qmcdu_step(qmcdu_t h, unsigned long long base_seed, int first_sweep, int nsweeps, double sigma,
+               int recompute, int use_graph, unsigned char *accepted_out, double *drift_out);
+
+/* Results of the last qmcdu_step / qmcdu_group_step of this handle for its
+ * first `nsweeps` sweeps (host or device buffers, each may be NULL): accept
+ * masks [nsweeps][batch][N] uint8, ratios [nsweeps][batch][N] fp64, near-tie
+ * counts [nsweeps][batch] int64. Synchronises. */
+int qmcdu_step_results(qmcdu_t h, int nsweeps, unsigned char *accepted_out, double *ratios_out,
+                       long long *near_ties_out);
+
+/*
+ * Walkers of uneven N: one handle per size class, stepped together. The group
+ * gives each handle a share of the SMs in proportion to its flush work
+ * (batch N^3; QMCDU_OPT_MAX_CTAS) so that the classes' persistent sweeps run
+ * side by side, forks every handle's stream from the first handle's stream
+ * and joins them back, and (use_graph) captures the whole fork/join step in
+ * one CUDA graph. seeds[i] is handle i's base seed. Handles of precision
+ * QMCDU_FP32_BF16X3 or without persistent sweeps are refused (ERR_ARG). The
+ * group does not own the handles; destroy it before them.
+ */
+int qmcdu_group_create(qmcdu_t *handles, int n, qmcdu_group_t *out);
+int qmcdu_group_step(qmcdu_group_t g, const unsigned long long *seeds, int first_sweep,
+                     int nsweeps, double sigma, int recompute, int use_graph);
+int qmcdu_group_destroy(qmcdu_group_t g);
+
 /* Wait for the handle's stream and return the latched device status. */
 int qmcdu_sync(qmcdu_t h);
 
@@ -201,6 +241,8 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       on expiry the call fails with ERR_TIMEOUT at the next sync
  *   QMCDU_OPT_TEST_STALL   [0] test hook: the next persistent sweep waits for
  *       one arrival that never comes, so that its wait runs out of budget
+ *   QMCDU_OPT_MAX_CTAS     [whole GPU] cap on the persistent sweep's grid, so
+ *       that several handles' sweeps can run side by side (qmcdu_group_*)
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {
@@ -208,7 +250,8 @@ enum {
     QMCDU_OPT_RATIO_CTAS = 2,
     QMCDU_OPT_FLUSH_CTAS = 3,
     QMCDU_OPT_WAIT_BUDGET_NS = 4,
-    QMCDU_OPT_TEST_STALL = 5
+    QMCDU_OPT_TEST_STALL = 5,
+    QMCDU_OPT_MAX_CTAS = 6
 };
 int qmcdu_set_option(qmcdu_t h, int option, long long value);
 

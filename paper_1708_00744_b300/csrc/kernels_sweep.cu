@@ -599,8 +599,13 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
 // Gaussians (Box-Muller pairs) and Metropolis uniforms of one sweep for every
 // walker, from the Philox counters of qmcdu_sweep.
 __global__ void sweep_draw_kernel(int N, int ld, int batch, unsigned long long seed, int sweep,
+                                  const unsigned long long *params, int sweep_offset,
                                   double *gauss, double *unif)
 {
+    if (params) {   // parameters in device memory (steps replayed from a CUDA graph)
+        seed = params[0];
+        sweep = (int)params[1] + sweep_offset;
+    }
     const int npair = (N + 1) / 2;
     const long long per_w = (long long)N * npair;
     const long long total = per_w * batch;
@@ -691,7 +696,8 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES>, STHREADS, smem);
     if (e != cudaSuccess) return e;
-    const int capacity = per_sm * c.num_sms;
+    int capacity = per_sm * c.num_sms;
+    if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
     if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
     const int ngroups = std::min(c.batch, std::max(1, capacity / Gf));
     if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
@@ -729,10 +735,11 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
 {
     const int N = c.N, K = c.K;
     int Gf, Gr;
-    if (c.batch >= c.num_sms) {
+    const int sms = c.opt_max_ctas > 0 ? std::min(c.num_sms, c.opt_max_ctas) : c.num_sms;
+    if (c.batch >= sms) {
         Gf = Gr = 1;
     } else {
-        Gf = std::max(1, c.num_sms / c.batch);
+        Gf = std::max(1, sms / c.batch);
         const int target_chunk = c.prec == QMCDU_FP64 ? 32 : 128;
         Gr = c.opt_ratio_ctas > 0 ? c.opt_ratio_ctas : (N + target_chunk - 1) / target_chunk;
         Gr = std::max(1, std::min(Gr, Gf));
@@ -750,7 +757,8 @@ cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)
 {
     // the sweep's proposal draws, then the sweep, then the running log-det
     sweep_draw_kernel<<<c.num_sms * 8, 256, 0, c.stream>>>(c.N, c.ld, c.batch, L.seed, L.sweep,
-                                                           c.sw_gauss, c.sw_unif);
+                                                           L.params, L.sweep_offset, c.sw_gauss,
+                                                           c.sw_unif);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = prof_begin(&c, c.ev_sweep);

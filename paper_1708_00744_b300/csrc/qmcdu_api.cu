@@ -60,6 +60,10 @@ static void release(Ctx *c)
                     c->sw_unif};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties};
+    for (void *p : more)
+        if (p) cudaFree(p);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
 }
 
 static bool is_device_ptr(const void *p)
@@ -254,6 +258,7 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
         AL(c->sw_phase, 8 * sizeof(unsigned long long));
         AL(c->sw_gauss, B * NN * sizeof(double));
         AL(c->sw_unif, B * N * sizeof(double));
+        AL(c->d_params, 2 * sizeof(unsigned long long));
     }
 #undef AL
     if (e != cudaSuccess) {
@@ -506,6 +511,314 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
     return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out);
 }
 
+}  // extern "C"
+
+namespace qmcdu {
+
+// Step buffers for `nsweeps` sweeps (outside any capture).
+static int ensure_step_buffers(Ctx *c, int nsweeps)
+{
+    if (nsweeps <= c->step_cap) return QMCDU_OK;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->step_acc);
+    cudaFree(c->step_ratio);
+    cudaFree(c->step_ties);
+    c->step_acc = nullptr; c->step_ratio = nullptr; c->step_ties = nullptr;
+    c->step_cap = 0;
+    const size_t BN = (size_t)c->batch * c->N;
+    CK(dalloc(&c->step_acc, (size_t)nsweeps * BN));
+    CK(dalloc(&c->step_ratio, (size_t)nsweeps * BN * sizeof(double)));
+    CK(dalloc(&c->step_ties, (size_t)nsweeps * c->batch * sizeof(long long)));
+    c->step_cap = nsweeps;
+    return QMCDU_OK;
+}
+
+// The kernels of one step on the handle's stream: nsweeps persistent sweeps
+// (proposal draws read their seed and sweep index from c->d_params), then the
+// recompute. No host synchronisation, so the sequence can be captured.
+static int enqueue_step(Ctx *c, int nsweeps, double sigma, int recompute)
+{
+    const size_t BN = (size_t)c->batch * c->N;
+    for (int i = 0; i < nsweeps; ++i) {
+        CK(cudaMemsetAsync(c->step_ties + (size_t)i * c->batch, 0, c->batch * sizeof(long long),
+                           c->stream));
+        SweepLaunch S{};
+        S.params = c->d_params;
+        S.sweep_offset = i;
+        S.sigma = sigma;
+        S.acc_out = c->step_acc + i * BN;
+        S.ratio_out = c->step_ratio + i * BN;
+        S.ties = c->step_ties + (size_t)i * c->batch;
+        CK(launch_sweep(*c, S));
+        CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
+        c->n_launch += 3;
+    }
+    if (recompute) return do_recompute(c, 1);
+    return QMCDU_OK;
+}
+
+static bool step_graph_ready(const Ctx *c, int nsweeps, int recompute, double sigma)
+{
+    return c->graph_exec && c->graph_key[0] == nsweeps && c->graph_key[1] == recompute &&
+           c->graph_sigma == sigma;
+}
+
+static int capture_step(Ctx *c, int nsweeps, double sigma, int recompute)
+{
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    const bool prof = c->prof;
+    c->prof = false;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    const long long launches = c->n_launch;
+    int st = enqueue_step(c, nsweeps, sigma, recompute);
+    c->n_launch = launches;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->prof = prof;
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_key[0] = nsweeps;
+    c->graph_key[1] = recompute;
+    c->graph_sigma = sigma;
+    return QMCDU_OK;
+}
+
+static int step_outputs(Ctx *c, int nsweeps, unsigned char *accepted_out, double *drift_out,
+                        int recompute)
+{
+    bool host_out = false;
+    if (accepted_out) {
+        CK(cudaMemcpyAsync(accepted_out, c->step_acc, (size_t)nsweeps * c->batch * c->N,
+                           cudaMemcpyDefault, c->stream));
+        host_out |= !is_device_ptr(accepted_out);
+    }
+    if (drift_out && recompute) {
+        CK(cudaMemcpy2DAsync(drift_out, 2 * sizeof(double), c->drift + 2, 4 * sizeof(double),
+                             2 * sizeof(double), c->batch, cudaMemcpyDefault, c->stream));
+        host_out |= !is_device_ptr(drift_out);
+    }
+    return host_out ? read_status(c) : QMCDU_OK;
+}
+
+struct GroupCtx {
+    std::vector<Ctx *> hs;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int key[2] = {-1, -1};
+    double sigma = 0.0;
+    std::string err;
+};
+
+// The fork/join body of a group step on the first handle's stream.
+static int group_body(GroupCtx *g, int nsweeps, double sigma, int recompute)
+{
+    Ctx *c0 = g->hs[0];
+    cudaStream_t s0 = c0->stream;
+    if (cudaError_t e = cudaEventRecord(g->fork, s0)) return cuda_fail(c0, e, "cudaEventRecord");
+    for (size_t i = 0; i < g->hs.size(); ++i) {
+        Ctx *c = g->hs[i];
+        CK(cudaStreamWaitEvent(c->stream, g->fork, 0));
+        int st = enqueue_step(c, nsweeps, sigma, recompute);
+        if (st) return st;
+        CK(cudaEventRecord(g->done[i], c->stream));
+        CK(cudaStreamWaitEvent(s0, g->done[i], 0));
+    }
+    return QMCDU_OK;
+}
+
+}  // namespace qmcdu
+
+extern "C" {
+
+int qmcdu_step(qmcdu_t h, unsigned long long base_seed, int first_sweep, int nsweeps, double sigma,
+               int recompute, int use_graph, unsigned char *accepted_out, double *drift_out)
+{
+    if (!h || first_sweep < 0 || nsweeps < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    const size_t BN = (size_t)c->batch * c->N;
+    if (!c->opt_persistent || c->prec == QMCDU_FP32_BF16X3) {
+        // per-proposal launches: run the sweeps one call at a time (no graph)
+        for (int i = 0; i < nsweeps; ++i) {
+            st = qmcdu_sweep(h, base_seed, first_sweep + i, sigma, nullptr,
+                             accepted_out ? accepted_out + i * BN : nullptr, nullptr, nullptr);
+            if (st) return st;
+        }
+        if (recompute) return qmcdu_recompute(h, drift_out);
+        return QMCDU_OK;
+    }
+    if (use_graph && c->stream == nullptr)
+        return fail(c, QMCDU_ERR_ARG, "graph capture needs a handle on a non-default stream%s");
+    st = ensure_step_buffers(c, nsweeps);
+    if (st) return st;
+    const unsigned long long hp[2] = {base_seed, (unsigned long long)first_sweep};
+    CK(cudaMemcpyAsync(c->d_params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream));
+    if (use_graph && step_graph_ready(c, nsweeps, recompute, sigma)) {
+        CK(cudaGraphLaunch(c->graph_exec, c->stream));
+        c->n_launch += 3 * nsweeps + (recompute ? 5 + 2 * ((c->N + c->nb - 1) / c->nb) : 0);
+    } else {
+        st = enqueue_step(c, nsweeps, sigma, recompute);
+        if (st) return st;
+        if (use_graph) {
+            st = capture_step(c, nsweeps, sigma, recompute);
+            if (st) return st;
+        }
+    }
+    return step_outputs(c, nsweeps, accepted_out, drift_out, recompute);
+}
+
+int qmcdu_step_results(qmcdu_t h, int nsweeps, unsigned char *accepted_out, double *ratios_out,
+                       long long *near_ties_out)
+{
+    if (!h || nsweeps < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (nsweeps > c->step_cap) return fail(c, QMCDU_ERR_STATE, "no step of that many sweeps%s");
+    const size_t BN = (size_t)c->batch * c->N;
+    if (accepted_out)
+        CK(cudaMemcpyAsync(accepted_out, c->step_acc, nsweeps * BN, cudaMemcpyDefault, c->stream));
+    if (ratios_out)
+        CK(cudaMemcpyAsync(ratios_out, c->step_ratio, nsweeps * BN * sizeof(double), cudaMemcpyDefault,
+                           c->stream));
+    if (near_ties_out)
+        CK(cudaMemcpyAsync(near_ties_out, c->step_ties, (size_t)nsweeps * c->batch * sizeof(long long),
+                           cudaMemcpyDefault, c->stream));
+    return read_status(c);
+}
+
+int qmcdu_group_create(qmcdu_t *hs, int n, qmcdu_group_t *out)
+{
+    if (!hs || n < 1 || !out) return QMCDU_ERR_ARG;
+    *out = nullptr;
+    GroupCtx *g = new (std::nothrow) GroupCtx();
+    if (!g) return QMCDU_ERR_OOM;
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) { delete g; return QMCDU_ERR_ARG; }
+        Ctx *c = reinterpret_cast<Ctx *>(hs[i]);
+        if (c->prec == QMCDU_FP32_BF16X3 || !c->opt_persistent) { delete g; return QMCDU_ERR_ARG; }
+        g->hs.push_back(c);
+        total += (double)c->batch * c->N * c->N * c->N;
+    }
+    // share of the SMs per size class, in proportion to its flush work (batch N^3)
+    const int sms = g->hs[0]->num_sms;
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        Ctx *c = g->hs[i];
+        int share = (int)((double)sms * c->batch * c->N * c->N * (double)c->N / total);
+        share = std::max(1, std::min(share, sms - (n - 1 - i) - used));
+        if (i == n - 1) share = std::max(1, sms - used);
+        used += share;
+        c->opt_max_ctas = 2 * share;   // at most two sweep CTAs fit on one SM
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+    g->done.assign(n, nullptr);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&g->done[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (g->fork) cudaEventDestroy(g->fork);
+        for (auto ev : g->done)
+            if (ev) cudaEventDestroy(ev);
+        delete g;
+        return QMCDU_ERR_CUDA;
+    }
+    *out = reinterpret_cast<qmcdu_group_t>(g);
+    return QMCDU_OK;
+}
+
+int qmcdu_group_step(qmcdu_group_t gh, const unsigned long long *seeds, int first_sweep, int nsweeps,
+                     double sigma, int recompute, int use_graph)
+{
+    if (!gh || !seeds || first_sweep < 0 || nsweeps < 0) return QMCDU_ERR_ARG;
+    GroupCtx *g = reinterpret_cast<GroupCtx *>(gh);
+    Ctx *c0 = g->hs[0];
+    if (use_graph && c0->stream == nullptr)
+        return fail(c0, QMCDU_ERR_ARG, "graph capture needs a non-default stream%s");
+    bool rebuilt = false;
+    for (size_t i = 0; i < g->hs.size(); ++i) {
+        Ctx *c = g->hs[i];
+        int st = flush_all(c);
+        if (st) return st;
+        c->pending = false;
+        const int had = c->step_cap;
+        st = ensure_step_buffers(c, nsweeps);
+        if (st) return st;
+        rebuilt |= c->step_cap != had;
+        // every parameter block is written on the first handle's stream, ahead of the fork
+        const unsigned long long hp[2] = {seeds[i], (unsigned long long)first_sweep};
+        CK(cudaMemcpyAsync(c->d_params, hp, sizeof hp, cudaMemcpyHostToDevice, c0->stream));
+    }
+    Ctx *c = c0;   // error reports of the group go to its first handle
+    if (rebuilt && g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    if (use_graph && g->exec && g->key[0] == nsweeps && g->key[1] == recompute && g->sigma == sigma) {
+        CK(cudaGraphLaunch(g->exec, c0->stream));
+        return QMCDU_OK;
+    }
+    int st = group_body(g, nsweeps, sigma, recompute);
+    if (st) return st;
+    if (!use_graph) return QMCDU_OK;
+    if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    std::vector<bool> prof(g->hs.size());
+    for (size_t i = 0; i < g->hs.size(); ++i) { prof[i] = g->hs[i]->prof; g->hs[i]->prof = false; }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeRelaxed));
+    st = group_body(g, nsweeps, sigma, recompute);
+    cudaError_t e = cudaStreamEndCapture(c0->stream, &graph);
+    for (size_t i = 0; i < g->hs.size(); ++i) g->hs[i]->prof = prof[i];
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c0, e, "cudaStreamEndCapture (group)");
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return cuda_fail(c0, e, "cudaGraphInstantiate (group)");
+    }
+    g->key[0] = nsweeps;
+    g->key[1] = recompute;
+    g->sigma = sigma;
+    return QMCDU_OK;
+}
+
+int qmcdu_group_destroy(qmcdu_group_t gh)
+{
+    if (!gh) return QMCDU_ERR_ARG;
+    GroupCtx *g = reinterpret_cast<GroupCtx *>(gh);
+    for (Ctx *c : g->hs) cudaStreamSynchronize(c->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->fork) cudaEventDestroy(g->fork);
+    for (auto ev : g->done)
+        if (ev) cudaEventDestroy(ev);
+    delete g;
+    return QMCDU_OK;
+}
+
 int qmcdu_set_option(qmcdu_t h, int option, long long value)
 {
     if (!h || value < 0) return QMCDU_ERR_ARG;
@@ -516,6 +829,7 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value)
     case QMCDU_OPT_FLUSH_CTAS: c->opt_flush_ctas = (int)std::min(value, 1LL << 20); break;
     case QMCDU_OPT_WAIT_BUDGET_NS: c->opt_budget_ns = value ? value : 2000000000LL; break;
     case QMCDU_OPT_TEST_STALL: c->opt_stall = value ? 1 : 0; break;
+    case QMCDU_OPT_MAX_CTAS: c->opt_max_ctas = (int)std::min(value, 1LL << 20); break;
     default: return fail(c, QMCDU_ERR_ARG, "unknown option%s");
     }
     return QMCDU_OK;

@@ -94,11 +94,23 @@ struct Ctx {
     int opt_flush_ctas = 0;
     long long opt_budget_ns = 2000000000LL;
     int opt_stall = 0;
+    int opt_max_ctas = 0;            // cap on the persistent sweep's grid (0: whole GPU)
+    // qmcdu_step: device parameter block and per-sweep outputs, graph cache
+    unsigned long long *d_params = nullptr;   // [0] base seed, [1] first sweep index
+    unsigned char *step_acc = nullptr;        // nsweeps x batch x N
+    double *step_ratio = nullptr;             // nsweeps x batch x N
+    long long *step_ties = nullptr;           // nsweeps x batch
+    int step_cap = 0;                         // sweeps the step buffers hold
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_key[3] = {-1, -1, -1};          // nsweeps, recompute, sigma bits (hashed)
+    double graph_sigma = 0.0;
 };
 
 struct SweepLaunch {
     unsigned long long seed;
     int sweep;
+    const unsigned long long *params;   // device [seed, first sweep] (then seed/sweep unused)
+    int sweep_offset;                   // added to params[1]
     double sigma;
     const signed char *override;
     unsigned char *acc_out;

@@ -38,6 +38,11 @@ SIGNATURES = {
     "qmcdu_logdet": (_I, [_VP, _VP, _VP]),
     "qmcdu_sweep": (_I, [_VP, _ULL, _I, _D, _VP, _VP, _VP, _VP]),
     "qmcdu_sync": (_I, [_VP]),
+    "qmcdu_step": (_I, [_VP, _ULL, _I, _I, _D, _I, _I, _VP, _VP]),
+    "qmcdu_step_results": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "qmcdu_group_create": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
+    "qmcdu_group_step": (_I, [_VP, _VP, _I, _I, _D, _I, _I]),
+    "qmcdu_group_destroy": (_I, [_VP]),
     "qmcdu_last_error": (ctypes.c_char_p, [_VP]),
     "qmcdu_philox4x32_10": (_I, [_VP, _VP, _VP, _VP, _I, _ULL, _VP, _VP]),
     "qmcdu_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
@@ -227,6 +232,42 @@ def qmcdu_gemm_bf16x3(A, B, C, alpha=1.0, beta=0.0, b_trans=False, stream=None):
         raise QmcduError("qmcdu_gemm_bf16x3", st, load().qmcdu_last_error(None).decode())
 
 
+def qmcdu_step(h, base_seed, first_sweep, nsweeps, sigma, N, batch, recompute=True,
+               use_graph=False, accepted_out=None, drift_out=None):
+    _need(accepted_out, nsweeps * batch * N, "uint8", "accepted_out", False)
+    _need(drift_out, 2 * batch, "float64", "drift_out", False)
+    _check("qmcdu_step", load().qmcdu_step(h, base_seed, first_sweep, nsweeps, sigma,
+                                           1 if recompute else 0, 1 if use_graph else 0,
+                                           _ptr(accepted_out), _ptr(drift_out)), h)
+
+
+def qmcdu_step_results(h, nsweeps, N, batch, accepted_out=None, ratios_out=None,
+                       near_ties_out=None):
+    _need(accepted_out, nsweeps * batch * N, "uint8", "accepted_out", False)
+    _need(ratios_out, nsweeps * batch * N, "float64", "ratios_out", False)
+    _need(near_ties_out, nsweeps * batch, "int64", "near_ties_out", False)
+    _check("qmcdu_step_results", load().qmcdu_step_results(h, nsweeps, _ptr(accepted_out),
+                                                           _ptr(ratios_out), _ptr(near_ties_out)), h)
+
+
+def qmcdu_group_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    g = ctypes.c_void_p()
+    _check("qmcdu_group_create", load().qmcdu_group_create(arr, len(handles), ctypes.byref(g)))
+    return g.value
+
+
+def qmcdu_group_step(g, seeds, first_sweep, nsweeps, sigma, recompute=True, use_graph=False):
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check("qmcdu_group_step", load().qmcdu_group_step(g, _ptr(seeds), first_sweep, nsweeps, sigma,
+                                                       1 if recompute else 0,
+                                                       1 if use_graph else 0))
+
+
+def qmcdu_group_destroy(g):
+    _check("qmcdu_group_destroy", load().qmcdu_group_destroy(g))
+
+
 def qmcdu_sync(h):
     _check("qmcdu_sync", load().qmcdu_sync(h), h)
 
@@ -245,7 +286,7 @@ def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
 
 
 OPTIONS = {"sweep_persistent": 1, "ratio_ctas": 2, "flush_ctas": 3, "wait_budget_ns": 4,
-           "test_stall": 5}
+           "test_stall": 5, "max_ctas": 6}
 
 
 def qmcdu_set_option(h, option, value):
@@ -336,6 +377,15 @@ class Walkers:
 
     def sync(self):
         qmcdu_sync(self.h)
+
+    def step(self, base_seed, first_sweep, nsweeps, sigma, recompute=True, use_graph=False,
+             accepted_out=None, drift_out=None):
+        qmcdu_step(self.h, base_seed, first_sweep, nsweeps, sigma, self.N, self.batch, recompute,
+                   use_graph, accepted_out, drift_out)
+
+    def step_results(self, nsweeps, accepted_out=None, ratios_out=None, near_ties_out=None):
+        qmcdu_step_results(self.h, nsweeps, self.N, self.batch, accepted_out, ratios_out,
+                           near_ties_out)
 
     def set_option(self, option, value):
         qmcdu_set_option(self.h, option, value)
