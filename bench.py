@@ -4,12 +4,20 @@
 Metric: accepted-move updates per second (the paper's Monte Carlo column
 updates per second over complete sweeps, Sec. III), whole job.
 
-Workload (default): one walker of N = 2048 electrons in fp64, A_ij ~ N(0,1),
-proposal v = a_j + 0.1 g (DMC-like acceptance), delay K = 64. A step is ten
-full Metropolis sweeps followed by the fp64 recompute of A^{-1} and log|det A|
-(the recompute every ten sweeps of the workload). Inputs are synthetic
-(seeded Philox draws). The same workload also runs with K = 1
-(Sherman-Morrison on the same GPU) for the speedup.
+Workloads (--workload):
+  single  (default) one walker of N = 2048 electrons in fp64, A_ij ~ N(0,1),
+          proposal v = a_j + 0.1 g (DMC-like acceptance), K tuned by the
+          autotuner (untimed, before the measurement). A step is ten full
+          Metropolis sweeps followed by the fp64 recompute of A^{-1} and
+          log|det A| (qmcdu_step). The same walker with K = 1
+          (Sherman-Morrison) on the same GPU gives the speedup.
+  uneven  256 walkers of N = 512 and 64 of N = 1536, fp64, sigma = 0.1, K = 64,
+          both size classes stepped together (qmcdu_group_step); a step is one
+          sweep of every walker.
+  mixed   64 walkers of N = 2048 and 8 of N = 4096 with A^{-1}, panels and the
+          flush in fp32 (k x k algebra, ratios, log-det in fp64), sigma = 0.1,
+          K = 64; a step is one sweep of every walker.
+Inputs are synthetic (seeded Philox draws). L2 is flushed between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,9 +46,16 @@ FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.203
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 77.0
 HBM_PEAK_FALLBACK_GBS = 6400.0
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the flush kernels,
-# from one ncu capture; keyed by the sha256 of kernels_gemm.cu at capture time.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the sweep kernel,
+# from one ncu capture; keyed by the sha256 of kernels_sweep.cu at capture time
+# and the workload.
 NCU_TRAFFIC = {}
+
+WORKLOADS = {
+    "single": [dict(N=2048, batch=1)],
+    "uneven": [dict(N=512, batch=256), dict(N=1536, batch=64)],
+    "mixed": [dict(N=2048, batch=64), dict(N=4096, batch=8)],
+}
 
 
 def parse():
@@ -49,33 +64,45 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--N", type=int, default=2048)
-    p.add_argument("--K", type=int, default=64)
-    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--workload", default="single", choices=sorted(WORKLOADS))
+    p.add_argument("--N", type=int, default=None, help="override N (single workload)")
+    p.add_argument("--K", default="auto", help="delay K, or 'auto' (autotuner)")
     p.add_argument("--sigma", type=float, default=0.1)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    p.add_argument("--sweeps-per-step", type=int, default=10)
+    p.add_argument("--precision", default=None, choices=["fp64", "fp32", "bf16x3"])
+    p.add_argument("--sweeps-per-step", type=int, default=None)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--k1-steps", type=int, default=1, help="steps of the K=1 comparison")
     p.add_argument("--cpu-moves", type=int, default=-1,
                    help="proposals in the CPU-oracle sample (default: sized for ~15 s)")
-    return p.parse_args()
+    a = p.parse_args()
+    a.classes = [dict(c) for c in WORKLOADS[a.workload]]
+    if a.N is not None and a.workload == "single":
+        a.classes[0]["N"] = a.N
+    if a.precision is None:
+        a.precision = "fp32" if a.workload == "mixed" else "fp64"
+    if a.sweeps_per_step is None:
+        a.sweeps_per_step = 10 if a.workload == "single" else 1
+    a.N = a.classes[0]["N"]
+    return a
 
 
 def workload_name(a):
-    return ("%d walker(s) x N=%d %s, K=%d, sigma=%g, %d sweeps + fp64 recompute per step"
-            % (a.batch, a.N, a.precision, a.K, a.sigma, a.sweeps_per_step))
+    cls = " + ".join("%d x N=%d" % (c["batch"], c["N"]) for c in a.classes)
+    rec = " + fp64 recompute" if a.workload == "single" else ""
+    return "%s walkers, %s, K=%s, sigma=%g, %d sweep(s)%s per step" % (
+        cls, a.precision, a.K, a.sigma, a.sweeps_per_step, rec)
 
 
 def config(a, world):
-    return {"workload": workload_name(a), "N": a.N, "K": a.K, "walkers_per_gpu": a.batch,
-            "walkers": a.batch * world, "precision": a.precision, "sigma": a.sigma,
-            "sweeps_per_step": a.sweeps_per_step, "recompute_every_sweeps": a.sweeps_per_step,
+    return {"workload": workload_name(a), "name": a.workload,
+            "classes": [dict(c, K=c.get("K", a.K)) for c in a.classes],
+            "precision": a.precision, "sigma": a.sigma, "sweeps_per_step": a.sweeps_per_step,
+            "recompute_every_sweeps": a.sweeps_per_step if a.workload == "single" else None,
             "l2": "flushed between timed steps (256 MB write)", "parallelism": "walkers x %d" % world}
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_sample(a, max_moves):
+def cpu_oracle_sample(a, max_moves, K):
     """The fp64 CPU oracle (delayed look-ahead + Woodbury with the same K; K = 1:
     Sherman-Morrison) on the first `max_moves` proposals of sweep 0 of one
     walker. The oracle's setup (an O(N^3) LU inverse of the starting matrix) is
@@ -86,23 +113,23 @@ def cpu_oracle_sample(a, max_moves):
     A = inputs.initial_matrix(a.seed, a.N)
     G = inputs.proposal_gaussians(a.seed, 0, a.N)[None]
     U = inputs.metropolis_uniforms(a.seed, 0, a.N)[None]
-    method = oracle.SM if a.K == 1 else oracle.DELAYED
+    method = oracle.SM if K == 1 else oracle.DELAYED
     oracle.build()
     t0 = time.perf_counter()
-    oracle.sweeps(method, A, G, U, a.sigma, K=a.K, max_moves=0)
+    oracle.sweeps(method, A, G, U, a.sigma, K=K, max_moves=0)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    out = oracle.sweeps(method, A, G, U, a.sigma, K=a.K, max_moves=max_moves)
+    out = oracle.sweeps(method, A, G, U, a.sigma, K=K, max_moves=max_moves)
     dt = time.perf_counter() - t0 - t_setup
     acc = int(out["accepted"][0, :max_moves].sum())
     return acc, max(dt, 1e-9), t_setup
 
 
-def cpu_sample_size(a, seconds=15.0):
+def cpu_sample_size(a, K, seconds=15.0):
     if a.cpu_moves > 0:
         return min(a.cpu_moves, a.N)
-    # about 2 N^2 K flop-equivalents per K accepted proposals at ~1 GFLOP/s
-    per_move = 4.0 * a.N * a.N / 1.0e9 + 2.0 * a.N * (2 * a.K + 1) / 1.0e9
+    # about 4 N^2 flops per accepted move at ~1 GFLOP/s, plus the look-ahead
+    per_move = 4.0 * a.N * a.N / 1.0e9 + 2.0 * a.N * (2 * K + 1) / 1.0e9
     return int(max(16, min(a.N, seconds / per_move)))
 
 
@@ -176,93 +203,146 @@ def source_hash(name):
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a, rank, world, local_rank):
     import torch
-    from paper_1708_00744_b300 import inputs
-    from paper_1708_00744_b300.qmcdu import Walkers
+    from paper_1708_00744_b300 import autotune, inputs
+    from paper_1708_00744_b300.qmcdu import Walkers, qmcdu_group_create, qmcdu_group_destroy, \
+        qmcdu_group_step
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
     dist = None
     if world > 1:
         import torch.distributed as dist
-    N, B, nsw = a.N, a.batch, a.sweeps_per_step
-    base = a.seed + rank * B
-    A0 = np.stack([inputs.initial_matrix(inputs.walker_seed(base, b), N) for b in range(B)])
-    A0_pinned = torch.from_numpy(A0).pin_memory()
+    nsw = a.sweeps_per_step
+    recompute = a.workload == "single"
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    acc_dev = torch.zeros(nsw, B, N, dtype=torch.uint8, device=dev)
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    def time_steps(W, K, nsteps, nwarm, sweep0, profile=False):
-        """Device-timed steps on resident state; returns (ms list, accepted, profile)."""
+    # ---- K (and the ratio-CTA count) from the autotuner, untimed
+    tuned = None
+    for c in a.classes:
+        if a.K == "auto" and a.workload == "single":
+            t = autotune.tune(c["N"], batch=c["batch"], precision=a.precision, sigma=a.sigma,
+                              sweeps=1, seed=a.seed + 12345)
+            c["K"], c["ratio_ctas"] = t["K"], t["ratio_ctas"]
+            tuned = {"K": t["K"], "ratio_ctas": t["ratio_ctas"],
+                     "candidates": [{k: r[k] for k in ("K", "ratio_ctas", "ms_per_sweep")}
+                                    for r in t["candidates"]]}
+        else:
+            c["K"] = 64 if a.K == "auto" else int(a.K)
+            c.setdefault("ratio_ctas", 0)
+    barrier()
+
+    # ---- handles: one per size class, each on its own stream
+    hs = []
+    for i, c in enumerate(a.classes):
+        st = torch.cuda.Stream()
+        base = a.seed + 100000 * i + rank * c["batch"]
+        A0 = torch.from_numpy(np.stack([inputs.initial_matrix(inputs.walker_seed(base, b), c["N"])
+                                        for b in range(c["batch"])])).pin_memory()
+        W = Walkers(c["N"], c["K"], a.precision, c["batch"], stream=st)
+        W.set_option("ratio_ctas", c.get("ratio_ctas", 0))
+        W.set_matrix(A0)
+        hs.append(dict(W=W, stream=st, base=base, A0=A0, cls=c))
+    s0 = hs[0]["stream"]
+    group = qmcdu_group_create([h["W"].h for h in hs]) if len(hs) > 1 else None
+    nprop = sum(c["N"] * c["batch"] for c in a.classes) * nsw
+
+    def step(handles, sweep0, use_graph):
+        if len(handles) == 1 or group is None:
+            for h in handles:
+                h["W"].step(h["base"], sweep0, nsw, a.sigma, recompute=recompute,
+                            use_graph=use_graph)
+        else:
+            qmcdu_group_step(group, [h["base"] for h in handles], sweep0, nsw, a.sigma, recompute,
+                             use_graph)
+
+    def accepted_in_step(handles):
+        tot = 0
+        for h in handles:
+            c = h["cls"]
+            acc = np.zeros((nsw, c["batch"], c["N"]), dtype=np.uint8)
+            h["W"].step_results(nsw, acc)
+            tot += int(acc.sum())
+        return tot
+
+    def timed(handles, nsteps, nwarm, sweep0, use_graph, profile=False):
+        stream = handles[0]["stream"]
         sweep = sweep0
         for _ in range(nwarm):
-            for s in range(nsw):
-                W.sweep(base, sweep, a.sigma)
-                sweep += 1
-            W.recompute()
+            step(handles, sweep, use_graph)
+            sweep += nsw
         barrier()
         if profile:
-            W.profile_enable(True)
+            for h in handles:
+                h["W"].profile_enable(True)
         ms, accepted = [], 0
         for _ in range(nsteps):
             flush_buf.zero_()
+            torch.cuda.synchronize()
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            for s in range(nsw):
-                W.sweep(base, sweep, a.sigma, accepted_out=acc_dev[s])
-                sweep += 1
-            W.recompute()
+            step(handles, sweep, use_graph)
+            sweep += nsw
             ev1.record(stream)
             ev1.synchronize()
             ms.append(ev0.elapsed_time(ev1))
-            accepted += int(acc_dev.sum().item())
-        prof = W.profile_read() if profile else None
+            accepted += accepted_in_step(handles)
+        prof = [h["W"].profile_read() for h in handles] if profile else None
         if profile:
-            W.profile_enable(False)
+            for h in handles:
+                h["W"].profile_enable(False)
         return ms, accepted, prof, sweep
 
-    W = Walkers(N, a.K, a.precision, B, stream=stream)
-    W.set_matrix(A0_pinned)
-    barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ms, accepted, prof, sweep_next = time_steps(W, a.K, a.steps, a.warmup, 0, profile=True)
+    ms, accepted, prof, sweep_next = timed(hs, a.steps, a.warmup, 0, use_graph=False, profile=True)
     clk = clocks.stop()
+    # the same steps replayed from the captured CUDA graph
+    msg, accg, _, sweep_next = timed(hs, a.steps, 1, sweep_next, use_graph=True)
 
     # end to end through the public API with host buffers: upload A from pinned
-    # host memory, run the step, read the accept masks and log-dets back.
-    h_logabs = torch.zeros(B, dtype=torch.float64).pin_memory()
-    h_sign = torch.zeros(B, dtype=torch.int32).pin_memory()
-    h_acc = torch.zeros(nsw, B, N, dtype=torch.uint8).pin_memory()
+    # host memory, run the step (graph replay), read accept masks and log-dets back.
     e2e_s, e2e_acc = [], 0
+    h2d = sum(c["batch"] * c["N"] * c["N"] * 8 for c in a.classes)
+    d2h = sum(nsw * c["batch"] * c["N"] + c["batch"] * 12 for c in a.classes)
     for it in range(a.warmup + a.steps):
         barrier()
         t0 = time.perf_counter()
-        W.set_matrix(A0_pinned)
-        for s in range(nsw):
-            W.sweep(base, s, a.sigma, accepted_out=acc_dev[s])
-        W.recompute()
-        h_acc.copy_(acc_dev, non_blocking=True)
-        W.logdet(h_logabs, h_sign)
+        for h in hs:
+            h["W"].set_matrix(h["A0"])
+        step(hs, 0, True)
+        got = 0
+        for h in hs:
+            c = h["cls"]
+            acc = np.zeros((nsw, c["batch"], c["N"]), dtype=np.uint8)
+            la = np.zeros(c["batch"])
+            sg = np.zeros(c["batch"], dtype=np.int32)
+            h["W"].step_results(nsw, acc)
+            h["W"].logdet(la, sg)
+            got += int(acc.sum())
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if it >= a.warmup:
             e2e_s.append(dt)
-            e2e_acc += int(h_acc.sum())
-    W.close()
+            e2e_acc += got
+    if group is not None:
+        qmcdu_group_destroy(group)
+    for h in hs:
+        h["W"].close()
 
-    # K = 1 (Sherman-Morrison) on the same GPU, same workload
+    # K = 1 (Sherman-Morrison) on the same GPU, same walker (single workload)
     k1 = None
-    if a.K != 1 and a.k1_steps > 0:
-        W1 = Walkers(N, 1, a.precision, B, stream=stream)
-        W1.set_matrix(A0_pinned)
-        ms1, acc1, _, _ = time_steps(W1, 1, a.k1_steps, 1, 0)
+    if a.workload == "single" and a.k1_steps > 0:
+        c = a.classes[0]
+        W1 = Walkers(c["N"], 1, a.precision, c["batch"], stream=s0)
+        W1.set_matrix(hs[0]["A0"])
+        h1 = [dict(W=W1, stream=s0, base=hs[0]["base"], cls=dict(c, K=1))]
+        ms1, acc1, _, _ = timed(h1, a.k1_steps, 1, 0, use_graph=True)
         W1.close()
         k1 = (ms1, acc1)
 
@@ -280,43 +360,47 @@ def run_ours(a, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
-    total_ms = allmax(sum(ms))
-    total_acc = allsum(accepted)
-    e2e_t = allmax(sum(e2e_s))
-    e2e_total_acc = allsum(e2e_acc)
-    res = dict(ms=ms, total_ms=total_ms, accepted=total_acc, prof=prof, clocks=clk,
-               e2e_s=e2e_t, e2e_acc=e2e_total_acc, k1=None)
+    res = dict(ms=ms, total_ms=allmax(sum(ms)), accepted=allsum(accepted), prof=prof, clocks=clk,
+               graph_ms=allmax(sum(msg)), graph_accepted=allsum(accg),
+               e2e_s=allmax(sum(e2e_s)), e2e_acc=allsum(e2e_acc), h2d=h2d, d2h=d2h,
+               nprop=nprop, tuned=tuned, k1=None)
     if k1 is not None:
         res["k1"] = dict(ms=allmax(sum(k1[0])), accepted=allsum(k1[1]))
     return res
 
 
 def roofline_for(a, res):
-    """Dominant kernel: the persistent sweep kernel (one launch per sweep). Its
-    algorithmic work is the Eq. 4 flush, 4 N^2 flops per accepted move, plus
-    the ratio dot products, 2 (2k + 2) N flops per proposal with k the mean
-    queue length (about K/2 at high acceptance), and the W-panel append,
-    4 k N flops per accepted move."""
-    prof = res["prof"] or {}
-    N, K = a.N, a.K
-    acc_per_gpu = res["accepted"] / max(1, a.gpus)
-    prop_per_gpu = a.steps * a.sweeps_per_step * a.N * a.batch
-    kbar = 0.0 if K == 1 else (K - 1) / 2.0
-    flops = 4.0 * N * N * acc_per_gpu + 2.0 * (2 * kbar + 2) * N * prop_per_gpu + 4.0 * kbar * N * acc_per_gpu
-    launches = prof.get("sweep_kernels", 0)
-    ms = prof.get("sweep_kernel_ms", 0.0)
+    """Dominant kernel: the persistent sweep kernel (one launch per sweep and
+    size class). Its algorithmic work is the Eq. 4 flush, 4 N^2 flops per
+    accepted move, plus the ratio dot products, 2 (2k + 2) N flops per proposal
+    with k the mean queue length (about K/2 at high acceptance), and the W-panel
+    append, 4 k N flops per accepted move."""
+    profs = res["prof"] or []
+    if not profs:
+        return None
+    flops, ms, launches = 0.0, 0.0, 0
+    acc_frac = res["accepted"] / max(1.0, res["nprop"] * a.steps * max(1, a.gpus))
+    for c, prof in zip(a.classes, profs):
+        N, K = c["N"], c["K"]
+        props = a.steps * a.sweeps_per_step * N * c["batch"]
+        acc = props * acc_frac
+        kbar = 0.0 if K == 1 else (K - 1) / 2.0
+        flops += 4.0 * N * N * acc + 2.0 * (2 * kbar + 2) * N * props + 4.0 * kbar * N * acc
+        ms = max(ms, prof.get("sweep_kernel_ms", 0.0))
+        launches += int(prof.get("sweep_kernels", 0))
     if not launches or ms <= 0:
         return None
-    achieved = flops / launches / (ms / launches * 1e-3) / 1e12
+    nlaunch_per_class = launches / len(profs)
+    achieved = flops / (ms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if a.precision == "fp64" else FP32_PEAK_TFLOPS
-    key = source_hash("kernels_sweep.cu")
+    key = "%s:%s" % (source_hash("kernels_sweep.cu"), a.workload)
     return {"kernel": "sweep_kernel (persistent fused sweep: Eq. 3 ratios, bordered append, Eq. 4 flush)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(key),
             "peak_source": "derived: 148 SMs x %s FMA/clk x 2 x 2032 MHz"
                            % ("2 FP64" if a.precision == "fp64" else "128 FP32"),
-            "flops_per_launch": flops / launches, "launches": launches,
-            "avg_launch_ms": ms / launches,
+            "flops_per_launch": flops / nlaunch_per_class, "launches": launches,
+            "avg_launch_ms": ms / nlaunch_per_class,
             "share_of_step": ms / res["total_ms"] if res["total_ms"] else None}
 
 
@@ -331,10 +415,11 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        nm = cpu_sample_size(a, seconds=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
+        K = 64 if a.K == "auto" else int(a.K)
+        nm = cpu_sample_size(a, K, seconds=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
         vals = []
         for it in range(a.warmup + a.steps):
-            acc, dt, _ = cpu_oracle_sample(a, nm)
+            acc, dt, _ = cpu_oracle_sample(a, nm, K)
             if it >= a.warmup:
                 vals.append(acc / dt)
         v = float(np.median(vals))
@@ -343,8 +428,8 @@ def main():
                 "higher_is_better": True, "dtype": "f64", "data": "synthetic",
                 "config": config(a, 1),
                 "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                                 "sample": "first %d proposals of sweep 0, one walker "
-                                           "(setup inverse timed apart and excluded)" % nm},
+                                 "sample": "first %d proposals of sweep 0 of one N=%d walker, K=%d "
+                                           "(setup inverse timed apart and excluded)" % (nm, a.N, K)},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -366,10 +451,15 @@ def main():
     line = {"metric": metric, "value": value, "unit": "updates/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["total_ms"] / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "f32", "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "f32 (bf16x3 flush)"}[a.precision],
+            "data": "synthetic",
             "config": config(a, a.gpus)}
     line["accepted_moves"] = res["accepted"]
-    line["acceptance"] = res["accepted"] / (a.steps * a.sweeps_per_step * a.N * a.batch * a.gpus)
+    line["acceptance"] = res["accepted"] / (res["nprop"] * a.steps * a.gpus)
+    line["graph_replay"] = {"value": res["graph_accepted"] / (res["graph_ms"] * 1e-3),
+                            "ms_per_step": res["graph_ms"] / a.steps}
+    if res["tuned"]:
+        line["autotune"] = res["tuned"]
     if res["k1"]:
         k1v = res["k1"]["accepted"] / (res["k1"]["ms"] * 1e-3)
         line["k1_sherman_morrison"] = {"value": k1v, "unit": "updates/s",
@@ -377,29 +467,31 @@ def main():
         line["speedup_vs_k1"] = value / k1v
     line["roofline"] = roofline_for(a, res)
     line["e2e"] = {"value": res["e2e_acc"] / res["e2e_s"], "unit": "updates/s",
-                   "h2d_bytes_per_step": a.batch * a.N * a.N * 8,
-                   "d2h_bytes_per_step": a.sweeps_per_step * a.batch * a.N + a.batch * 12}
-    prof = res["prof"] or {}
-    line["gpu_launches"] = int(prof.get("launches", 0))
-    sweep_ms = prof.get("sweep_kernel_ms", 0.0)
-    rec_ms = prof.get("recompute_ms", 0.0)
-    line["breakdown_ms_per_step"] = {
-        "sweep kernel": sweep_ms / a.steps,
-        "recompute (fp64 Gauss-Jordan)": rec_ms / a.steps,
-        "proposal draws + log-det + launches": (res["total_ms"] - sweep_ms - rec_ms) / a.steps}
-    nprop = a.steps * a.sweeps_per_step * a.N
-    line["sweep_phases_us_per_proposal"] = {
-        k[6:-3]: v * 1000.0 / nprop for k, v in prof.items()
-        if k.startswith("sweep_") and k.endswith("_ms") and k != "sweep_kernel_ms"}
+                   "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]}
+    profs = res["prof"] or []
+    line["gpu_launches"] = int(sum(p.get("launches", 0) for p in profs))
+    if len(profs) == 1:
+        prof = profs[0]
+        sweep_ms = prof.get("sweep_kernel_ms", 0.0)
+        rec_ms = prof.get("recompute_ms", 0.0)
+        line["breakdown_ms_per_step"] = {
+            "sweep kernel": sweep_ms / a.steps,
+            "recompute (fp64 Gauss-Jordan)": rec_ms / a.steps,
+            "proposal draws + log-det + launches": (res["total_ms"] - sweep_ms - rec_ms) / a.steps}
+        nprop = a.steps * a.sweeps_per_step * a.N
+        line["sweep_phases_us_per_proposal"] = {
+            k[6:-3]: v * 1000.0 / nprop for k, v in prof.items()
+            if k.startswith("sweep_") and k.endswith("_ms") and k != "sweep_kernel_ms"}
     line["clocks"] = res["clocks"]
     if a.gpus == 1:
-        nm = cpu_sample_size(a)
-        acc, dt, t_setup = cpu_oracle_sample(a, nm)
+        K = a.classes[0]["K"]
+        nm = cpu_sample_size(a, K)
+        acc, dt, t_setup = cpu_oracle_sample(a, nm, K)
         line["cpu_baseline"] = {"value": acc / dt, "unit": "updates/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": "first %d proposals of sweep 0 of one walker (N=%d, K=%d): "
                                           "%.1f s of updates; the %.1f s setup inverse excluded"
-                                          % (nm, a.N, a.K, dt, t_setup)}
+                                          % (nm, a.N, K, dt, t_setup)}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

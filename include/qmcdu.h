@@ -47,8 +47,8 @@ enum {
     QMCDU_FP32 = 1,        /* A^{-1}, panels, flush fp32; k x k inverse, ratios,  */
                            /* log-det and the recompute fp64                      */
     QMCDU_FP32_BF16X3 = 2  /* as FP32, flush on tensor cores with split-bf16 x3   */
-                           /* (tcgen05); sweeps of such a handle run as        */
-                           /* per-proposal launches around the tensor-core flush */
+                           /* (tcgen05) wherever a flush block is >= 128       */
+                           /* columns and K <= 64; fp32 SIMT flush otherwise   */
 };
 
 enum {
@@ -168,8 +168,8 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
  * Graph capture needs a handle on a non-default stream (ERR_ARG otherwise).
  *   accepted_out  host or device [nsweeps][batch][N] uint8, or NULL
  *   drift_out     host or device [batch][2] (as qmcdu_recompute), or NULL
- * Handles of precision QMCDU_FP32_BF16X3, or with persistent sweeps switched
- * off, run the sweeps call by call without a graph.
+ * Handles with persistent sweeps switched off run the sweeps call by call
+ * without a graph.
  */
 int qmcdu_step(qmcdu_t h, unsigned long long base_seed, int first_sweep, int nsweeps, double sigma,
                int recompute, int use_graph, unsigned char *accepted_out, double *drift_out);
@@ -187,9 +187,9 @@ int qmcdu_step_results(qmcdu_t h, int nsweeps, unsigned char *accepted_out, doub
  * (batch N^3; QMCDU_OPT_MAX_CTAS) so that the classes' persistent sweeps run
  * side by side, forks every handle's stream from the first handle's stream
  * and joins them back, and (use_graph) captures the whole fork/join step in
- * one CUDA graph. seeds[i] is handle i's base seed. Handles of precision
- * QMCDU_FP32_BF16X3 or without persistent sweeps are refused (ERR_ARG). The
- * group does not own the handles; destroy it before them.
+ * one CUDA graph. seeds[i] is handle i's base seed. Handles without
+ * persistent sweeps are refused (ERR_ARG). The group does not own the
+ * handles; destroy it before them.
  */
 int qmcdu_group_create(qmcdu_t *handles, int n, qmcdu_group_t *out);
 int qmcdu_group_step(qmcdu_group_t g, const unsigned long long *seeds, int first_sweep,

@@ -31,6 +31,7 @@
 // Every spin-wait has a time budget (globaltimer); on expiry the kernel sets
 // ST_TIMEOUT in the status word and returns. Data written by other CTAs is read
 // with ld.global.cg (L2, not the SM's L1).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -67,6 +68,7 @@ struct SweepParams {
     long long budget_ns;    // per wait
     int stall;              // test hook: the first ratio barrier waits for one CTA too many
     int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm, off_bar;
+    int kp;                         // tensor-core flush: K rounded up to 16 (<= 64)
     unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
 };
 
@@ -345,12 +347,225 @@ __device__ bool flush_columns(const SweepParams<T> &p, int w, int k, int c_begin
     return true;
 }
 
-template <typename T, bool RES>
-__global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
+
+// ---------------------------------------------------------------------------
+// Tensor-core flush (fp32 working precision, split-bf16 x3 on tcgen05), for
+// flush CTAs that own at least 128 columns of A^{-1}. Per tile of 128 columns
+// (rows of the column-major storage):
+//   T' (128 x k) = X V'          K = N, staged 32 at a time, double buffered
+//   X (128 x N) -= T' W           K = k, 128 columns of X at a time
+// with x = hi + lo, hi = bf16(x), lo = bf16(x - hi), and hi*hi + hi*lo + lo*hi
+// accumulated in fp32 tensor memory (columns [0, 128) hold T', [128, 256) the
+// update). Operands are written by the CTA's threads as K-major 8 x 8 bf16
+// core matrices (no swizzle), which the shared-memory descriptors describe.
+namespace tcf {
+constexpr int BM = 128, BK = 32;
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ uint32_t idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// byte offset of (row r, column k) in a K-major tile of `kc` columns
+__device__ __forceinline__ uint32_t coff(int r, int k, int kc)
+{
+    return (uint32_t)((((r >> 3) * (kc >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void put(__nv_bfloat16 *hi, __nv_bfloat16 *lo, uint32_t off, float x)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[off >> 1] = h;
+    lo[off >> 1] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+        " [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// shared-memory region of the tensor-core flush, for kp = K rounded up to 16
+__host__ __device__ inline size_t region_bytes(int kp)
+{
+    return (size_t)2 * 2 * BM * BK * 2 + (size_t)2 * 2 * kp * BK * 2 + (size_t)2 * BM * kp * 2 * 2 +
+           4 * sizeof(unsigned long long);
+}
+}  // namespace tcf
+
+// Returns false after a wait ran out of budget (ST_TIMEOUT recorded).
+template <typename T>
+__device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int c_end,
+                         unsigned char *smem, uint32_t tmem, unsigned *tph)
+{
+    using namespace tcf;
+    const int N = p.N, ld = p.ld, K = p.K, KP = p.kp;
+    unsigned char *reg = smem + p.off_xs;
+    __nv_bfloat16 *a1h = (__nv_bfloat16 *)reg;                    // [2][BM*BK]
+    __nv_bfloat16 *a1l = a1h + 2 * BM * BK;
+    __nv_bfloat16 *b1h = a1l + 2 * BM * BK;                      // [2][KP*BK]
+    __nv_bfloat16 *b1l = b1h + 2 * KP * BK;
+    __nv_bfloat16 *a2h = b1l + 2 * KP * BK;                      // [BM*KP]
+    __nv_bfloat16 *a2l = a2h + BM * KP;
+    __nv_bfloat16 *b2h = a2l + BM * KP;                          // [BM*KP]
+    __nv_bfloat16 *b2l = b2h + BM * KP;
+    unsigned long long *bars = (unsigned long long *)(b2l + BM * KP);
+    __shared__ int ok_s;
+    const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
+    T *Ab = p.Ainv + (size_t)w * wN;
+    const T *Vb = p.V + (size_t)w * wK;
+    const T *Wb = p.W + (size_t)w * wK;
+    const int *idxw = p.idx + (size_t)w * K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kp = (k + 15) / 16 * 16;
+    const uint32_t id1 = idesc(BM, kp), id2 = idesc(BM, BM);
+    const int nk = (N + BK - 1) / BK;
+    for (int c0 = c_begin; c0 < c_end; c0 += BM) {
+        const int nrows = min(BM, c_end - c0);
+        // ---- T' = X V' over K = N
+        int pend[2] = {0, 0};
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb & 1;
+            if (pend[s]) {
+                if (threadIdx.x == 0) ok_s = mbar_wait(&bars[s], tph[s], p.status, p.budget_ns) ? 1 : 0;
+                __syncthreads();
+                tph[s] ^= 1u;
+                pend[s] = 0;
+                if (!ok_s) return false;
+            }
+            const int k0 = kb * BK;
+            for (int e = threadIdx.x; e < BM * BK; e += STHREADS) {
+                const int r = e / BK, kk = e - r * BK, i = k0 + kk;
+                const float x = (r < nrows && i < N) ? (float)__ldcg(Ab + (size_t)(c0 + r) * ld + i) : 0.f;
+                put(a1h + s * BM * BK, a1l + s * BM * BK, coff(r, kk, BK), x);
+            }
+            for (int e = threadIdx.x; e < kp * BK; e += STHREADS) {
+                const int m = e / BK, kk = e - m * BK, i = k0 + kk;
+                const float x = (m < k && i < N) ? (float)__ldcg(Vb + (size_t)m * ld + i) : 0.f;
+                put(b1h + s * KP * BK, b1l + s * KP * BK, coff(m, kk, BK), x);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int ks = 0; ks < BK / 16; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    const uint64_t ah = sdesc(su32(a1h + s * BM * BK) + ko, 128, 512);
+                    const uint64_t al = sdesc(su32(a1l + s * BM * BK) + ko, 128, 512);
+                    const uint64_t bh = sdesc(su32(b1h + s * KP * BK) + ko, 128, 512);
+                    const uint64_t bl = sdesc(su32(b1l + s * KP * BK) + ko, 128, 512);
+                    mma(tmem, ah, bh, id1, (kb == 0 && ks == 0) ? 0u : 1u);
+                    mma(tmem, ah, bl, id1, 1u);
+                    mma(tmem, al, bh, id1, 1u);
+                }
+                commit(&bars[s]);
+            }
+            pend[s] = 1;
+        }
+        for (int s = 0; s < 2; ++s) {
+            if (pend[s]) {
+                if (threadIdx.x == 0) ok_s = mbar_wait(&bars[s], tph[s], p.status, p.budget_ns) ? 1 : 0;
+                __syncthreads();
+                tph[s] ^= 1u;
+                if (!ok_s) return false;
+            }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // ---- T' (minus the selector E') into shared memory as the A operand of the update
+        if (warp < 4) {
+            const int r = warp * 32 + lane;
+            for (int m0 = 0; m0 < kp; m0 += 16) {
+                uint32_t v[16];
+                ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)m0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int m = m0 + j;
+                    float t = 0.f;
+                    if (m < k) t = __uint_as_float(v[j]) - (__ldcg(idxw + m) == c0 + r ? 1.f : 0.f);
+                    put(a2h, a2l, coff(r, m, KP), t);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        // ---- X -= T' W, 128 columns of X (entries i of A^{-1}[:, c]) at a time
+        for (int i0 = 0; i0 < N; i0 += BM) {
+            for (int e = threadIdx.x; e < BM * kp; e += STHREADS) {
+                const int m = e / BM, r = e - m * BM, i = i0 + r;
+                const float x = (m < k && i < N) ? (float)__ldcg(Wb + (size_t)m * ld + i) : 0.f;
+                put(b2h, b2l, coff(r, m, KP), x);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sbo = (uint32_t)(KP / 8) * 128u;
+                for (int ks = 0; ks < kp / 16; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    const uint64_t ah = sdesc(su32(a2h) + ko, 128, sbo);
+                    const uint64_t al = sdesc(su32(a2l) + ko, 128, sbo);
+                    const uint64_t bh = sdesc(su32(b2h) + ko, 128, sbo);
+                    const uint64_t bl = sdesc(su32(b2l) + ko, 128, sbo);
+                    mma(tmem + 128u, ah, bh, id2, ks == 0 ? 0u : 1u);
+                    mma(tmem + 128u, ah, bl, id2, 1u);
+                    mma(tmem + 128u, al, bh, id2, 1u);
+                }
+                commit(&bars[2]);
+                ok_s = mbar_wait(&bars[2], tph[2], p.status, p.budget_ns) ? 1 : 0;
+            }
+            __syncthreads();
+            tph[2] ^= 1u;
+            if (!ok_s) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (warp < 4) {
+                const int r = warp * 32 + lane;
+                T *xrow = Ab + (size_t)(c0 + r) * ld;
+                for (int j0 = 0; j0 < BM; j0 += 16) {
+                    uint32_t v[16];
+                    ld16(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)j0, v);
+                    if (r < nrows) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int i = i0 + j0 + j;
+                            if (i < N) xrow[i] -= (T)__uint_as_float(v[j]);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
+template <typename T, bool RES, bool TC>
+__device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_t tmem)
+{
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
     if (grp >= p.ngroups) return;
+    unsigned tph[3] = {0, 0, 0};     // phases of the tensor-core flush's mbarriers
     const int N = p.N, K = p.K, ld = p.ld, Gf = p.Gf, Gr = p.Gr;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     unsigned *ratio_ctr = p.sync + SYNC_STRIDE * grp + 0;
@@ -360,8 +575,6 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
     const int cpc = (N + Gf - 1) / Gf;                 // columns per CTA in the flush
     const int fc0 = min(N, rank * cpc), fc1 = min(N, fc0 + cpc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) mbar_init((unsigned long long *)(smem + p.off_bar));
-    __syncthreads();
 
     if (rank >= Gr) {
         // Helper CTA: take part in every flush of every walker of the group.
@@ -372,8 +585,13 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
                 ++n_event;
                 if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
                 const int k = __ldcg(p.kglob + w);
-                if (k > 0 && k < SMALL_K) flush_columns_small(p, w, k, fc0, fc1);
-                else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) return;
+                if (TC) {
+                    if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
+                } else if (k > 0 && k < SMALL_K) {
+                    flush_columns_small(p, w, k, fc0, fc1);
+                } else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) {
+                    return;
+                }
                 if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
                 if (last) break;
             }
@@ -456,16 +674,30 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
                     part[job] = (double)acc0 + (double)acc1;
                 }
             } else {
-                for (int job = warp; job < 2 * k + 1; job += SWARPS) {
-                    const T *src, *with;
-                    if (job == 0) { src = asb; with = vsb; }
-                    else if (job <= k) { src = Ww + (size_t)(job - 1) * ld + i0; with = vsb; }
-                    else { src = Vw + (size_t)(job - 1 - k) * ld + i0; with = asb; }
-                    T acc = 0;
+                // queue rows in global memory: four jobs per warp at a time, so that
+                // each lane keeps 4 x (unroll) independent loads in flight
+                const int nj_k = 2 * k + 1;
+                for (int j0 = warp * 4; j0 < nj_k; j0 += SWARPS * 4) {
+                    const T *src[4];
+                    const T *with[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int job = min(j0 + q, nj_k - 1);
+                        if (job == 0) { src[q] = asb; with[q] = vsb; }
+                        else if (job <= k) { src[q] = Ww + (size_t)(job - 1) * ld + i0; with[q] = vsb; }
+                        else { src[q] = Vw + (size_t)(job - 1 - k) * ld + i0; with[q] = asb; }
+                    }
+                    T acc[4] = {0, 0, 0, 0};
 #pragma unroll 4
-                    for (int t = lane; t < L; t += 32) acc += src[t] * with[t];
-                    acc = warp_allsum(acc);
-                    if (lane == 0) part[job] = (double)acc;
+                    for (int t = lane; t < L; t += 32) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[q] += src[q][t] * with[q][t];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const T v = warp_allsum(acc[q]);
+                        if (lane == 0 && j0 + q < nj_k) part[j0 + q] = (double)v;
+                    }
                 }
             }
             tick(0);
@@ -550,15 +782,46 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
                         else Wsm[k * LP + t] = zs[t] * rT;
                     }
                 } else {
+                    // queue rows in global memory: four rows per thread, m outermost,
+                    // so that loads of different (m, row) are independent
                     const T rT = (T)rinv;
-                    for (int t = threadIdx.x; t < L; t += STHREADS) {
-                        const int i = i0 + t;
-                        T z = asb[t];
-                        for (int m = 0; m < k; ++m) z -= cT[m] * Ww[(size_t)m * ld + i];
-                        for (int m = 0; m < k; ++m) Ww[(size_t)m * ld + i] -= z * yT[m];
-                        Ww[(size_t)k * ld + i] = z * rT;
-                        Vw[(size_t)k * ld + i] = vsb[t];
-                        arow_w[i] = vdb[t];
+                    constexpr int SUB = 4;
+                    for (int tb = 0; tb < L; tb += STHREADS * SUB) {
+                        T z[SUB];
+#pragma unroll
+                        for (int q = 0; q < SUB; ++q) {
+                            const int t = tb + threadIdx.x + q * STHREADS;
+                            z[q] = t < L ? asb[t] : (T)0;
+                        }
+#pragma unroll 4
+                        for (int m = 0; m < k; ++m) {
+                            const T cm = cT[m];
+                            const T *wr = Ww + (size_t)m * ld + i0;
+#pragma unroll
+                            for (int q = 0; q < SUB; ++q) {
+                                const int t = tb + threadIdx.x + q * STHREADS;
+                                if (t < L) z[q] -= cm * wr[t];
+                            }
+                        }
+#pragma unroll 4
+                        for (int m = 0; m < k; ++m) {
+                            const T ym = yT[m];
+                            T *wr = Ww + (size_t)m * ld + i0;
+#pragma unroll
+                            for (int q = 0; q < SUB; ++q) {
+                                const int t = tb + threadIdx.x + q * STHREADS;
+                                if (t < L) wr[t] -= z[q] * ym;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < SUB; ++q) {
+                            const int t = tb + threadIdx.x + q * STHREADS;
+                            if (t < L) {
+                                Ww[(size_t)k * ld + i0 + t] = z[q] * rT;
+                                Vw[(size_t)k * ld + i0 + t] = vsb[t];
+                                arow_w[i0 + t] = vdb[t];
+                            }
+                        }
                     }
                 }
                 ++k;
@@ -583,8 +846,13 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
             ++n_event;
             if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
             tick(5);
-            if (k > 0 && k < SMALL_K) flush_columns_small(p, w, k, fc0, fc1);
-            else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) return;
+            if (TC) {
+                if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
+            } else if (k > 0 && k < SMALL_K) {
+                flush_columns_small(p, w, k, fc0, fc1);
+            } else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) {
+                return;
+            }
             tick(6);
             if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
             if (k > 0 && j + 1 < N) stage(j + 1, b ^ 1, false, true);   // the column changed
@@ -594,6 +862,40 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
         if (timed)
             for (int q = 0; q < 8; ++q) p.phase_ns[q] += ph[q];
     }
+}
+
+
+// The kernel: tensor memory for the tensor-core flush (256 columns: two of
+// these CTAs at most share an SM, 2 x 256 = 512 columns), the mbarriers, the
+// sweep, and the release of the tensor memory on every exit path.
+template <typename T, bool RES, bool TC>
+__global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_s;
+    if (TC && threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+                     ::"r"(tcf::su32(&tmem_s)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init((unsigned long long *)(smem + p.off_bar));
+        if (TC) {
+            unsigned long long *bars = (unsigned long long *)(smem + p.off_xs + tcf::region_bytes(p.kp) -
+                                                              4 * sizeof(unsigned long long));
+            for (int q = 0; q < 3; ++q)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    sweep_body<T, RES, TC>(p, smem, TC ? tmem_s : 0u);
+    if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (TC && threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_s) : "memory");
 }
 
 // Gaussians (Box-Muller pairs) and Metropolis uniforms of one sweep for every
@@ -660,7 +962,7 @@ __global__ void sweep_logdet_kernel(int N, const unsigned char *acc, const doubl
 static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 template <typename T>
-static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int *offs)
+static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, int *offs)
 {
     size_t o = 0;
     offs[8] = (int)o; o = align16(o + 16);                                   // mbarrier
@@ -669,7 +971,8 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int *offs)
     offs[2] = (int)o; o = align16(o + (size_t)2 * chunk * sizeof(double));   // vd
     offs[3] = (int)o; o = align16(o + (size_t)(2 * K + 1) * sizeof(double)); // red
     offs[4] = (int)o; o = align16(o + (size_t)std::max(K * cb, 2 * K + chunk) * sizeof(T));  // ts
-    offs[5] = (int)o; o = align16(o + (size_t)cb * ld * sizeof(T));          // xs
+    offs[5] = (int)o;                                                        // xs / tc region
+    o = align16(o + (tc ? tcf::region_bytes((K + 15) / 16 * 16) : (size_t)cb * ld * sizeof(T)));
     offs[6] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Wsm
     offs[7] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Vsm
     return o;
@@ -678,23 +981,23 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int *offs)
 static const size_t SMEM_BUDGET = 200 * 1024;
 static const size_t RES_BUDGET = 128 * 1024;
 
-template <typename T, bool RES>
+template <typename T, bool RES, bool TC>
 static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, int chunk)
 {
     const int K = c.K;
     int offs[9];
     int cb = MAX_CB;
-    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, offs);
+    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, offs);
     while (cb > 1 && smem > SMEM_BUDGET) {
         cb >>= 1;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, offs);
     }
     if (smem > SMEM_BUDGET) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, TC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES>, STHREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, TC>, STHREADS, smem);
     if (e != cudaSuccess) return e;
     int capacity = per_sm * c.num_sms;
     if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
@@ -716,17 +1019,18 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.off_vs = offs[0]; p.off_as = offs[1]; p.off_vd = offs[2]; p.off_red = offs[3];
     p.off_ts = offs[4]; p.off_xs = offs[5]; p.off_wsm = offs[6]; p.off_vsm = offs[7];
     p.off_bar = offs[8];
+    p.kp = (K + 15) / 16 * 16;
     p.phase_ns = c.prof ? c.sw_phase : nullptr;
     e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {&p};
-    e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES>, dim3(ngroups * Gf),
+    e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES, TC>, dim3(ngroups * Gf),
                                     dim3(STHREADS), args, smem, c.stream);
     c.last_sweep_shape[0] = Gf;
     c.last_sweep_shape[1] = Gr;
     c.last_sweep_shape[2] = ngroups;
     c.last_sweep_shape[3] = chunk;
-    c.last_sweep_shape[4] = RES ? cb : -cb;
+    c.last_sweep_shape[4] = TC ? 1000 : (RES ? cb : -cb);
     return e;
 }
 
@@ -750,7 +1054,13 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
     Gr = std::min(Gr, (N + chunk - 1) / chunk);
     Gf = std::max(Gf, Gr);
     const bool res = chunk <= 256 && 2 * (size_t)K * (chunk + 1) * sizeof(T) <= RES_BUDGET;
-    return res ? launch_shape<T, true>(c, L, Gf, Gr, chunk) : launch_shape<T, false>(c, L, Gf, Gr, chunk);
+    // tensor-core flush: split-bf16 precision, flush blocks of >= 128 columns, K <= 64
+    const int cpc = (N + Gf - 1) / Gf;
+    const bool tc = std::is_same<T, float>::value && c.prec == QMCDU_FP32_BF16X3 && !res &&
+                    K <= 64 && cpc >= 128;
+    if (tc) return launch_shape<T, false, true>(c, L, Gf, Gr, chunk);
+    return res ? launch_shape<T, true, false>(c, L, Gf, Gr, chunk)
+               : launch_shape<T, false, false>(c, L, Gf, Gr, chunk);
 }
 
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)

@@ -450,7 +450,7 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         ov = c->sw_override;
     }
     CK(cudaMemsetAsync(c->sw_ties, 0, c->batch * sizeof(long long), c->stream));
-    if (c->opt_persistent && c->prec != QMCDU_FP32_BF16X3) {
+    if (c->opt_persistent) {
         SweepLaunch S{};
         S.seed = base_seed;
         S.sweep = sweep_index;
@@ -656,7 +656,7 @@ int qmcdu_step(qmcdu_t h, unsigned long long base_seed, int first_sweep, int nsw
     if (st) return st;
     c->pending = false;
     const size_t BN = (size_t)c->batch * c->N;
-    if (!c->opt_persistent || c->prec == QMCDU_FP32_BF16X3) {
+    if (!c->opt_persistent) {
         // per-proposal launches: run the sweeps one call at a time (no graph)
         for (int i = 0; i < nsweeps; ++i) {
             st = qmcdu_sweep(h, base_seed, first_sweep + i, sigma, nullptr,
@@ -714,7 +714,7 @@ int qmcdu_group_create(qmcdu_t *hs, int n, qmcdu_group_t *out)
     for (int i = 0; i < n; ++i) {
         if (!hs[i]) { delete g; return QMCDU_ERR_ARG; }
         Ctx *c = reinterpret_cast<Ctx *>(hs[i]);
-        if (c->prec == QMCDU_FP32_BF16X3 || !c->opt_persistent) { delete g; return QMCDU_ERR_ARG; }
+        if (!c->opt_persistent) { delete g; return QMCDU_ERR_ARG; }
         g->hs.push_back(c);
         total += (double)c->batch * c->N * c->N * c->N;
     }

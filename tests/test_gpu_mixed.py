@@ -55,3 +55,37 @@ def test_mixed_precision_within_stated_bound(precision, N, K, sigma):
         assert np.array_equal(acc[:, b].astype(bool), ref["accepted"])
         assert errs[0] < bound and errs[1] < bound and errs[2] < bound
         assert sg[b] == ref["sign"]
+
+
+@pytest.mark.parametrize("N,K", [(768, 32), (700, 48)])
+def test_tensor_core_flush_inside_the_sweep(N, K):
+    """Split-bf16 precision with flush blocks of >= 128 columns: the persistent
+    sweep applies Eq. 4 on tcgen05 (ragged last tile for N = 700)."""
+    need_gpu()
+    batch, nsweeps, base, sigma = 2, 2, 1500 + N, 0.1
+    A, G, U = walker_inputs(base, batch, N, nsweeps)
+    refs = [oracle.sweeps(oracle.SM, A[b], G[b], U[b], sigma) for b in range(batch)]
+    override = np.stack([r["accepted"].astype(np.int8) for r in refs], axis=1)
+    W = Walkers(N, K, "bf16x3", batch)
+    W.set_option("max_ctas", 4)           # two CTAs per walker: flush blocks of N/2 columns
+    W.set_matrix(A)
+    rat = np.zeros((nsweeps, batch, N))
+    for s in range(nsweeps):
+        W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s]), ratios_out=rat[s])
+    shape = W.sweep_shape()
+    Ai = np.zeros((batch, N, N))
+    la = np.zeros(batch)
+    sg = np.zeros(batch, dtype=np.int32)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.close()
+    assert shape["col_tile"] == 1000 and shape["flush_ctas"] == 2, shape   # tensor-core flush ran
+    for b, ref in enumerate(refs):
+        kappa = max(np.linalg.cond(A[b], 1), np.linalg.cond(ref["A"], 1))
+        bound = 8 * N * U_W["bf16x3"] * kappa
+        errs = (rel_ratio_err(rat[:, b], ref["ratios"]), rel_norm_err(Ai[b], ref["Ainv"]),
+                logdet_err(la[b], ref["logabs"]))
+        print("tc flush N=%d K=%d walker %d: bound %.1e ratio %.1e inverse %.1e logdet %.1e"
+              % ((N, K, b, bound) + errs))
+        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
+        assert errs[1] < 1e-2                 # far tighter than the bound: split bf16 is working
