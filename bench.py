@@ -55,6 +55,9 @@ WORKLOADS = {
     "single": [dict(N=2048, batch=1)],
     "uneven": [dict(N=512, batch=256), dict(N=1536, batch=64)],
     "mixed": [dict(N=2048, batch=64), dict(N=4096, batch=8)],
+    # serving: Poisson arrivals, N uniform over the size set; slots per pool
+    "serve": [dict(N=128, batch=16), dict(N=256, batch=16), dict(N=512, batch=16),
+              dict(N=1024, batch=8), dict(N=2048, batch=8), dict(N=4096, batch=8)],
 }
 
 
@@ -74,12 +77,15 @@ def parse():
     p.add_argument("--k1-steps", type=int, default=1, help="steps of the K=1 comparison")
     p.add_argument("--cpu-moves", type=int, default=-1,
                    help="proposals in the CPU-oracle sample (default: sized for ~15 s)")
+    p.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    p.add_argument("--window", type=float, default=20.0, help="serve: seconds of arrivals timed")
+    p.add_argument("--budget-gb", type=float, default=150.0, help="serve: HBM budget (GB)")
     a = p.parse_args()
     a.classes = [dict(c) for c in WORKLOADS[a.workload]]
     if a.N is not None and a.workload == "single":
         a.classes[0]["N"] = a.N
     if a.precision is None:
-        a.precision = "fp32" if a.workload == "mixed" else "fp64"
+        a.precision = "fp32" if a.workload in ("mixed", "serve") else "fp64"
     if a.sweeps_per_step is None:
         a.sweeps_per_step = 10 if a.workload == "single" else 1
     a.N = a.classes[0]["N"]
@@ -87,6 +93,11 @@ def parse():
 
 
 def workload_name(a):
+    if a.workload == "serve":
+        return ("serving: Poisson arrivals at %g/s for %g s, N uniform over {%s}, %s + fp64 "
+                "recompute every 10 sweeps, sigma=%g, 20 sweeps per request, %g GB budget"
+                % (a.rate, a.window, ", ".join(str(c["N"]) for c in a.classes), a.precision,
+                   a.sigma, a.budget_gb))
     cls = " + ".join("%d x N=%d" % (c["batch"], c["N"]) for c in a.classes)
     rec = " + fp64 recompute" if a.workload == "single" else ""
     return "%s walkers, %s, K=%s, sigma=%g, %d sweep(s)%s per step" % (
@@ -369,6 +380,78 @@ def run_ours(a, rank, world, local_rank):
     return res
 
 
+# ------------------------------------------------------------------ serving
+def serve_once(a, trace, plain, window, budget):
+    """One timed run of the library's serving loop over `trace` (arrivals in
+    [0, window)); the loop stops at the end of the window. plain: the
+    one-walker-per-launch fp64 path (one slot per pool, one walker resident, one
+    pool in flight, each walker's sweep on the whole GPU)."""
+    from paper_1708_00744_b300.qmcdu import Server
+    if plain:
+        classes = [dict(N=c["N"], slots=1, group_ctas=148) for c in a.classes]
+        srv = Server(classes, precision="fp64", sigma=a.sigma, recompute_every=10,
+                     hbm_budget=budget, max_walkers=1, max_inflight=1)
+    else:
+        classes = [dict(N=c["N"], slots=c["batch"]) for c in a.classes]
+        srv = Server(classes, precision=a.precision, sigma=a.sigma, recompute_every=10,
+                     hbm_budget=budget)
+    srv.submit(trace)
+    srv.run(until_s=window)
+    st = srv.stats()
+    res = srv.results()
+    srv.close()
+    return st, res
+
+
+def serve_summary(st, res, window):
+    ok = [r for r in res if r["status"] == 0]
+    return {"updates_per_s": st["accepted"] / window, "proposals_per_s": st["proposals"] / window,
+            "walker_sweeps_per_s": st["walker_sweeps"] / window,
+            "acceptance": st["accepted"] / max(1.0, st["proposals"]),
+            "sweep_latency_ms": {"p50": st["sweep_ms_p50"], "p99": st["sweep_ms_p99"]},
+            "request_latency_s": {"p50": st["request_s_p50"], "p99": st["request_s_p99"]},
+            "admission_wait_s": {"p50": st["wait_s_p50"], "p99": st["wait_s_p99"]},
+            "requests": {"arrived": int(st["submitted"]), "finished": len(ok),
+                         "failed": int(st["failed"])},
+            "peak_gb_held": st["peak_bytes"] / 1e9, "pools_created": int(st["pools_created"]),
+            "pools_destroyed": int(st["pools_destroyed"]), "rounds": int(st["rounds"]),
+            "max_walkers_resident": int(st["max_resident"]),
+            "max_pools_in_flight": int(st["max_inflight"]),
+            "walker_sweeps_in_mixed_rounds": int(st["mixed_walker_sweeps"]),
+            "max_drift_logdet": max([r["drift_logdet"] for r in ok] or [0.0]),
+            "max_drift_inverse": max([r["drift_inverse"] for r in ok] or [0.0])}
+
+
+def run_serve(a):
+    import torch
+    from paper_1708_00744_b300 import inputs
+    torch.cuda.set_device(0)
+    budget = int(a.budget_gb * 1e9)
+    sizes = tuple(c["N"] for c in a.classes)
+    # warm-up (untimed): one request of every class through a server of its own
+    warm = [dict(id=i, seed=99 + i, N=n, nsweeps=1, arrival_s=0.0) for i, n in enumerate(sizes)]
+    for plain in (False, True):
+        serve_once(a, warm, plain, -1.0, budget)
+    trace = inputs.serving_trace(a.seed, a.rate, a.window, sizes=sizes, nsweeps=20)
+    clocks = ClockSampler(0)
+    clocks.start()
+    st, res = serve_once(a, trace, False, a.window, budget)
+    clk = clocks.stop()
+    batched = serve_summary(st, res, a.window)
+    st_p, res_p = serve_once(a, trace, True, a.window, budget)
+    plain = serve_summary(st_p, res_p, a.window)
+    # capacity in requests/s from the saturated run, then an offered load below it
+    cap = batched["walker_sweeps_per_s"] / 20.0
+    low_rate = max(0.5, 0.6 * cap)
+    below = None
+    if low_rate < a.rate:
+        trace_lo = inputs.serving_trace(a.seed + 1, low_rate, a.window, sizes=sizes, nsweeps=20)
+        st_l, res_l = serve_once(a, trace_lo, False, a.window, budget)
+        below = dict(serve_summary(st_l, res_l, a.window), offered_rate_per_s=low_rate)
+    return dict(batched=batched, plain=plain, below=below, clocks=clk, capacity_req_s=cap,
+                requests_in_trace=len(trace))
+
+
 def roofline_for(a, res):
     """Dominant kernel: the persistent sweep kernel (one launch per sweep and
     size class). Its algorithmic work is the Eq. 4 flush, 4 N^2 flops per
@@ -432,6 +515,28 @@ def main():
                                            "(setup inverse timed apart and excluded)" % (nm, a.N, K)},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if a.workload == "serve":
+        if world > 1 and rank != 0:
+            return                     # one serving loop per GPU: run it on rank 0's
+        r = run_serve(a)
+        b = r["batched"]
+        line = {"metric": metric, "value": b["updates_per_s"], "unit": "updates/s",
+                "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": a.window * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "f32 (bf16x3 flush)"}[a.precision],
+                "data": "synthetic", "config": config(a, 1),
+                "serving": dict(b, offered_rate_per_s=a.rate, requests_in_trace=r["requests_in_trace"],
+                                capacity_req_per_s=r["capacity_req_s"]),
+                "plain_one_walker_fp64": r["plain"],
+                "below_capacity": r["below"],
+                "speedup_vs_plain": b["updates_per_s"] / max(1e-9, r["plain"]["updates_per_s"]),
+                "roofline": None, "clocks": r["clocks"],
+                "e2e": {"value": b["updates_per_s"], "unit": "updates/s",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": None,
+                        "note": "requests carry keys; matrices are drawn on the device"}}
         print(json.dumps(line))
         return
 

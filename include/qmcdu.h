@@ -243,6 +243,10 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       one arrival that never comes, so that its wait runs out of budget
  *   QMCDU_OPT_MAX_CTAS     [whole GPU] cap on the persistent sweep's grid, so
  *       that several handles' sweeps can run side by side (qmcdu_group_*)
+ *   QMCDU_OPT_GROUP_CTAS   [from the batch] fixed CTAs per walker group (at
+ *       most the grid cap). Every walker then gets the same arithmetic, in the
+ *       same order, whatever the number of walkers in the launch: its results
+ *       are bit-identical alone and in a batch (qmcdu_sweep_walkers, serving)
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {
@@ -251,7 +255,8 @@ enum {
     QMCDU_OPT_FLUSH_CTAS = 3,
     QMCDU_OPT_WAIT_BUDGET_NS = 4,
     QMCDU_OPT_TEST_STALL = 5,
-    QMCDU_OPT_MAX_CTAS = 6
+    QMCDU_OPT_MAX_CTAS = 6,
+    QMCDU_OPT_GROUP_CTAS = 7
 };
 int qmcdu_set_option(qmcdu_t h, int option, long long value);
 
@@ -261,6 +266,46 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value);
  * flush column tile.
  */
 int qmcdu_sweep_shape(qmcdu_t h, int *shape5);
+
+/*
+ * Walker subsets: walkers that join and leave a handle between sweeps
+ * (continuous batching in a serving loop). The paper runs one walker per
+ * process; these calls let one handle hold `batch` walker slots whose walkers
+ * advance at their own pace.
+ *
+ * qmcdu_footprint: device bytes a handle of these sizes allocates (every
+ * cudaMalloc of qmcdu_create, each rounded up to 512 bytes). Host only; needs
+ * no GPU. ERR_ARG for sizes qmcdu_create would refuse.
+ *
+ * qmcdu_load_walkers: walkers first..first+count-1 get new matrices and
+ * start afresh (empty delay queues), then A^{-1} and log|det A| are computed
+ * from them by the fp64 LU of qmcdu_recompute. A: host or device
+ * [count][N][N] fp64 row-major, copied; or NULL to draw each walker's matrix
+ * on the device from its key seeds[t] (host [count]): A_ij ~ N(0,1), Box-
+ * Muller pairs at Philox counters (i, 0, 2, pair), the draws of qmcdu_create's
+ * conventions above. Pending queues of the other walkers are flushed first.
+ * Asynchronous. ERR_ARG: range outside 0..batch, both A and seeds NULL.
+ *
+ * qmcdu_recompute_walkers: qmcdu_recompute for walkers first..first+count-1
+ * only; drift_out host or device [count][2] (log-det, inverse) or NULL.
+ *
+ * qmcdu_sweep_walkers: one Metropolis sweep (as qmcdu_sweep) of the `count`
+ * listed walkers only. walkers[t] (distinct slots in 0..batch-1) draws its
+ * proposals and uniforms from key seeds[t] and sweep number sweeps[t] (host
+ * arrays, read before the call returns); unlisted walkers are untouched.
+ * Outputs (host or device, each may be NULL) are compact, in list order:
+ * accepted_out [count][N] uint8, ratios_out [count][N] fp64, near_ties_out
+ * [count] int64; host outputs make the call synchronise. Needs persistent
+ * sweeps (ERR_STATE otherwise). ERR_ARG: bad or repeated index, negative
+ * sweep number, null arrays with count > 0.
+ */
+int qmcdu_footprint(int N, int K, int precision, int batch, unsigned long long *bytes);
+int qmcdu_load_walkers(qmcdu_t h, int first, int count, const double *A,
+                       const unsigned long long *seeds);
+int qmcdu_recompute_walkers(qmcdu_t h, int first, int count, double *drift_out);
+int qmcdu_sweep_walkers(qmcdu_t h, int count, const int *walkers, const unsigned long long *seeds,
+                        const int *sweeps, double sigma, unsigned char *accepted_out,
+                        double *ratios_out, long long *near_ties_out);
 
 /*
  * Determinant ratio of one proposed move for callers that cannot allocate
@@ -310,6 +355,105 @@ int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v, c
  */
 int qmcdu_gemm_bf16x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
                       int b_trans, float *C, int ldc, float alpha, float beta, void *stream);
+
+/*
+ * Serving loop (native, in the library). Requests for walkers of different
+ * electron counts arrive over time. Each is admitted, when a walker slot,
+ * device memory and the GPU's compute allow (the resident walkers' CTAs within
+ * `sm_oversubscription` times the SM count), into a size-class handle (a "pool" of `class_slots`
+ * slots, created while the pools held stay within `hbm_budget`; idle pools of
+ * other classes are destroyed to make room). Admission draws the walker's
+ * matrix from its key and computes A^{-1} and log|det A| by the fp64 LU on a
+ * second stream of the pool. Every pool sweeps the walkers it holds, one
+ * sweep each per round (qmcdu_sweep_walkers), on its own stream, several pools
+ * at once with their CTA shares summing to at most the SM count; walkers join
+ * between rounds (continuous batching) and leave after `nsweeps` sweeps and a
+ * final fp64 recompute. A walker's sweep s uses Philox key `seed` and sweep
+ * number s, and every pool of a class has the same walker-group shape, so a
+ * request's results are bit-identical alone and in any mix.
+ *
+ * The paper runs one walker per process and has no serving layer; this is the
+ * continuous-batching pattern applied to its delayed-update sweep.
+ */
+#define QMCDU_SERVER_MAX_CLASSES 16
+typedef struct qmcdu_server *qmcdu_server_t;
+
+typedef struct {
+    int precision;                  /* working precision of every walker */
+    int recompute_every;            /* fp64 recompute every R sweeps of a walker (0: only at the end) */
+    double sigma;                   /* proposal width: v = a_j + sigma g */
+    unsigned long long hbm_budget;  /* device bytes the pools may hold (qmcdu_footprint + outputs) */
+    int num_classes;                /* 1..QMCDU_SERVER_MAX_CLASSES */
+    int class_N[QMCDU_SERVER_MAX_CLASSES];      /* electrons of each class (requests match one) */
+    int class_K[QMCDU_SERVER_MAX_CLASSES];      /* delay K (0: min(N, 32)) */
+    int class_slots[QMCDU_SERVER_MAX_CLASSES];  /* walker slots per pool (0: 8) */
+    int class_group_ctas[QMCDU_SERVER_MAX_CLASSES]; /* CTAs per walker group (0: max(1, min(32, N/128))) */
+    int max_inflight;               /* pools sweeping at once (0: no cap but the SMs) */
+    int max_walkers;                /* walkers resident at once (0: no cap but slots and budget) */
+    int keep_traces;                /* 1: keep each request's accept masks and ratios (qmcdu_server_trace) */
+    int simulate;                   /* 1: no GPU work; a cost model on a virtual clock (tests of the scheduler) */
+    double sim_flops;               /* simulate: flush flop/s of the whole GPU (working precision) */
+    double sim_fp64_flops;          /* simulate: LU flop/s */
+    double sim_proposal_s;          /* simulate: latency of one proposal of a sweep */
+    double sm_oversubscription;     /* admission stops while the resident walkers' group CTAs,
+                                       summed, would pass this multiple of the SM count (0: 2;
+                                       < 0: no cap but slots and budget) */
+} qmcdu_server_config;
+
+typedef struct {
+    unsigned long long id;          /* caller's tag, returned in the result */
+    unsigned long long seed;        /* Philox key of the walker: its matrix and every draw */
+    int N;                          /* electrons; must be one of class_N */
+    int nsweeps;                    /* >= 1 */
+    double arrival_s;               /* arrival time on the server clock (s) */
+} qmcdu_request;
+
+typedef struct {
+    unsigned long long id;
+    int N, nsweeps;
+    int status;                     /* QMCDU_OK, ERR_OOM (can never fit the budget), or the pool's error */
+    int pool;                       /* pool that served it (-1 if none) */
+    double arrival_s, admit_s, done_s;
+    long long accepted, near_ties;
+    int recomputes;
+    int sign;                       /* of det A after the final recompute */
+    double logabs;                  /* log|det A| after the final recompute */
+    double drift_logdet, drift_inverse; /* largest drift of the running values at a recompute */
+    double sweep_ms_mean, sweep_ms_max; /* device time of the rounds that swept it */
+    long long first_round, last_round;  /* the pool's round numbers of its first and last sweep */
+} qmcdu_result;
+
+/*
+ * create: copies the configuration (validated: ERR_ARG). The server uses the
+ * current device. submit: queues requests (any arrival order; each is held
+ * until the clock passes its arrival_s); ERR_ARG for an N that is no class,
+ * nsweeps < 1. run: runs the loop until every submitted request has
+ * finished, or the server clock passes until_s (< 0: no limit); the clock
+ * starts at the first run (wall clock; virtual under `simulate`). Returns the
+ * first fatal CUDA error (ERR_CUDA, ERR_OOM), else QMCDU_OK. results: copies
+ * out up to `max` finished requests not returned before, in order of
+ * completion. trace (keep_traces): accept masks [nsweeps][N] and ratios
+ * [nsweeps][N] of a finished request (host; either may be NULL); ERR_ARG for
+ * an unknown id. stats: QMCDU_SERVER_STATS doubles, in order: clock (s),
+ * submitted, finished, failed, walker-sweeps, accepted updates, proposals,
+ * per-sweep latency p50 and p99 (ms, device time of the round per walker-
+ * sweep), request latency p50 and p99 (s, arrival to done), admission wait p50
+ * and p99 (s), peak bytes held, budget, pools created, pools destroyed,
+ * rounds, most walkers resident at once, most pools in flight at once,
+ * walker-sweeps in rounds that held walkers admitted at different times, clock
+ * at the last finished round (s). destroy: waits for the device work of the
+ * pools and frees them. Not thread-safe: one host thread drives a server.
+ */
+#define QMCDU_SERVER_STATS 22
+int qmcdu_server_create(const qmcdu_server_config *cfg, qmcdu_server_t *out);
+int qmcdu_server_submit(qmcdu_server_t s, const qmcdu_request *reqs, int n);
+int qmcdu_server_run(qmcdu_server_t s, double until_s);
+int qmcdu_server_results(qmcdu_server_t s, qmcdu_result *out, int max, int *count);
+int qmcdu_server_trace(qmcdu_server_t s, unsigned long long id, unsigned char *accepted,
+                       double *ratios);
+int qmcdu_server_stats(qmcdu_server_t s, double *out, int n);
+const char *qmcdu_server_error(qmcdu_server_t s);
+int qmcdu_server_destroy(qmcdu_server_t s);
 
 /* Library version string. */
 const char *qmcdu_version(void);

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "qmcdu_internal.cuh"
+#include "philox.cuh"
 
 namespace qmcdu {
 
@@ -240,6 +241,32 @@ __global__ void lu_finish_kernel(int batch, double *logabs, int *sign, const dou
     drift[4 * b + 3] = have_old ? sqrt(drift[4 * b + 0] / fmax(drift[4 * b + 1], 1e-300)) : 0.0;
     logabs[b] = lu_logabs[b];
     sign[b] = lu_sign[b];
+}
+
+// Initial matrices of walkers [w0, w0 + n) from their keys seeds[0..n): row i
+// of walker w0 + t holds the Gaussian pairs at Philox counters (i, 0, 2, q).
+__global__ void init_matrix_kernel(int N, int ld, int n, const unsigned long long *seeds, double *A)
+{
+    const int npair = (N + 1) / 2;
+    const long long per_w = (long long)N * npair, total = per_w * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / per_w);
+        const long long r = e - (long long)t * per_w;
+        const int i = (int)(r / npair), q = (int)(r - (long long)i * npair);
+        const double2 g = matrix_gaussian_pair(seeds[t], i, q);
+        double *row = A + ((size_t)t * N + i) * ld;
+        row[2 * q] = g.x;
+        if (2 * q + 1 < N) row[2 * q + 1] = g.y;
+    }
+}
+
+cudaError_t launch_init_matrix(Ctx &c, int w0, int n, const unsigned long long *seeds)
+{
+    if (n <= 0) return cudaSuccess;
+    init_matrix_kernel<<<c.num_sms * 8, 256, 0, c.stream>>>(c.N, c.ld, n, seeds,
+                                                           c.A + (size_t)w0 * c.N * c.ld);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_recompute(Ctx &c, int have_old)

@@ -70,6 +70,8 @@ struct SweepParams {
     int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm, off_bar;
     int kp;                         // tensor-core flush: K rounded up to 16 (<= 64)
     unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
+    const int *wlist;               // optional [nw]: the walkers this launch sweeps (else 0..nw)
+    int nw;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -578,7 +580,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 
     if (rank >= Gr) {
         // Helper CTA: take part in every flush of every walker of the group.
-        for (int w = grp; w < p.batch; w += p.ngroups) {
+        for (int t = grp; t < p.nw; t += p.ngroups) {
+            const int w = p.wlist ? __ldg(p.wlist + t) : t;
             for (;;) {
                 if (!group_wait_for(cmd, 2u * (n_event + 1), p.status, p.budget_ns, 128)) return;
                 const bool last = (ld_acquire(cmd) & 1u) != 0;
@@ -614,7 +617,9 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     const int L = max(0, min(chunk, N - i0));
     const int nj = 2 * K + 1;
 
-    for (int w = grp; w < p.batch; w += p.ngroups) {
+    for (int t = grp; t < p.nw; t += p.ngroups) {
+        const int w = p.wlist ? __ldg(p.wlist + t) : t;
+        const int orow = t;            // output row: walker w, or list entry t
         double *Aw = p.A + (size_t)w * wN;
         const T *Ainv = p.Ainv + (size_t)w * wN;
         const double *Gw = p.gauss + (size_t)w * wN;
@@ -741,9 +746,9 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     rr_s = r;
                     acc_s = a;
                     if (rank == 0) {
-                        p.acc_out[(size_t)w * N + j] = (unsigned char)a;
-                        p.ratio_out[(size_t)w * N + j] = r;
-                        if (fabs(prob - u) < 1e-10) p.ties[w] += 1;
+                        p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
+                        p.ratio_out[(size_t)orow * N + j] = r;
+                        if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
                         if (a) p.idx[(size_t)w * K + k] = j;
                     }
                 }
@@ -900,9 +905,10 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
 
 // Gaussians (Box-Muller pairs) and Metropolis uniforms of one sweep for every
 // walker, from the Philox counters of qmcdu_sweep.
-__global__ void sweep_draw_kernel(int N, int ld, int batch, unsigned long long seed, int sweep,
+__global__ void sweep_draw_kernel(int N, int ld, int nw, unsigned long long seed, int sweep,
                                   const unsigned long long *params, int sweep_offset,
-                                  double *gauss, double *unif)
+                                  const int *wlist, const unsigned long long *wseed,
+                                  const int *wsweep, double *gauss, double *unif)
 {
     if (params) {   // parameters in device memory (steps replayed from a CUDA graph)
         seed = params[0];
@@ -910,34 +916,38 @@ __global__ void sweep_draw_kernel(int N, int ld, int batch, unsigned long long s
     }
     const int npair = (N + 1) / 2;
     const long long per_w = (long long)N * npair;
-    const long long total = per_w * batch;
+    const long long total = per_w * nw;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int w = (int)(e / per_w);
-        const long long r = e - (long long)w * per_w;
+        const int t = (int)(e / per_w);
+        const long long r = e - (long long)t * per_w;
         const int j = (int)(r / npair), q = (int)(r - (long long)j * npair);
-        const unsigned long long ws = seed + (unsigned long long)w;
-        const double2 g = proposal_gaussian_pair(ws, j, sweep, q);
+        // walker t of the launch, or the listed walker with its own key and sweep
+        const int w = wlist ? wlist[t] : t;
+        const unsigned long long ws = wseed ? wseed[t] : seed + (unsigned long long)w;
+        const int sw = wsweep ? wsweep[t] : sweep;
+        const double2 g = proposal_gaussian_pair(ws, j, sw, q);
         double *row = gauss + ((size_t)w * N + j) * ld;
         row[2 * q] = g.x;
         if (2 * q + 1 < N) row[2 * q + 1] = g.y;
-        if (q == 0) unif[(size_t)w * N + j] = metropolis_uniform(ws, j, sweep);
+        if (q == 0) unif[(size_t)w * N + j] = metropolis_uniform(ws, j, sw);
     }
 }
 
 // log|det A| and sign after the sweep: one CTA per walker sums log|r| over the
 // accepted proposals in a fixed order.
-__global__ void sweep_logdet_kernel(int N, const unsigned char *acc, const double *ratio,
-                                    double *logabs, int *sign)
+__global__ void sweep_logdet_kernel(int N, const int *wlist, const unsigned char *acc,
+                                    const double *ratio, double *logabs, int *sign)
 {
-    const int w = blockIdx.x;
+    const int t = blockIdx.x;                 // output row
+    const int w = wlist ? wlist[t] : t;       // walker
     __shared__ double sred[STHREADS];
     __shared__ int sneg[STHREADS];
     double s = 0.0;
     int neg = 0;
     for (int j = threadIdx.x; j < N; j += STHREADS) {
-        if (acc[(size_t)w * N + j]) {
-            const double r = ratio[(size_t)w * N + j];
+        if (acc[(size_t)t * N + j]) {
+            const double r = ratio[(size_t)t * N + j];
             s += log(fabs(r));
             neg += r < 0.0;
         }
@@ -1002,7 +1012,8 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     int capacity = per_sm * c.num_sms;
     if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
     if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
-    const int ngroups = std::min(c.batch, std::max(1, capacity / Gf));
+    const int nw = L.wlist ? L.nlist : c.batch;
+    const int ngroups = std::min(nw, std::max(1, capacity / Gf));
     if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
     if ((size_t)ngroups * 2 * Gr * (2 * K + 1) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
 
@@ -1021,6 +1032,8 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.off_bar = offs[8];
     p.kp = (K + 15) / 16 * 16;
     p.phase_ns = c.prof ? c.sw_phase : nullptr;
+    p.wlist = L.wlist;
+    p.nw = nw;
     e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {&p};
@@ -1038,13 +1051,20 @@ template <typename T>
 static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
 {
     const int N = c.N, K = c.K;
+    const int nw = L.wlist ? L.nlist : c.batch;
     int Gf, Gr;
     const int sms = c.opt_max_ctas > 0 ? std::min(c.num_sms, c.opt_max_ctas) : c.num_sms;
-    if (c.batch >= sms) {
+    const int target_chunk = c.prec == QMCDU_FP64 ? 32 : 128;
+    if (c.opt_group_ctas > 0) {
+        // fixed walker-group shape: a walker's arithmetic does not depend on how
+        // many walkers share the launch
+        Gf = std::min(c.opt_group_ctas, sms);
+        Gr = c.opt_ratio_ctas > 0 ? c.opt_ratio_ctas : (N + target_chunk - 1) / target_chunk;
+        Gr = std::max(1, std::min(Gr, Gf));
+    } else if (nw >= sms) {
         Gf = Gr = 1;
     } else {
-        Gf = std::max(1, sms / c.batch);
-        const int target_chunk = c.prec == QMCDU_FP64 ? 32 : 128;
+        Gf = std::max(1, sms / nw);
         Gr = c.opt_ratio_ctas > 0 ? c.opt_ratio_ctas : (N + target_chunk - 1) / target_chunk;
         Gr = std::max(1, std::min(Gr, Gf));
         if (c.opt_flush_ctas > 0) Gf = std::max(Gr, std::min(Gf, c.opt_flush_ctas));
@@ -1066,8 +1086,11 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)
 {
     // the sweep's proposal draws, then the sweep, then the running log-det
-    sweep_draw_kernel<<<c.num_sms * 8, 256, 0, c.stream>>>(c.N, c.ld, c.batch, L.seed, L.sweep,
-                                                           L.params, L.sweep_offset, c.sw_gauss,
+    const int nw = L.wlist ? L.nlist : c.batch;
+    if (nw == 0) return cudaSuccess;
+    sweep_draw_kernel<<<c.num_sms * 8, 256, 0, c.stream>>>(c.N, c.ld, nw, L.seed, L.sweep,
+                                                           L.params, L.sweep_offset, L.wlist,
+                                                           L.wseed, L.wsweep, c.sw_gauss,
                                                            c.sw_unif);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1077,7 +1100,7 @@ cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)
     if (e != cudaSuccess) return e;
     e = prof_end(&c, c.ev_sweep);
     if (e != cudaSuccess) return e;
-    sweep_logdet_kernel<<<c.batch, STHREADS, 0, c.stream>>>(c.N, L.acc_out, L.ratio_out, c.logabs,
+    sweep_logdet_kernel<<<nw, STHREADS, 0, c.stream>>>(c.N, L.wlist, L.acc_out, L.ratio_out, c.logabs,
                                                             c.sign);
     return cudaGetLastError();
 }

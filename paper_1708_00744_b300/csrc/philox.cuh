@@ -43,13 +43,12 @@ __device__ __forceinline__ double metropolis_uniform(unsigned long long seed, in
     return uniform53(o.x0, o.x1);
 }
 
-// Gaussian pair (entries 2 blk and 2 blk + 1 of the proposal row of electron j,
-// sweep s) by the Box-Muller transform (Box and Muller, Ann. Math. Stat. 1958).
-__device__ __forceinline__ double2 proposal_gaussian_pair(unsigned long long seed, int j, int s,
-                                                          int blk)
+// Gaussian pair from the Philox output at counter (c0, c1, tag, blk) by the
+// Box-Muller transform (Box and Muller, Ann. Math. Stat. 1958).
+__device__ __forceinline__ double2 box_muller_pair(unsigned long long seed, uint32_t c0, uint32_t c1,
+                                                   uint32_t tag, uint32_t blk)
 {
-    u32x4 o = philox4x32_10(u32x4{(uint32_t)j, (uint32_t)s, TAG_PROPOSAL, (uint32_t)blk},
-                            (uint32_t)seed, (uint32_t)(seed >> 32));
+    u32x4 o = philox4x32_10(u32x4{c0, c1, tag, blk}, (uint32_t)seed, (uint32_t)(seed >> 32));
     const double u1 = uniform53(o.x0, o.x1);
     const double u2 = uniform53(o.x2, o.x3);
     const double rho = sqrt(-2.0 * log(1.0 - u1));
@@ -57,6 +56,19 @@ __device__ __forceinline__ double2 proposal_gaussian_pair(unsigned long long see
     double sn, cs;
     sincos(ang, &sn, &cs);
     return make_double2(rho * cs, rho * sn);
+}
+
+// Entries 2 blk and 2 blk + 1 of the proposal row of electron j, sweep s.
+__device__ __forceinline__ double2 proposal_gaussian_pair(unsigned long long seed, int j, int s,
+                                                          int blk)
+{
+    return box_muller_pair(seed, (uint32_t)j, (uint32_t)s, TAG_PROPOSAL, (uint32_t)blk);
+}
+
+// Entries 2 blk and 2 blk + 1 of row i of a walker's initial matrix, A_ij ~ N(0, 1).
+__device__ __forceinline__ double2 matrix_gaussian_pair(unsigned long long seed, int i, int blk)
+{
+    return box_muller_pair(seed, (uint32_t)i, 0u, TAG_MATRIX, (uint32_t)blk);
 }
 
 }  // namespace qmcdu

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "qmcdu_internal.cuh"
 
@@ -41,12 +42,82 @@ static int cuda_fail(Ctx *c, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
     } while (0)
 
+// Allocate and zero on the handle's stream (a plain cudaMemset runs on the
+// legacy default stream, which work on non-blocking streams does not wait for).
 template <typename P>
-static cudaError_t dalloc(P **p, size_t bytes)
+static cudaError_t dalloc(P **p, size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc((void **)p, bytes);
-    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, s);
+    return e;
+}
+
+// Every device allocation of a handle, in one list: with do_alloc false only
+// the bytes are summed (qmcdu_footprint), each rounded up to cudaMalloc's
+// 512-byte granule.
+static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
+{
+    const int N = c->N, K = c->K;
+    const size_t es = elem_size(c->prec);
+    const size_t B = c->batch, ld = c->ld, NN = (size_t)N * ld, KN = (size_t)K * ld;
+    cudaError_t e = cudaSuccess;
+    *total = 0;
+#define AL(ptr, bytes)                                                  \
+    do {                                                                \
+        const size_t b_ = (bytes);                                      \
+        *total += (std::max<size_t>(b_, 16) + 511) / 512 * 512;         \
+        if (do_alloc && e == cudaSuccess) e = dalloc(&(ptr), b_, c->stream); \
+    } while (0)
+    AL(c->A, B * NN * sizeof(double));
+    AL(c->Ainv, B * NN * es);
+    AL(c->P, B * KN * es);
+    AL(c->V, B * KN * es);
+    AL(c->vstash, B * ld * sizeof(double));
+    AL(c->Kinv, B * K * K * sizeof(double));
+    AL(c->idx, B * K * sizeof(int));
+    AL(c->kcount, B * sizeof(int));
+    AL(c->logabs, B * sizeof(double));
+    AL(c->sign, B * sizeof(int));
+    AL(c->rs, B * rs_stride(K) * sizeof(double));
+    AL(c->partial, B * c->nsplit * (2 * K + 1) * sizeof(double));
+    AL(c->arrive, B * sizeof(unsigned));
+    AL(c->acc, B);
+    AL(c->elec_d, B * sizeof(int));
+    AL(c->mask_d, B);
+    AL(c->status, sizeof(int));
+    if (K > 1) {
+        AL(c->Tbuf, B * KN * es);
+        AL(c->Wbuf, B * KN * es);
+    }
+    AL(c->work, B * NN * sizeof(double));
+    AL(c->piv, B * N * sizeof(int));
+    AL(c->colperm, B * N * sizeof(int));
+    AL(c->Lt, B * c->nb * ld * sizeof(double));
+    AL(c->R, B * c->nb * ld * sizeof(double));
+    AL(c->lu_logabs, B * sizeof(double));
+    AL(c->lu_sign, B * sizeof(int));
+    AL(c->drift, B * 4 * sizeof(double));
+    AL(c->sw_acc, B * N);
+    AL(c->sw_ratio, B * N * sizeof(double));
+    AL(c->sw_ties, B * sizeof(long long));
+    AL(c->sw_override, B * N);
+    {
+        const size_t cap = (size_t)c->num_sms * 8;   // 256-thread CTAs resident per GPU, at most
+        c->sw_partial_len = cap * 2 * (2 * K + 1);
+        c->sync_words = (int)(cap * 96);
+        AL(c->sw_partial, c->sw_partial_len * sizeof(double));
+        AL(c->sw_sync, cap * 96 * sizeof(unsigned));
+        AL(c->sw_phase, 8 * sizeof(unsigned long long));
+        AL(c->sw_gauss, B * NN * sizeof(double));
+        AL(c->sw_unif, B * N * sizeof(double));
+        AL(c->d_params, 2 * sizeof(unsigned long long));
+        AL(c->d_wlist, B * sizeof(int));
+        AL(c->d_wseed, B * sizeof(unsigned long long));
+        AL(c->d_wsweep, B * sizeof(int));
+        AL(c->d_lseed, B * sizeof(unsigned long long));
+    }
+#undef AL
     return e;
 }
 
@@ -60,7 +131,8 @@ static void release(Ctx *c)
                     c->sw_unif};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties};
+    void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
+                    c->d_wseed, c->d_wsweep, c->d_lseed};
     for (void *p : more)
         if (p) cudaFree(p);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -167,7 +239,7 @@ static void drop_events(Ctx *c)
 }
 
 int copy_sweep_outputs(Ctx *c, unsigned char *accepted_out, double *ratios_out,
-                       long long *near_ties_out);
+                       long long *near_ties_out, int rows = -1);
 
 static int flush_all(Ctx *c)
 {
@@ -212,55 +284,10 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
         c->num_sms = 148;
     c->nsplit = (N + 255) / 256;
     c->nb = choose_panel_width(N);
-    const size_t es = elem_size(precision);
-    const size_t B = batch, ld = c->ld, NN = (size_t)N * ld, KN = (size_t)K * ld;
-    cudaError_t e = cudaSuccess;
-#define AL(ptr, bytes) if (e == cudaSuccess) e = dalloc(&(ptr), (bytes))
-    AL(c->A, B * NN * sizeof(double));
-    AL(c->Ainv, B * NN * es);
-    AL(c->P, B * KN * es);
-    AL(c->V, B * KN * es);
-    AL(c->vstash, B * ld * sizeof(double));
-    AL(c->Kinv, B * K * K * sizeof(double));
-    AL(c->idx, B * K * sizeof(int));
-    AL(c->kcount, B * sizeof(int));
-    AL(c->logabs, B * sizeof(double));
-    AL(c->sign, B * sizeof(int));
-    AL(c->rs, B * rs_stride(K) * sizeof(double));
-    AL(c->partial, B * c->nsplit * (2 * K + 1) * sizeof(double));
-    AL(c->arrive, B * sizeof(unsigned));
-    AL(c->acc, B);
-    AL(c->elec_d, B * sizeof(int));
-    AL(c->mask_d, B);
-    AL(c->status, sizeof(int));
-    if (K > 1) {
-        AL(c->Tbuf, B * KN * es);
-        AL(c->Wbuf, B * KN * es);
-    }
-    AL(c->work, B * NN * sizeof(double));
-    AL(c->piv, B * N * sizeof(int));
-    AL(c->colperm, B * N * sizeof(int));
-    AL(c->Lt, B * c->nb * ld * sizeof(double));
-    AL(c->R, B * c->nb * ld * sizeof(double));
-    AL(c->lu_logabs, B * sizeof(double));
-    AL(c->lu_sign, B * sizeof(int));
-    AL(c->drift, B * 4 * sizeof(double));
-    AL(c->sw_acc, B * N);
-    AL(c->sw_ratio, B * N * sizeof(double));
-    AL(c->sw_ties, B * sizeof(long long));
-    AL(c->sw_override, B * N);
-    {
-        const size_t cap = (size_t)c->num_sms * 8;   // 256-thread CTAs resident per GPU, at most
-        c->sw_partial_len = cap * 2 * (2 * K + 1);
-        c->sync_words = (int)(cap * 96);
-        AL(c->sw_partial, c->sw_partial_len * sizeof(double));
-        AL(c->sw_sync, cap * 96 * sizeof(unsigned));
-        AL(c->sw_phase, 8 * sizeof(unsigned long long));
-        AL(c->sw_gauss, B * NN * sizeof(double));
-        AL(c->sw_unif, B * N * sizeof(double));
-        AL(c->d_params, 2 * sizeof(unsigned long long));
-    }
-#undef AL
+    size_t total = 0;
+    cudaError_t e = alloc_state(c, true, &total);
+    // the zeroing is complete when create returns: any stream may use the handle
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         release(c);
@@ -530,9 +557,9 @@ static int ensure_step_buffers(Ctx *c, int nsweeps)
     c->step_acc = nullptr; c->step_ratio = nullptr; c->step_ties = nullptr;
     c->step_cap = 0;
     const size_t BN = (size_t)c->batch * c->N;
-    CK(dalloc(&c->step_acc, (size_t)nsweeps * BN));
-    CK(dalloc(&c->step_ratio, (size_t)nsweeps * BN * sizeof(double)));
-    CK(dalloc(&c->step_ties, (size_t)nsweeps * c->batch * sizeof(long long)));
+    CK(dalloc(&c->step_acc, (size_t)nsweeps * BN, c->stream));
+    CK(dalloc(&c->step_ratio, (size_t)nsweeps * BN * sizeof(double), c->stream));
+    CK(dalloc(&c->step_ties, (size_t)nsweeps * c->batch * sizeof(long long), c->stream));
     c->step_cap = nsweeps;
     return QMCDU_OK;
 }
@@ -830,9 +857,160 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value)
     case QMCDU_OPT_WAIT_BUDGET_NS: c->opt_budget_ns = value ? value : 2000000000LL; break;
     case QMCDU_OPT_TEST_STALL: c->opt_stall = value ? 1 : 0; break;
     case QMCDU_OPT_MAX_CTAS: c->opt_max_ctas = (int)std::min(value, 1LL << 20); break;
+    case QMCDU_OPT_GROUP_CTAS: c->opt_group_ctas = (int)std::min(value, 1LL << 20); break;
     default: return fail(c, QMCDU_ERR_ARG, "unknown option%s");
     }
     return QMCDU_OK;
+}
+
+// ---- walker subsets (serving: walkers join and leave between sweeps)
+
+int qmcdu_footprint(int N, int K, int precision, int batch, unsigned long long *bytes)
+{
+    if (!bytes || N < 1 || N > QMCDU_MAX_N || K < 1 || K > QMCDU_MAX_K || K > N || batch < 1 ||
+        batch > 65535 || precision < QMCDU_FP64 || precision > QMCDU_FP32_BF16X3)
+        return QMCDU_ERR_ARG;
+    Ctx c;
+    c.N = N; c.K = K; c.prec = precision; c.batch = batch; c.ld = padded_ld(N);
+    c.nsplit = (N + 255) / 256;
+    c.nb = choose_panel_width(N);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        c.num_sms = sms;
+    else
+        cudaGetLastError();      // no device: size the sweep scratch for 148 SMs
+    size_t total = 0;
+    alloc_state(&c, false, &total);
+    *bytes = total;
+    return QMCDU_OK;
+}
+
+// The handle restricted to walkers [w0, w0 + n) for the recompute kernels:
+// device pointers offset, no host state.
+static void range_view(const Ctx &c, int w0, int n, Ctx &v)
+{
+    const size_t wN = (size_t)c.N * c.ld, w = (size_t)w0;
+    v.N = c.N; v.K = c.K; v.prec = c.prec; v.batch = n; v.ld = c.ld;
+    v.stream = c.stream; v.device = c.device; v.num_sms = c.num_sms;
+    v.nb = c.nb; v.nsplit = c.nsplit; v.status = c.status;
+    v.A = c.A + w * wN;
+    v.Ainv = (char *)c.Ainv + w * wN * elem_size(c.prec);
+    v.work = c.work + w * wN;
+    v.piv = c.piv + w * c.N;
+    v.colperm = c.colperm + w * c.N;
+    v.Lt = c.Lt + w * c.nb * c.ld;
+    v.R = c.R + w * c.nb * c.ld;
+    v.lu_logabs = c.lu_logabs + w;
+    v.lu_sign = c.lu_sign + w;
+    v.drift = c.drift + 4 * w;
+    v.logabs = c.logabs + w;
+    v.sign = c.sign + w;
+}
+
+static int recompute_range(Ctx *c, int first, int count, int have_old)
+{
+    Ctx v;
+    range_view(*c, first, count, v);
+    CK(prof_begin(c, c->ev_recompute));
+    CK(launch_recompute(v, have_old));
+    CK(prof_end(c, c->ev_recompute));
+    c->n_launch += 5 + 2 * ((c->N + c->nb - 1) / c->nb);
+    c->n_recompute += 1;
+    return QMCDU_OK;
+}
+
+int qmcdu_load_walkers(qmcdu_t h, int first, int count, const double *A,
+                       const unsigned long long *seeds)
+{
+    if (!h || first < 0 || count < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if ((long long)first + count > c->batch) return fail(c, QMCDU_ERR_ARG, "walker range out of bounds%s");
+    if (count == 0) return QMCDU_OK;
+    if (!A && !seeds) return fail(c, QMCDU_ERR_ARG, "need matrices or seeds%s");
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    const size_t N = c->N, ld = c->ld;
+    if (A) {
+        CK(cudaMemcpy2DAsync(c->A + (size_t)first * N * ld, ld * sizeof(double), A,
+                             N * sizeof(double), N * sizeof(double), N * count, cudaMemcpyDefault,
+                             c->stream));
+    } else {
+        // staged through pageable memory: the caller's array may change on return
+        std::vector<unsigned long long> hs(seeds, seeds + count);
+        CK(cudaMemcpyAsync(c->d_lseed, hs.data(), count * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(launch_init_matrix(*c, first, count, c->d_lseed));
+        c->n_launch += 1;
+    }
+    CK(cudaMemsetAsync(c->kcount + first, 0, count * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->arrive + first, 0, count * sizeof(unsigned), c->stream));
+    return recompute_range(c, first, count, 0);
+}
+
+int qmcdu_recompute_walkers(qmcdu_t h, int first, int count, double *drift_out)
+{
+    if (!h || first < 0 || count < 0) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if ((long long)first + count > c->batch) return fail(c, QMCDU_ERR_ARG, "walker range out of bounds%s");
+    if (count == 0) return QMCDU_OK;
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    st = recompute_range(c, first, count, 1);
+    if (st) return st;
+    if (drift_out) {
+        CK(cudaMemcpy2DAsync(drift_out, 2 * sizeof(double), c->drift + 4 * (size_t)first + 2,
+                             4 * sizeof(double), 2 * sizeof(double), count, cudaMemcpyDefault,
+                             c->stream));
+        if (!is_device_ptr(drift_out)) return read_status(c);
+    }
+    return QMCDU_OK;
+}
+
+int qmcdu_sweep_walkers(qmcdu_t h, int count, const int *walkers, const unsigned long long *seeds,
+                        const int *sweeps, double sigma, unsigned char *accepted_out,
+                        double *ratios_out, long long *near_ties_out)
+{
+    if (!h || count < 0 || (count > 0 && (!walkers || !seeds || !sweeps))) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    if (!c->opt_persistent)
+        return fail(c, QMCDU_ERR_STATE, "walker subsets need the persistent sweep%s");
+    if (count > c->batch) return fail(c, QMCDU_ERR_ARG, "more walkers listed than the handle holds%s");
+    std::vector<unsigned char> seen(c->batch, 0);
+    for (int t = 0; t < count; ++t) {
+        if (walkers[t] < 0 || walkers[t] >= c->batch || seen[walkers[t]])
+            return fail(c, QMCDU_ERR_ARG, "walker list has an index out of range or twice%s");
+        if (sweeps[t] < 0) return fail(c, QMCDU_ERR_ARG, "negative sweep number%s");
+        seen[walkers[t]] = 1;
+    }
+    if (count == 0) return QMCDU_OK;
+    int st = flush_all(c);
+    if (st) return st;
+    c->pending = false;
+    // staged through pageable memory: the caller's arrays may change on return
+    std::vector<int> hl(walkers, walkers + count), hw(sweeps, sweeps + count);
+    std::vector<unsigned long long> hs(seeds, seeds + count);
+    CK(cudaMemcpyAsync(c->d_wlist, hl.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_wseed, hs.data(), count * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_wsweep, hw.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->sw_ties, 0, count * sizeof(long long), c->stream));
+    SweepLaunch S{};
+    S.sigma = sigma;
+    S.acc_out = c->sw_acc;
+    S.ratio_out = c->sw_ratio;
+    S.ties = c->sw_ties;
+    S.wlist = c->d_wlist;
+    S.nlist = count;
+    S.wseed = c->d_wseed;
+    S.wsweep = c->d_wsweep;
+    CK(launch_sweep(*c, S));
+    c->n_launch += 3;
+    c->opt_stall = 0;
+    CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
+    return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out, count);
 }
 
 int qmcdu_sweep_shape(qmcdu_t h, int *shape5)
@@ -847,21 +1025,22 @@ int qmcdu_sweep_shape(qmcdu_t h, int *shape5)
 
 namespace qmcdu {
 int copy_sweep_outputs(Ctx *c, unsigned char *accepted_out, double *ratios_out,
-                       long long *near_ties_out)
+                       long long *near_ties_out, int rows)
 {
     const int N = c->N;
+    const size_t R = rows < 0 ? (size_t)c->batch : (size_t)rows;
     bool host_out = false;
     if (accepted_out) {
-        CK(cudaMemcpyAsync(accepted_out, c->sw_acc, (size_t)c->batch * N, cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(accepted_out, c->sw_acc, R * N, cudaMemcpyDefault, c->stream));
         host_out |= !is_device_ptr(accepted_out);
     }
     if (ratios_out) {
-        CK(cudaMemcpyAsync(ratios_out, c->sw_ratio, (size_t)c->batch * N * sizeof(double),
-                           cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(ratios_out, c->sw_ratio, R * N * sizeof(double), cudaMemcpyDefault,
+                           c->stream));
         host_out |= !is_device_ptr(ratios_out);
     }
     if (near_ties_out) {
-        CK(cudaMemcpyAsync(near_ties_out, c->sw_ties, c->batch * sizeof(long long), cudaMemcpyDefault,
+        CK(cudaMemcpyAsync(near_ties_out, c->sw_ties, R * sizeof(long long), cudaMemcpyDefault,
                            c->stream));
         host_out |= !is_device_ptr(near_ties_out);
     }
@@ -898,7 +1077,8 @@ int qmcdu_profile_enable(qmcdu_t h, int enable)
     drop_events(c);
     c->prof = enable != 0;
     c->n_launch = c->n_flush = c->n_recompute = c->n_sync = c->n_ratio = c->n_accept = 0;
-    CK(cudaMemset(c->sw_phase, 0, 8 * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(c->sw_phase, 0, 8 * sizeof(unsigned long long), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return QMCDU_OK;
 }
 
@@ -924,7 +1104,8 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n)
         ms_rec += ms;
     }
     unsigned long long ph[8];
-    CK(cudaMemcpy(ph, c->sw_phase, sizeof ph, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(ph, c->sw_phase, sizeof ph, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     const double vals[18] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
                              (double)c->n_recompute, ms_rec, (double)c->n_sync,
                              (double)c->n_ratio, (double)c->n_accept,
@@ -945,3 +1126,19 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
 }
 
 }  // extern "C"
+
+namespace qmcdu {
+// qmcdu_load_walkers on another stream than the handle's (the serving loop's
+// admission stream): the loaded walkers' kernels touch only their own slots
+// and the seed buffer of loads, so they may overlap sweeps of other walkers.
+int load_walkers_on(qmcdu_t h, cudaStream_t s, int first, int count,
+                    const unsigned long long *seeds)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    cudaStream_t keep = c->stream;
+    c->stream = s;
+    const int st = qmcdu_load_walkers(h, first, count, nullptr, seeds);
+    c->stream = keep;
+    return st;
+}
+}  // namespace qmcdu

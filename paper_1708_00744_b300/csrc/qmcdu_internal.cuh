@@ -95,6 +95,12 @@ struct Ctx {
     long long opt_budget_ns = 2000000000LL;
     int opt_stall = 0;
     int opt_max_ctas = 0;            // cap on the persistent sweep's grid (0: whole GPU)
+    int opt_group_ctas = 0;          // fixed CTAs per walker group (0: from the batch)
+    // walker subsets (qmcdu_sweep_walkers): list, keys and sweep numbers
+    int *d_wlist = nullptr;
+    unsigned long long *d_wseed = nullptr;
+    int *d_wsweep = nullptr;
+    unsigned long long *d_lseed = nullptr;   // keys of qmcdu_load_walkers' draws
     // qmcdu_step: device parameter block and per-sweep outputs, graph cache
     unsigned long long *d_params = nullptr;   // [0] base seed, [1] first sweep index
     unsigned char *step_acc = nullptr;        // nsweeps x batch x N
@@ -116,6 +122,12 @@ struct SweepLaunch {
     unsigned char *acc_out;
     double *ratio_out;
     long long *ties;
+    // optional subset of walkers (device arrays of nlist entries): walker
+    // wlist[t] draws from key wseed[t] and sweep number wsweep[t]
+    const int *wlist;
+    int nlist;
+    const unsigned long long *wseed;
+    const int *wsweep;
 };
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L);
 cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
@@ -157,6 +169,7 @@ cudaError_t launch_flush(Ctx &c, int kthresh);
 
 // ---- recompute (kernels_recompute.cu) ----
 cudaError_t launch_recompute(Ctx &c, int have_old_inverse);
+cudaError_t launch_init_matrix(Ctx &c, int w0, int n, const unsigned long long *seeds);
 cudaError_t launch_gj_update(Ctx &c, int nbe);
 int choose_panel_width(int N);
 
@@ -172,5 +185,9 @@ cudaError_t launch_philox_fill(const unsigned *c0, const unsigned *c1, const uns
                                const unsigned *c3, int n, unsigned long long seed,
                                unsigned *out, cudaStream_t s);
 cudaError_t launch_inverse_export(Ctx &c, double *dst);
+
+// qmcdu_load_walkers (drawn matrices) on stream s instead of the handle's.
+int load_walkers_on(qmcdu_t h, cudaStream_t s, int first, int count,
+                    const unsigned long long *seeds);
 
 }  // namespace qmcdu

@@ -35,7 +35,8 @@ import numpy as np
 __all__ = [
     "philox4x32_10", "uniform_from_words", "gaussian_pairs",
     "metropolis_uniforms", "proposal_gaussians", "initial_matrix",
-    "walker_seed", "TAG_UNIFORM", "TAG_PROPOSAL", "TAG_MATRIX",
+    "walker_seed", "serving_trace", "SERVING_SIZES", "TAG_UNIFORM", "TAG_PROPOSAL",
+    "TAG_MATRIX",
 ]
 
 TAG_UNIFORM = 0
@@ -125,3 +126,27 @@ def initial_matrix(seed: int, n: int) -> np.ndarray:
 
 def walker_seed(base_seed: int, walker: int) -> int:
     return (int(base_seed) + int(walker)) & 0xFFFFFFFFFFFFFFFF
+
+
+# Electron counts of the serving workload: a geometric set, drawn uniformly
+# (log-uniform in N), spanning the paper's sizes (hundreds to thousands).
+SERVING_SIZES = (128, 256, 512, 1024, 2048, 4096)
+
+
+def serving_trace(seed: int, rate_hz: float, duration_s: float, sizes=SERVING_SIZES,
+                  nsweeps: int = 20, max_requests: int | None = None):
+    """Poisson stream of walker requests: exponential inter-arrival times of
+    mean 1/rate_hz over [0, duration_s), N uniform over `sizes`, and request i
+    carries walker key walker_seed(10**6 * (seed + 1), i). Uses numpy's PCG64
+    generator seeded with `seed` (the arrival process is an input, not a step
+    of the method)."""
+    rng = np.random.default_rng(seed)
+    out, t, i = [], 0.0, 0
+    base = 10**6 * (int(seed) + 1)
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s or (max_requests is not None and i >= max_requests):
+            return out
+        out.append(dict(id=i, seed=walker_seed(base, i), N=int(rng.choice(sizes)),
+                        nsweeps=int(nsweeps), arrival_s=float(t)))
+        i += 1

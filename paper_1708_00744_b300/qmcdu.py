@@ -52,6 +52,18 @@ SIGNATURES = {
     "qmcdu_ratio_noalloc": (_I, [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "qmcdu_gemm_bf16x3": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _I, _VP, _I, ctypes.c_float,
                                ctypes.c_float, _VP]),
+    "qmcdu_footprint": (_I, [_I, _I, _I, _I, ctypes.POINTER(_ULL)]),
+    "qmcdu_load_walkers": (_I, [_VP, _I, _I, _VP, _VP]),
+    "qmcdu_recompute_walkers": (_I, [_VP, _I, _I, _VP]),
+    "qmcdu_sweep_walkers": (_I, [_VP, _I, _VP, _VP, _VP, _D, _VP, _VP, _VP]),
+    "qmcdu_server_create": (_I, [_VP, ctypes.POINTER(_VP)]),
+    "qmcdu_server_submit": (_I, [_VP, _VP, _I]),
+    "qmcdu_server_run": (_I, [_VP, _D]),
+    "qmcdu_server_results": (_I, [_VP, _VP, _I, ctypes.POINTER(_I)]),
+    "qmcdu_server_trace": (_I, [_VP, _ULL, _VP, _VP]),
+    "qmcdu_server_stats": (_I, [_VP, _VP, _I]),
+    "qmcdu_server_error": (ctypes.c_char_p, [_VP]),
+    "qmcdu_server_destroy": (_I, [_VP]),
     "qmcdu_version": (ctypes.c_char_p, []),
 }
 
@@ -286,7 +298,7 @@ def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
 
 
 OPTIONS = {"sweep_persistent": 1, "ratio_ctas": 2, "flush_ctas": 3, "wait_budget_ns": 4,
-           "test_stall": 5, "max_ctas": 6}
+           "test_stall": 5, "max_ctas": 6, "group_ctas": 7}
 
 
 def qmcdu_set_option(h, option, value):
@@ -313,6 +325,191 @@ def qmcdu_profile_read(h):
     out = np.zeros(len(PROFILE_FIELDS))
     _check("qmcdu_profile_read", load().qmcdu_profile_read(h, _ptr(out), out.size), h)
     return dict(zip(PROFILE_FIELDS, out.tolist()))
+
+
+# ---------------------------------------------------------------- walker subsets
+def qmcdu_footprint(N, K, precision, batch):
+    """Device bytes a handle of these sizes allocates (host only, no GPU needed)."""
+    out = _ULL()
+    _check("qmcdu_footprint", load().qmcdu_footprint(N, K, PRECISIONS.get(precision, precision),
+                                                     batch, ctypes.byref(out)))
+    return out.value
+
+
+def qmcdu_load_walkers(h, first, count, N, A=None, seeds=None):
+    if A is not None:
+        _need(A, count * N * N, "float64", "A", False)
+    if seeds is not None:
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        _need(seeds, count, "uint64", "seeds", False)
+    _check("qmcdu_load_walkers", load().qmcdu_load_walkers(h, first, count, _ptr(A), _ptr(seeds)), h)
+
+
+def qmcdu_recompute_walkers(h, first, count, drift_out=None):
+    _need(drift_out, 2 * count, "float64", "drift_out", False)
+    _check("qmcdu_recompute_walkers",
+           load().qmcdu_recompute_walkers(h, first, count, _ptr(drift_out)), h)
+
+
+def qmcdu_sweep_walkers(h, walkers, seeds, sweeps, sigma, N, accepted_out=None, ratios_out=None,
+                        near_ties_out=None):
+    walkers = np.ascontiguousarray(walkers, dtype=np.int32)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    sweeps = np.ascontiguousarray(sweeps, dtype=np.int32)
+    n = walkers.size
+    if seeds.size != n or sweeps.size != n:
+        raise ValueError("walkers, seeds and sweeps must have the same length")
+    _need(accepted_out, n * N, "uint8", "accepted_out", False)
+    _need(ratios_out, n * N, "float64", "ratios_out", False)
+    _need(near_ties_out, n, "int64", "near_ties_out", False)
+    _check("qmcdu_sweep_walkers",
+           load().qmcdu_sweep_walkers(h, n, _ptr(walkers), _ptr(seeds), _ptr(sweeps), sigma,
+                                      _ptr(accepted_out), _ptr(ratios_out), _ptr(near_ties_out)),
+           h)
+
+
+# ---------------------------------------------------------------- serving loop
+SERVER_MAX_CLASSES = 16
+_IARR = ctypes.c_int * SERVER_MAX_CLASSES
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("precision", _I), ("recompute_every", _I), ("sigma", _D),
+                ("hbm_budget", _ULL), ("num_classes", _I), ("class_N", _IARR),
+                ("class_K", _IARR), ("class_slots", _IARR), ("class_group_ctas", _IARR),
+                ("max_inflight", _I), ("max_walkers", _I), ("keep_traces", _I),
+                ("simulate", _I), ("sim_flops", _D), ("sim_fp64_flops", _D),
+                ("sim_proposal_s", _D), ("sm_oversubscription", _D)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("id", _ULL), ("seed", _ULL), ("N", _I), ("nsweeps", _I), ("arrival_s", _D)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", _ULL), ("N", _I), ("nsweeps", _I), ("status", _I), ("pool", _I),
+                ("arrival_s", _D), ("admit_s", _D), ("done_s", _D), ("accepted", ctypes.c_longlong),
+                ("near_ties", ctypes.c_longlong), ("recomputes", _I), ("sign", _I),
+                ("logabs", _D), ("drift_logdet", _D), ("drift_inverse", _D),
+                ("sweep_ms_mean", _D), ("sweep_ms_max", _D), ("first_round", ctypes.c_longlong),
+                ("last_round", ctypes.c_longlong)]
+
+
+SERVER_STATS = ("clock_s", "submitted", "finished", "failed", "walker_sweeps", "accepted",
+                "proposals", "sweep_ms_p50", "sweep_ms_p99", "request_s_p50", "request_s_p99",
+                "wait_s_p50", "wait_s_p99", "peak_bytes", "budget_bytes", "pools_created",
+                "pools_destroyed", "rounds", "max_resident", "max_inflight",
+                "mixed_walker_sweeps", "last_round_end_s")
+
+
+def _server_check(name, status, s):
+    if status != 0:
+        raise QmcduError(name, status, load().qmcdu_server_error(s).decode() if s else "")
+
+
+def qmcdu_server_create(cfg):
+    s = _VP()
+    _server_check("qmcdu_server_create", load().qmcdu_server_create(ctypes.byref(cfg), ctypes.byref(s)),
+                  None)
+    return s.value
+
+
+def qmcdu_server_submit(s, reqs):
+    arr = (Request * len(reqs))(*reqs)
+    _server_check("qmcdu_server_submit", load().qmcdu_server_submit(s, ctypes.addressof(arr), len(reqs)), s)
+
+
+def qmcdu_server_run(s, until_s=-1.0):
+    _server_check("qmcdu_server_run", load().qmcdu_server_run(s, until_s), s)
+
+
+def qmcdu_server_results(s, max_results=4096):
+    arr = (Result * max_results)()
+    n = _I()
+    _server_check("qmcdu_server_results",
+                  load().qmcdu_server_results(s, ctypes.addressof(arr), max_results, ctypes.byref(n)), s)
+    return [{f: getattr(arr[i], f) for f, _ in Result._fields_} for i in range(n.value)]
+
+
+def qmcdu_server_trace(s, req_id, nsweeps, N):
+    acc = np.zeros((nsweeps, N), dtype=np.uint8)
+    rat = np.zeros((nsweeps, N))
+    _server_check("qmcdu_server_trace", load().qmcdu_server_trace(s, req_id, _ptr(acc), _ptr(rat)), s)
+    return acc, rat
+
+
+def qmcdu_server_stats(s):
+    out = np.zeros(len(SERVER_STATS))
+    _server_check("qmcdu_server_stats", load().qmcdu_server_stats(s, _ptr(out), out.size), s)
+    return dict(zip(SERVER_STATS, out.tolist()))
+
+
+def qmcdu_server_destroy(s):
+    _server_check("qmcdu_server_destroy", load().qmcdu_server_destroy(s), None)
+
+
+class Server:
+    """The library's serving loop (qmcdu_server_*).
+
+    classes: list of dicts with N and optionally K, slots, group_ctas.
+    """
+
+    def __init__(self, classes, precision="fp32", sigma=0.1, recompute_every=10,
+                 hbm_budget=150 * 10**9, max_inflight=0, max_walkers=0, keep_traces=False,
+                 simulate=False, sim_flops=10e12, sim_fp64_flops=0.3e12, sim_proposal_s=10e-6,
+                 sm_oversubscription=0.0):
+        if not 1 <= len(classes) <= SERVER_MAX_CLASSES:
+            raise ValueError("1..%d size classes" % SERVER_MAX_CLASSES)
+        cfg = ServerConfig()
+        cfg.precision = PRECISIONS.get(precision, precision)
+        cfg.recompute_every = recompute_every
+        cfg.sigma = sigma
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.num_classes = len(classes)
+        for i, c in enumerate(classes):
+            cfg.class_N[i] = c["N"]
+            cfg.class_K[i] = c.get("K", 0)
+            cfg.class_slots[i] = c.get("slots", 0)
+            cfg.class_group_ctas[i] = c.get("group_ctas", 0)
+        cfg.max_inflight, cfg.max_walkers = max_inflight, max_walkers
+        cfg.keep_traces, cfg.simulate = int(bool(keep_traces)), int(bool(simulate))
+        cfg.sim_flops, cfg.sim_fp64_flops, cfg.sim_proposal_s = sim_flops, sim_fp64_flops, sim_proposal_s
+        cfg.sm_oversubscription = sm_oversubscription
+        self.s = qmcdu_server_create(cfg)
+
+    def submit(self, requests):
+        """requests: iterable of dicts with id, seed, N, nsweeps, arrival_s."""
+        qmcdu_server_submit(self.s, [Request(int(r["id"]), int(r["seed"]), int(r["N"]),
+                                             int(r["nsweeps"]), float(r["arrival_s"]))
+                                     for r in requests])
+
+    def run(self, until_s=-1.0):
+        qmcdu_server_run(self.s, until_s)
+
+    def results(self, max_results=4096):
+        out = []
+        while True:
+            got = qmcdu_server_results(self.s, max_results)
+            out += got
+            if len(got) < max_results:
+                return out
+
+    def trace(self, req_id, nsweeps, N):
+        return qmcdu_server_trace(self.s, req_id, nsweeps, N)
+
+    def stats(self):
+        return qmcdu_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            qmcdu_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- handle object
@@ -392,6 +589,17 @@ class Walkers:
 
     def sweep_shape(self):
         return qmcdu_sweep_shape(self.h)
+
+    def load_walkers(self, first, count, A=None, seeds=None):
+        qmcdu_load_walkers(self.h, first, count, self.N, A, seeds)
+
+    def recompute_walkers(self, first, count, drift_out=None):
+        qmcdu_recompute_walkers(self.h, first, count, drift_out)
+
+    def sweep_walkers(self, walkers, seeds, sweeps, sigma, accepted_out=None, ratios_out=None,
+                      near_ties_out=None):
+        qmcdu_sweep_walkers(self.h, walkers, seeds, sweeps, sigma, self.N, accepted_out,
+                            ratios_out, near_ties_out)
 
     def profile_enable(self, enable=True):
         qmcdu_profile_enable(self.h, enable)
