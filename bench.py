@@ -357,35 +357,28 @@ def run_ours(a, rank, world, local_rank):
         W1.close()
         k1 = (ms1, acc1)
 
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    res = dict(ms=ms, total_ms=allmax(sum(ms)), accepted=allsum(accepted), prof=prof, clocks=clk,
-               graph_ms=allmax(sum(msg)), graph_accepted=allsum(accg),
-               e2e_s=allmax(sum(e2e_s)), e2e_acc=allsum(e2e_acc), h2d=h2d, d2h=d2h,
+    # end-of-run reduction over ranks (the only collective): sums of counts,
+    # max of times
+    from paper_1708_00744_b300.shard import reduce_counters
+    red = reduce_counters({"total_ms": sum(ms), "accepted": accepted, "graph_ms": sum(msg),
+                           "graph_accepted": accg, "e2e_s": sum(e2e_s), "e2e_acc": e2e_acc,
+                           "k1_ms": sum(k1[0]) if k1 else 0.0,
+                           "k1_accepted": k1[1] if k1 else 0})
+    res = dict(ms=ms, total_ms=red["total_ms"], accepted=red["accepted"], prof=prof, clocks=clk,
+               graph_ms=red["graph_ms"], graph_accepted=red["graph_accepted"],
+               e2e_s=red["e2e_s"], e2e_acc=red["e2e_acc"], h2d=h2d, d2h=d2h,
                nprop=nprop, tuned=tuned, k1=None)
     if k1 is not None:
-        res["k1"] = dict(ms=allmax(sum(k1[0])), accepted=allsum(k1[1]))
+        res["k1"] = dict(ms=red["k1_ms"], accepted=red["k1_accepted"])
     return res
 
 
 # ------------------------------------------------------------------ serving
-def serve_once(a, trace, plain, window, budget):
-    """One timed run of the library's serving loop over `trace` (arrivals in
-    [0, window)); the loop stops at the end of the window. plain: the
-    one-walker-per-launch fp64 path (one slot per pool, one walker resident, one
-    pool in flight, each walker's sweep on the whole GPU)."""
+def serve_once(a, trace, plain, until, budget):
+    """One run of the library's serving loop over `trace`, stopped when the
+    server clock passes `until` (< 0: when every request has finished). plain:
+    the one-walker-per-launch fp64 path (one slot per pool, one walker
+    resident, one pool in flight, each walker's sweep on the whole GPU)."""
     from paper_1708_00744_b300.qmcdu import Server
     if plain:
         classes = [dict(N=c["N"], slots=1, group_ctas=148) for c in a.classes]
@@ -396,23 +389,30 @@ def serve_once(a, trace, plain, window, budget):
         srv = Server(classes, precision=a.precision, sigma=a.sigma, recompute_every=10,
                      hbm_budget=budget)
     srv.submit(trace)
-    srv.run(until_s=window)
+    srv.run(until_s=until)
     st = srv.stats()
+    per_class = {str(c["N"]): srv.class_stats(i) for i, c in enumerate(a.classes)}
     res = srv.results()
     srv.close()
-    return st, res
+    return st, res, per_class
 
 
-def serve_summary(st, res, window):
+def serve_summary(st, res, per_class, seconds):
     ok = [r for r in res if r["status"] == 0]
-    return {"updates_per_s": st["accepted"] / window, "proposals_per_s": st["proposals"] / window,
-            "walker_sweeps_per_s": st["walker_sweeps"] / window,
+    return {"seconds": seconds, "updates_per_s": st["accepted"] / seconds,
+            "proposals_per_s": st["proposals"] / seconds,
+            "walker_sweeps_per_s": st["walker_sweeps"] / seconds,
             "acceptance": st["accepted"] / max(1.0, st["proposals"]),
             "sweep_latency_ms": {"p50": st["sweep_ms_p50"], "p99": st["sweep_ms_p99"]},
             "request_latency_s": {"p50": st["request_s_p50"], "p99": st["request_s_p99"]},
             "admission_wait_s": {"p50": st["wait_s_p50"], "p99": st["wait_s_p99"]},
             "requests": {"arrived": int(st["submitted"]), "finished": len(ok),
                          "failed": int(st["failed"])},
+            "per_class": {n: {"walker_sweeps": int(v["walker_sweeps"]),
+                              "sweep_ms_p50": v["sweep_ms_p50"], "sweep_ms_p99": v["sweep_ms_p99"],
+                              "finished": int(v["finished"]), "request_s_p50": v["request_s_p50"],
+                              "request_s_p99": v["request_s_p99"]}
+                          for n, v in per_class.items()},
             "peak_gb_held": st["peak_bytes"] / 1e9, "pools_created": int(st["pools_created"]),
             "pools_destroyed": int(st["pools_destroyed"]), "rounds": int(st["rounds"]),
             "max_walkers_resident": int(st["max_resident"]),
@@ -432,24 +432,31 @@ def run_serve(a):
     warm = [dict(id=i, seed=99 + i, N=n, nsweeps=1, arrival_s=0.0) for i, n in enumerate(sizes)]
     for plain in (False, True):
         serve_once(a, warm, plain, -1.0, budget)
+    # capacity: makespan of a backlog of the same size mix, all present at t = 0
+    backlog = [dict(r, arrival_s=0.0) for r in
+               inputs.serving_trace(a.seed + 7, 1000.0, 1.0, sizes=sizes, nsweeps=20,
+                                    max_requests=48)]
+    st_c, res_c, pc_c = serve_once(a, backlog, False, -1.0, budget)
+    makespan = st_c["last_round_end_s"]
+    capacity = len(backlog) / makespan
+    # the offered load (Poisson at --rate) for --window seconds; the loop stops there
     trace = inputs.serving_trace(a.seed, a.rate, a.window, sizes=sizes, nsweeps=20)
     clocks = ClockSampler(0)
     clocks.start()
-    st, res = serve_once(a, trace, False, a.window, budget)
+    st, res, pc = serve_once(a, trace, False, a.window, budget)
     clk = clocks.stop()
-    batched = serve_summary(st, res, a.window)
-    st_p, res_p = serve_once(a, trace, True, a.window, budget)
-    plain = serve_summary(st_p, res_p, a.window)
-    # capacity in requests/s from the saturated run, then an offered load below it
-    cap = batched["walker_sweeps_per_s"] / 20.0
-    low_rate = max(0.5, 0.6 * cap)
-    below = None
-    if low_rate < a.rate:
-        trace_lo = inputs.serving_trace(a.seed + 1, low_rate, a.window, sizes=sizes, nsweeps=20)
-        st_l, res_l = serve_once(a, trace_lo, False, a.window, budget)
-        below = dict(serve_summary(st_l, res_l, a.window), offered_rate_per_s=low_rate)
-    return dict(batched=batched, plain=plain, below=below, clocks=clk, capacity_req_s=cap,
-                requests_in_trace=len(trace))
+    batched = serve_summary(st, res, pc, a.window)
+    st_p, res_p, pc_p = serve_once(a, trace, True, a.window, budget)
+    plain = serve_summary(st_p, res_p, pc_p, a.window)
+    # below capacity: 70 % of it, every request served to the end
+    low_rate = 0.7 * capacity
+    trace_lo = inputs.serving_trace(a.seed + 1, low_rate, a.window, sizes=sizes, nsweeps=20)
+    st_l, res_l, pc_l = serve_once(a, trace_lo, False, -1.0, budget)
+    below = dict(serve_summary(st_l, res_l, pc_l, st_l["last_round_end_s"]),
+                 offered_rate_per_s=low_rate)
+    sat = dict(serve_summary(st_c, res_c, pc_c, makespan), requests_per_s=capacity)
+    return dict(batched=batched, plain=plain, below=below, saturation=sat, clocks=clk,
+                capacity_req_s=capacity, requests_in_trace=len(trace))
 
 
 def roofline_for(a, res):
@@ -531,6 +538,7 @@ def main():
                 "serving": dict(b, offered_rate_per_s=a.rate, requests_in_trace=r["requests_in_trace"],
                                 capacity_req_per_s=r["capacity_req_s"]),
                 "plain_one_walker_fp64": r["plain"],
+                "saturation_backlog_48": r["saturation"],
                 "below_capacity": r["below"],
                 "speedup_vs_plain": b["updates_per_s"] / max(1e-9, r["plain"]["updates_per_s"]),
                 "roofline": None, "clocks": r["clocks"],

@@ -445,6 +445,13 @@ typedef struct {
  * pools and frees them. Not thread-safe: one host thread drives a server.
  */
 #define QMCDU_SERVER_STATS 22
+/*
+ * Per size class (index into class_N): QMCDU_SERVER_CLASS_STATS doubles, in
+ * order: walker-sweeps, per-sweep latency p50 and p99 (ms), requests finished,
+ * request latency p50 and p99 (s), accepted updates of finished requests.
+ * ERR_ARG for a class index out of range.
+ */
+#define QMCDU_SERVER_CLASS_STATS 7
 int qmcdu_server_create(const qmcdu_server_config *cfg, qmcdu_server_t *out);
 int qmcdu_server_submit(qmcdu_server_t s, const qmcdu_request *reqs, int n);
 int qmcdu_server_run(qmcdu_server_t s, double until_s);
@@ -452,6 +459,7 @@ int qmcdu_server_results(qmcdu_server_t s, qmcdu_result *out, int max, int *coun
 int qmcdu_server_trace(qmcdu_server_t s, unsigned long long id, unsigned char *accepted,
                        double *ratios);
 int qmcdu_server_stats(qmcdu_server_t s, double *out, int n);
+int qmcdu_server_class_stats(qmcdu_server_t s, int cls, double *out, int n);
 const char *qmcdu_server_error(qmcdu_server_t s);
 int qmcdu_server_destroy(qmcdu_server_t s);
 

@@ -108,6 +108,7 @@ struct Server {
     int error = QMCDU_OK;
     std::string err;
     std::vector<double> sweep_lat_ms;
+    std::vector<double> class_lat_ms[QMCDU_SERVER_MAX_CLASSES];   // per size class
     long long walker_sweeps = 0, accepted_total = 0, proposals_total = 0;
     long long pools_created = 0, pools_destroyed = 0, rounds = 0, mixed_walker_sweeps = 0;
     int max_resident = 0, max_inflight_seen = 0;
@@ -630,6 +631,7 @@ struct Server {
             ++walker_sweeps;
             if (p.mixed) ++mixed_walker_sweeps;
             sweep_lat_ms.push_back(lat_ms);
+            class_lat_ms[p.cls].push_back(lat_ms);
             q.lat_sum += lat_ms;
             q.lat_max = std::max(q.lat_max, (double)lat_ms);
             if (q.first_round < 0) q.first_round = p.rounds;
@@ -898,6 +900,27 @@ int qmcdu_server_stats(qmcdu_server_t h, double *out, int n)
         s->last_round_end,
     };
     for (int i = 0; i < n && i < QMCDU_SERVER_STATS; ++i) out[i] = v[i];
+    return QMCDU_OK;
+}
+
+int qmcdu_server_class_stats(qmcdu_server_t h, int cls, double *out, int n)
+{
+    if (!h || !out || n < 0) return QMCDU_ERR_ARG;
+    Server *s = reinterpret_cast<Server *>(h);
+    if (cls < 0 || cls >= s->cfg.num_classes) return QMCDU_ERR_ARG;
+    std::vector<double> lat_req;
+    long long fin = 0, acc = 0;
+    for (const qmcdu::Req &q : s->reqs)
+        if (q.cls == cls && q.finished && q.status == QMCDU_OK) {
+            ++fin;
+            acc += q.accepted;
+            lat_req.push_back(q.done_s - q.r.arrival_s);
+        }
+    const std::vector<double> &l = s->class_lat_ms[cls];
+    const double v[QMCDU_SERVER_CLASS_STATS] = {
+        (double)l.size(), qmcdu::percentile(l, 0.50), qmcdu::percentile(l, 0.99), (double)fin,
+        qmcdu::percentile(lat_req, 0.50), qmcdu::percentile(lat_req, 0.99), (double)acc};
+    for (int i = 0; i < n && i < QMCDU_SERVER_CLASS_STATS; ++i) out[i] = v[i];
     return QMCDU_OK;
 }
 

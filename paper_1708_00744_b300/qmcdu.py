@@ -62,6 +62,7 @@ SIGNATURES = {
     "qmcdu_server_results": (_I, [_VP, _VP, _I, ctypes.POINTER(_I)]),
     "qmcdu_server_trace": (_I, [_VP, _ULL, _VP, _VP]),
     "qmcdu_server_stats": (_I, [_VP, _VP, _I]),
+    "qmcdu_server_class_stats": (_I, [_VP, _I, _VP, _I]),
     "qmcdu_server_error": (ctypes.c_char_p, [_VP]),
     "qmcdu_server_destroy": (_I, [_VP]),
     "qmcdu_version": (ctypes.c_char_p, []),
@@ -444,6 +445,17 @@ def qmcdu_server_stats(s):
     return dict(zip(SERVER_STATS, out.tolist()))
 
 
+SERVER_CLASS_STATS = ("walker_sweeps", "sweep_ms_p50", "sweep_ms_p99", "finished",
+                      "request_s_p50", "request_s_p99", "accepted")
+
+
+def qmcdu_server_class_stats(s, cls):
+    out = np.zeros(len(SERVER_CLASS_STATS))
+    _server_check("qmcdu_server_class_stats",
+                  load().qmcdu_server_class_stats(s, cls, _ptr(out), out.size), s)
+    return dict(zip(SERVER_CLASS_STATS, out.tolist()))
+
+
 def qmcdu_server_destroy(s):
     _server_check("qmcdu_server_destroy", load().qmcdu_server_destroy(s), None)
 
@@ -499,6 +511,9 @@ class Server:
 
     def stats(self):
         return qmcdu_server_stats(self.s)
+
+    def class_stats(self, cls):
+        return qmcdu_server_class_stats(self.s, cls)
 
     def close(self):
         if self.s:
