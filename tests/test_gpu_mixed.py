@@ -89,3 +89,68 @@ def test_tensor_core_flush_inside_the_sweep(N, K):
               % ((N, K, b, bound) + errs))
         assert errs[0] < bound and errs[1] < bound and errs[2] < bound
         assert errs[1] < 1e-2                 # far tighter than the bound: split bf16 is working
+
+
+_TRAJ = {}
+
+
+def _oracle_trajectory(N, nsweeps, sigma, base):
+    key = (N, nsweeps, sigma, base)
+    if key not in _TRAJ:
+        A, G, U = walker_inputs(base, 1, N, nsweeps)
+        _TRAJ[key] = (A, U[0], oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma))
+    return _TRAJ[key]
+
+
+@pytest.mark.parametrize("sigma", [0.1, 1.0])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_error_vs_recompute_interval(precision, sigma):
+    """Working-precision walkers recomputed in fp64 every R sweeps, R in
+    {1, 5, 20}, over 20 sweeps of the oracle's trajectory (decisions replayed).
+    Per R: the largest ratio error of the run, the largest drift the recomputes
+    found (the error accumulated over R sweeps, against the fp64 LU of the
+    current A), and A^{-1} and log|det| against the oracle after the last sweep,
+    before its recompute. The running inverse takes one rounding error per
+    update, so the bound grows with the sweeps between recomputes:
+    8 N u_w kappa_1 max(1, R / 2) (the two-sweep bound above at R <= 2)."""
+    need_gpu()
+    N, K, nsweeps, base = 512, 32, 20, 4100
+    A, U, ref = _oracle_trajectory(N, nsweeps, sigma, base)
+    kappa = max(np.linalg.cond(A[0], 1), np.linalg.cond(ref["A"], 1))
+    override = ref["accepted"].astype(np.int8)
+    for R in (1, 5, 20):
+        W = Walkers(N, K, precision, 1)
+        if precision == "bf16x3":
+            W.set_option("max_ctas", 1)    # one CTA: a 512-column flush block, on tcgen05
+        W.set_matrix(A)
+        rat = np.zeros((nsweeps, 1, N))
+        drift_max = np.zeros(2)
+        Ai = np.zeros((1, N, N))
+        la = np.zeros(1)
+        sg = np.zeros(1, dtype=np.int32)
+        for s in range(nsweeps):
+            W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s][None]),
+                    ratios_out=rat[s])
+            if s == nsweeps - 1:
+                W.get_inverse(Ai)
+                W.logdet(la, sg)
+            if (s + 1) % R == 0:
+                drift = np.zeros((1, 2))
+                W.recompute(drift)
+                drift_max = np.maximum(drift_max, drift[0])
+        shape = W.sweep_shape()
+        W.close()
+        if precision == "bf16x3":
+            assert shape["col_tile"] == 1000, shape          # the tensor-core flush ran
+        bound = 8 * N * U_W[precision] * kappa * max(1.0, R / 2.0)
+        errs = (rel_ratio_err(rat[:, 0], ref["ratios"]), rel_norm_err(Ai[0], ref["Ainv"]),
+                logdet_err(la[0], ref["logabs"]))
+        flips = int(np.sum(np.abs(np.minimum(1, ref["ratios"] ** 2) - U) < 2 * errs[0]))
+        print("R-study %s sigma=%g R=%d: acceptance %.3f kappa_1 %.1e bound %.1e | ratio %.1e "
+              "inverse %.1e logdet %.1e | drift logdet %.1e inverse %.1e | decisions within "
+              "error of a tie %d of %d"
+              % ((precision, sigma, R, ref["accepted"].mean(), kappa, bound) + errs +
+                 tuple(drift_max) + (flips, nsweeps * N)))
+        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
+        assert drift_max[0] < bound and drift_max[1] < bound
+        assert sg[0] == ref["sign"]
