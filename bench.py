@@ -56,6 +56,8 @@ WORKLOADS = {
     "uneven": [dict(N=512, batch=256), dict(N=1536, batch=64)],
     "mixed": [dict(N=2048, batch=64), dict(N=4096, batch=8)],
     # serving: Poisson arrivals, N uniform over the size set; slots per pool
+    "ksweep": [dict(N=2048, batch=1)],
+    "kernels": [dict(N=512, batch=128)],
     "serve": [dict(N=128, batch=16), dict(N=256, batch=16), dict(N=512, batch=16),
               dict(N=1024, batch=8), dict(N=2048, batch=8), dict(N=4096, batch=8)],
 }
@@ -80,6 +82,9 @@ def parse():
     p.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     p.add_argument("--window", type=float, default=20.0, help="serve: seconds of arrivals timed")
     p.add_argument("--budget-gb", type=float, default=150.0, help="serve: HBM budget (GB)")
+    p.add_argument("--reps", type=int, default=5, help="ksweep: timed sweeps per point (median)")
+    p.add_argument("--ksweep-N", default="512,1024,2048,4096", help="ksweep: electron counts")
+    p.add_argument("--kernels-batch", type=int, default=512, help="kernels: walkers of the ratio run")
     a = p.parse_args()
     a.classes = [dict(c) for c in WORKLOADS[a.workload]]
     if a.N is not None and a.workload == "single":
@@ -93,6 +98,11 @@ def parse():
 
 
 def workload_name(a):
+    if a.workload == "ksweep":
+        return ("one fp64 walker, N in {%s}, K in {1, 16, 32, 64, 128, 256}, sigma 0.1 and 1.0 "
+                "and forced acceptance; median of %d single sweeps per point" % (a.ksweep_N, a.reps))
+    if a.workload == "kernels":
+        return "kernel microbenchmarks: batched ratio, split-bf16 GEMM, fp64 recompute"
     if a.workload == "serve":
         return ("serving: Poisson arrivals at %g/s for %g s, N uniform over {%s}, %s + fp64 "
                 "recompute every 10 sweeps, sigma=%g, 20 sweeps per request, %g GB budget"
@@ -373,6 +383,149 @@ def run_ours(a, rank, world, local_rank):
     return res
 
 
+# ------------------------------------------------------------------ K sweep
+def run_ksweep(a):
+    """Updates/s of one fp64 walker against K (the paper's Fig. 1 axes), with
+    sigma 0.1 (DMC-like), sigma 1.0 (VMC-like) and forced acceptance (the
+    paper's test condition): per point the median of --reps single sweeps timed
+    with CUDA events, L2 flushed before each."""
+    import torch
+    from paper_1708_00744_b300 import inputs
+    from paper_1708_00744_b300.qmcdu import Walkers
+    torch.cuda.set_device(0)
+    st = torch.cuda.Stream()
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rows = []
+    for N in [int(x) for x in a.ksweep_N.split(",")]:
+        A0 = inputs.initial_matrix(a.seed, N)[None]
+        acc = torch.zeros(1, N, dtype=torch.uint8, device="cuda")
+        ones = torch.ones(1, N, dtype=torch.int8, device="cuda")
+        for mode in ("sigma=0.1", "sigma=1.0", "forced"):
+            sigma = 1.0 if mode == "sigma=1.0" else 0.1
+            for K in (1, 16, 32, 64, 128, 256):
+                if K > N:
+                    continue
+                W = Walkers(N, K, "fp64", 1, stream=st)
+                W.set_matrix(A0)
+                ov = ones if mode == "forced" else None
+                W.sweep(a.seed, 0, sigma, override=ov, accepted_out=acc)     # warm-up
+                ms, got = [], []
+                for r in range(a.reps):
+                    flush_buf.zero_()
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    W.sweep(a.seed, 1 + r, sigma, override=ov, accepted_out=acc)
+                    e1.record(st)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    got.append(int(acc.sum().item()))
+                W.close()
+                order = np.argsort(ms)
+                med = order[len(ms) // 2]
+                rows.append({"N": N, "mode": mode, "K": K, "ms_per_sweep": ms[med],
+                             "updates_per_s": got[med] / (ms[med] * 1e-3),
+                             "proposals_per_s": N / (ms[med] * 1e-3),
+                             "acceptance": got[med] / N,
+                             "ms_spread": [min(ms), max(ms)]})
+    # speedup over K = 1 per (N, mode)
+    for r in rows:
+        k1 = [x for x in rows if x["N"] == r["N"] and x["mode"] == r["mode"] and x["K"] == 1]
+        r["vs_k1"] = r["updates_per_s"] / k1[0]["updates_per_s"] if k1 else None
+    return rows
+
+
+# ------------------------------------------------------------------ kernels
+def run_kernels(a):
+    """Microbenchmarks of single kernels, timed with CUDA events: the batched
+    per-call ratio (Eq. 3 through a queue of k = 128 moves; HBM-bound), the
+    split-bf16 x3 tensor-core GEMM, and the fp64 recompute."""
+    import torch
+    from paper_1708_00744_b300.qmcdu import Walkers, qmcdu_gemm_bf16x3
+    torch.cuda.set_device(0)
+    st = torch.cuda.Stream()
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+
+    def timed(fn, reps, stream, flush=True):
+        ms = []
+        for _ in range(reps):
+            if flush:
+                flush_buf.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    # ratio: walkers of N = 512 with 128 queued moves; each ratio reads
+    # A^{-1}[:, j], the proposal and the 2 x 128 queue rows of every walker.
+    # fp64 does one FMA per 8 bytes read, above B300's fp64 ridge (1.2 TFLOP/s
+    # over 6.5 TB/s = 0.19 flop/B): ALU-bound. fp32 halves the bytes and has
+    # 64x the ALU rate: HBM-bound.
+    N, K, B, k = 512, 256, a.kernels_batch, 128
+    for prec in ("fp64", "fp32"):
+        es = 8 if prec == "fp64" else 4
+        W = Walkers(N, K, prec, B, stream=st)
+        W.load_walkers(0, B, seeds=[a.seed + b for b in range(B)])
+        r = torch.zeros(B, dtype=torch.float64, device="cuda")
+        ones = np.ones(B, dtype=np.uint8)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(a.seed)
+        torch.cuda.synchronize()
+        for m in range(k):
+            # a fresh random row per move (a repeated row would make A singular),
+            # drawn on the handle's stream so that the ratio kernel reads it after
+            with torch.cuda.stream(st):
+                v = torch.randn(B, N, dtype=torch.float64, device="cuda", generator=gen)
+            W.ratio(np.full(B, m, dtype=np.int32), v, r)
+            W.accept(ones)
+        with torch.cuda.stream(st):
+            v = torch.randn(B, N, dtype=torch.float64, device="cuda", generator=gen)
+        elec = np.full(B, N - 1, dtype=np.int32)
+        W.ratio(elec, v, r)
+        ms = timed(lambda: W.ratio(elec, v, r), 20, st)
+        W.sync()
+        W.close()
+        bytes_per = (2 * k + 1) * N * es * B + k * k * 8 * B   # rows, column, Kinv
+        flops = 2.0 * ((2 * k + 1) * N + 2 * k * k) * B
+        out["ratio_" + prec] = {"walkers": B, "N": N, "k": k, "ms": ms,
+                                "algorithmic_bytes": bytes_per,
+                                "GB_per_s": bytes_per / (ms * 1e-3) / 1e9,
+                                "TFLOP_per_s": flops / (ms * 1e-3) / 1e12,
+                                "note": "one qmcdu_ratio call (three kernels) with its host "
+                                        "argument copy"}
+    # split-bf16 x3 GEMM on tcgen05: C = A B', 4096^3
+    M = Nn = Kk = 4096
+    Ag = torch.randn(M, Kk, device="cuda")
+    Bg = torch.randn(Nn, Kk, device="cuda")
+    Cg = torch.zeros(M, Nn, device="cuda")
+    cur = torch.cuda.current_stream()
+    qmcdu_gemm_bf16x3(Ag, Bg, Cg)
+    ms = timed(lambda: qmcdu_gemm_bf16x3(Ag, Bg, Cg), 10, cur)
+    fl = 2.0 * M * Nn * Kk
+    out["gemm_bf16x3"] = {"M": M, "N": Nn, "K": Kk, "ms": ms,
+                          "fp32_equivalent_TFLOP_per_s": fl / (ms * 1e-3) / 1e12,
+                          "bf16_tensor_TFLOP_per_s": 3 * fl / (ms * 1e-3) / 1e12}
+    del Ag, Bg, Cg
+    # fp64 recompute (Gauss-Jordan with partial pivoting) of 8 walkers of N = 2048
+    Nr, Br = 2048, 8
+    W = Walkers(Nr, 32, "fp64", Br, stream=st)
+    W.load_walkers(0, Br, seeds=[a.seed + 7 + b for b in range(Br)])
+    W.recompute()
+    ms = timed(lambda: W.recompute(), 5, st)
+    W.sync()
+    W.close()
+    out["recompute_fp64"] = {"walkers": Br, "N": Nr, "ms": ms,
+                             "TFLOP_per_s": 2.0 * Nr ** 3 * Br / (ms * 1e-3) / 1e12}
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def serve_once(a, trace, plain, until, budget):
     """One run of the library's serving loop over `trace`, stopped when the
@@ -522,6 +675,31 @@ def main():
                                            "(setup inverse timed apart and excluded)" % (nm, a.N, K)},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if a.workload in ("ksweep", "kernels"):
+        if world > 1 and rank != 0:
+            return
+        clocks = ClockSampler(0)
+        clocks.start()
+        if a.workload == "ksweep":
+            rows = run_ksweep(a)
+            best = max((r for r in rows if r["N"] == 2048 and r["mode"] == "sigma=0.1"),
+                       key=lambda r: r["updates_per_s"], default=None)
+            extra = {"table": rows}
+            value = best["updates_per_s"] if best else None
+        else:
+            k = run_kernels(a)
+            extra = {"kernels": k}
+            value = k["ratio_fp32"]["GB_per_s"]
+            metric = "ratio (fp32 walkers) HBM GB/s"
+        line = {"metric": metric, "value": value,
+                "unit": "updates/s" if a.workload == "ksweep" else "GB/s", "n_gpus": 1,
+                "steps": a.reps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a, 1),
+                "clocks": clocks.stop()}
+        line.update(extra)
         print(json.dumps(line))
         return
 

@@ -10,19 +10,20 @@
 //                 A^{-1}: per column, a dot product with v and a rank-1 axpy.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "philox.cuh"
 #include "qmcdu_internal.cuh"
 
 namespace qmcdu {
 
-constexpr int RCHUNK = 256;    // elements of N handled by one CTA of the ratio kernel
 constexpr int RTHREADS = 256;  // 8 warps
 
 template <typename T>
 struct RatioParams {
-    int N, K, ld, nsplit;
+    int N, K, ld, jsplit;
     const double *A;
     const T *Ainv;
     T *P, *V;
@@ -31,6 +32,7 @@ struct RatioParams {
     const int *kcount;
     double *rs;
     double *partial;
+    double *scr;                // [batch][kparts][K + 1]: partial y and b.x of the k x k pass
     unsigned *arrive;
     int *status;
     const double *v_in;
@@ -56,136 +58,337 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Grid (nsplit, batch). CTA `split` owns elements [split*RCHUNK, +RCHUNK) of N
-// for walker blockIdx.y. Each CTA stages v and A^{-1}[:, j] for its chunk in
-// shared memory, writes them speculatively into slot k of V and P (the slot a
-// subsequent accept would fill), and computes 2k+1 partial dot products:
-//   d = v . A^{-1}[:, j],  b_m = P[m] . v,  c_m = V[m] . A^{-1}[:, j].
-// The last CTA to arrive for the walker sums the partials in split order
-// (deterministic), forms x = Kinv c and y = Kinv' b, and the ratio
-//   r = d - b' Kinv c   (the Schur complement of the bordered V'P, Eq. 3).
-template <typename T>
-__global__ void __launch_bounds__(RTHREADS) ratio_kernel(RatioParams<T> p)
+__device__ __forceinline__ void fma16(double &acc, double2 x, double2 y)
 {
-    using Acc = T;
-    const int b = blockIdx.y, split = blockIdx.x;
+    acc = fma(x.x, y.x, acc);
+    acc = fma(x.y, y.y, acc);
+}
+__device__ __forceinline__ void fma16(float &acc, float4 x, float4 y)
+{
+    acc = fmaf(x.x, y.x, acc);
+    acc = fmaf(x.y, y.y, acc);
+    acc = fmaf(x.z, y.z, acc);
+    acc = fmaf(x.w, y.w, acc);
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+
+// The ratio of one proposal per walker (Eq. 1 at k = 0, Eq. 3 through the
+// queued panels otherwise) in three launches:
+//   ratio_stage_kernel   v and A^{-1}[:, j] into slot k of V and P (the slot a
+//                        subsequent accept fills; the rows the dots read)
+//   ratio_dots_kernel    the 2k+1 full-row dot products of every walker,
+//                          d = v . A^{-1}[:, j],  b_m = P[m] . v,  c_m = V[m] . A^{-1}[:, j]:
+//                        grid-stride over (walker, row), one warp per row, so
+//                        that every warp streams rows from HBM the whole time
+//   ratio_finish_kernel  per walker: x = Kinv c and y = Kinv' b in one
+//                        coalesced pass over Kinv, r = d - b' Kinv c (the
+//                        Schur complement of the bordered V'P, Eq. 3)
+// Rows are padded to ld with zeros (nothing writes past N), so 16-byte vectors
+// that reach into the padding add nothing.
+
+template <typename T>
+__global__ void __launch_bounds__(RTHREADS) ratio_stage_kernel(RatioParams<T> p)
+{
+    const int b = blockIdx.y;
     const int N = p.N, K = p.K, ld = p.ld;
-    const int i0 = split * RCHUNK;
-    const int n = min(RCHUNK, N - i0);
     const int k = p.kcount[b];
     const int j = p.elec ? p.elec[b] : p.uniform_elec;
     if (j < 0 || j >= N || k < 0 || k >= K) {
-        if (threadIdx.x == 0 && split == 0) atomicOr(p.status, ST_BADARG);
-        return;  // every CTA of this walker returns: the arrival count stays 0
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(p.status, ST_BADARG);
+        return;
     }
-    __shared__ T vs[RCHUNK];
-    __shared__ T as[RCHUNK];
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     const T *acol = p.Ainv + b * wN + (size_t)j * ld;
     T *Pk = p.P + b * wK + (size_t)k * ld;
     T *Vk = p.V + b * wK + (size_t)k * ld;
-
+    const int i0 = blockIdx.x * (2 * RTHREADS);
+    for (int i = i0 + threadIdx.x; i < min(N, i0 + 2 * RTHREADS); i += RTHREADS) Pk[i] = acol[i];
     if (p.generate) {
-        // v = a_j + sigma g, g from Philox / Box-Muller in pairs (i0 is even).
+        // v = a_j + sigma g, g from Philox / Box-Muller in pairs
         const double *arow = p.A + b * wN + (size_t)j * ld;
         const unsigned long long wseed = p.seed + (unsigned long long)b;
-        for (int q = threadIdx.x; 2 * q < n; q += blockDim.x) {
-            const int i = i0 + 2 * q;
+        const int i = i0 + 2 * threadIdx.x;
+        if (i < N) {
             const double2 g = proposal_gaussian_pair(wseed, j, p.sweep, i >> 1);
             const double v0 = arow[i] + p.sigma * g.x;
-            vs[2 * q] = (T)v0;
             Vk[i] = (T)v0;
             if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i] = v0;
             if (i + 1 < N) {
                 const double v1 = arow[i + 1] + p.sigma * g.y;
-                vs[2 * q + 1] = (T)v1;
                 Vk[i + 1] = (T)v1;
                 if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i + 1] = v1;
             }
         }
     } else {
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const double v0 = p.v_in[(size_t)b * N + i0 + t];
-            vs[t] = (T)v0;
-            Vk[i0 + t] = (T)v0;
-            if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i0 + t] = v0;
+        for (int i = i0 + threadIdx.x; i < min(N, i0 + 2 * RTHREADS); i += RTHREADS) {
+            const double v0 = p.v_in[(size_t)b * N + i];
+            Vk[i] = (T)v0;
+            if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i] = v0;
         }
     }
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const T a = acol[i0 + t];
-        as[t] = a;
-        Pk[i0 + t] = a;
+}
+
+constexpr int KROWS = 32;   // rows of Kinv per CTA of the k x k pass
+constexpr int TSEG = 4096;   // bytes of a streamed row segment (one bulk copy)
+constexpr int TNS = 16;      // stages of the segment ring
+constexpr int TRU = 32;      // rows per CTA of the dots
+constexpr int TMAXSEG = 16;  // segments per row at most (rows of <= 64 KB: N <= 8192 in fp64)
+constexpr int TTHREADS = 288;  // 8 consumer warps + 1 producer warp
+
+static size_t dots_smem_bytes(size_t rowbytes)
+{
+    return 512 + (size_t)TRU * TMAXSEG * sizeof(double) + rowbytes + (size_t)TNS * TSEG;
+}
+
+// Rows of walker b are the jobs t = 0..2k: t = 0 the A^{-1} column (P row k),
+// t = 1..k P row t-1, both against v (V row k); t = k+1..2k V row t-k-1
+// against the column (P row k). Grid (U, batch): CTA u takes up to TRU rows
+// that share their vector, units 0..U/2-1 the rows against v and U/2..U-1 the
+// rows against the column (U = 2 ceil((kmax + 1) / TRU); a walker's units past
+// its own k return at once).
+//
+// The vector goes to shared memory in one bulk copy; the rows stream through a
+// ring of TNS segment buffers of 4 KB: the producer warp issues
+// cp.async.bulk copies (completion counted in bytes on the stage's "full"
+// mbarrier) as soon as the stage's "empty" mbarrier says its last segment was
+// read; consumer warp w takes segments w, w + 8, ... and leaves one partial sum
+// per (row, segment). Every wait is bounded: on a timeout the CTA stops, flags
+// ST_TIMEOUT and waits (bounded) for its copies in flight before it exits.
+template <typename T>
+__global__ void __launch_bounds__(TTHREADS) ratio_dots_kernel(RatioParams<T> p, int U,
+                                                              long long budget_ns)
+{
+    using V16 = typename Vec16<T>::type;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(tsm);
+    unsigned long long *empty = full + TNS;
+    unsigned long long *wbar = empty + TNS;
+    double *part = reinterpret_cast<double *>(tsm + 512);                    // [TRU][TMAXSEG]
+    unsigned char *wv = tsm + 512 + TRU * TMAXSEG * sizeof(double);          // the shared vector
+    const int K = p.K, ld = p.ld;
+    const unsigned rowbytes = (unsigned)ld * sizeof(T);                     // a multiple of 128
+    unsigned char *ring = wv + rowbytes;                                     // [TNS][TSEG]
+    __shared__ int abort_s, issued_s;
+
+    const int b = blockIdx.y, u = blockIdx.x, half = U / 2;
+    const int k = p.kcount[b];
+    if (k < 0 || k >= K) return;                      // flagged by the stage kernel
+    const size_t wK = (size_t)K * ld;
+    const T *Pw = p.P + b * wK, *Vw = p.V + b * wK;
+    int rb, re;
+    const T *with;
+    if (u < half) {
+        rb = u * TRU;
+        re = min(rb + TRU, k + 1);
+        with = Vw + (size_t)k * ld;
+    } else {
+        rb = k + 1 + (u - half) * TRU;
+        re = min(rb + TRU, 2 * k + 1);
+        with = Pw + (size_t)k * ld;
+    }
+    if (rb >= re) return;
+    const int nrows = re - rb;
+    const int nseg = (int)((rowbytes + TSEG - 1) / TSEG);
+    const int items = nrows * nseg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TNS; ++s) {
+            mbar_init_count(&full[s], 1);
+            mbar_init_count(&empty[s], 1);
+        }
+        mbar_init_count(wbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+        issued_s = 0;
     }
     __syncthreads();
 
+    if (warp == 8) {
+        // producer: one lane issues every copy
+        if (lane == 0) {
+            mbar_expect(wbar, rowbytes);
+            bulk_g2s(wv, with, rowbytes, wbar);
+            int i = 0;
+            for (; i < items; ++i) {
+                const int s = i % TNS;
+                if (i >= TNS && !mbar_wait(&empty[s], ((i / TNS) - 1) & 1, p.status, budget_ns)) {
+                    abort_s = 1;
+                    break;
+                }
+                if (*(volatile int *)&abort_s) break;
+                const int r = i / nseg, sg = i - r * nseg;
+                const int t = rb + r;
+                const T *row = t == 0 ? Pw + (size_t)k * ld
+                                      : (t <= k ? Pw + (size_t)(t - 1) * ld : Vw + (size_t)(t - 1 - k) * ld);
+                const unsigned off = (unsigned)sg * TSEG;
+                const unsigned bytes = min((unsigned)TSEG, rowbytes - off);
+                mbar_expect(&full[s], bytes);
+                bulk_g2s(ring + (size_t)s * TSEG, reinterpret_cast<const unsigned char *>(row) + off,
+                         bytes, &full[s]);
+            }
+            issued_s = i;
+        }
+    } else {
+        // consumers
+        bool ok = mbar_wait(wbar, 0, p.status, budget_ns);
+        for (int i = warp; ok && i < items; i += 8) {
+            const int s = i % TNS;
+            if (!mbar_wait(&full[s], (i / TNS) & 1, p.status, budget_ns) ||
+                *(volatile int *)&abort_s) {
+                ok = false;
+                break;
+            }
+            const int r = i / nseg, sg = i - r * nseg;
+            const unsigned off = (unsigned)sg * TSEG;
+            const int nv = (int)(min((unsigned)TSEG, rowbytes - off) / 16);
+            const V16 *x = reinterpret_cast<const V16 *>(ring + (size_t)s * TSEG);
+            const V16 *w = reinterpret_cast<const V16 *>(wv + off);
+            T acc = 0;
+#pragma unroll 4
+            for (int v = lane; v < nv; v += 32) fma16(acc, x[v], w[v]);
+            acc = warp_sum(acc);
+            __syncwarp();
+            if (lane == 0) {
+                part[r * TMAXSEG + sg] = (double)acc;
+                mbar_arrive(&empty[s]);
+            }
+        }
+        if (!ok) abort_s = 1;
+    }
+    __syncthreads();
+    if (abort_s) {
+        // copies issued but not waited for may still be landing: wait for the
+        // last TNS of them (bounded) before the CTA's shared memory goes away
+        if (threadIdx.x == 0) {
+            const int n = issued_s;
+            for (int i = max(0, n - TNS); i < n; ++i)
+                mbar_wait(&full[i % TNS], (i / TNS) & 1, p.status, budget_ns);
+            mbar_wait(wbar, 0, p.status, budget_ns);
+        }
+        __syncthreads();
+        return;
+    }
+    if (threadIdx.x < nrows) {
+        double d = 0.0;
+        for (int sg = 0; sg < nseg; ++sg) d += part[threadIdx.x * TMAXSEG + sg];
+        p.partial[(size_t)b * (2 * K + 1) + rb + threadIdx.x] = d;
+    }
+}
+
+// The k x k pass, grid (kparts, batch): CTA part takes rows m in
+// [part KROWS, +KROWS) of Kinv (four per warp), writes x_m = (Kinv c)_m, and
+// leaves its share of y = Kinv' b and of b.x in scratch; the last CTA of the
+// walker to arrive sums the shares in part order (deterministic) and forms
+// r = d - b.x.
+template <typename T>
+__global__ void __launch_bounds__(RTHREADS) ratio_finish_kernel(RatioParams<T> p, int kparts)
+{
+    const int b = blockIdx.y, part = blockIdx.x;
+    const int N = p.N, K = p.K;
+    const int k = p.kcount[b];
+    const int j = p.elec ? p.elec[b] : p.uniform_elec;
+    if (j < 0 || j >= N || k < 0 || k >= K) return;     // flagged by the stage kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int njobs = 2 * k + 1;
-    double *part = p.partial + ((size_t)b * p.nsplit + split) * (2 * K + 1);
-    for (int job = warp; job < njobs; job += RTHREADS / 32) {
-        const T *src;
-        const T *with;
-        if (job == 0) {
-            src = as;
-            with = vs;
-        } else if (job <= k) {
-            src = p.P + b * wK + (size_t)(job - 1) * ld + i0;
-            with = vs;
-        } else {
-            src = p.V + b * wK + (size_t)(job - 1 - k) * ld + i0;
-            with = as;
-        }
-        Acc acc = 0;
-        for (int t = lane; t < n; t += 32) acc += src[t] * with[t];
-        acc = warp_sum(acc);
-        if (lane == 0) part[job] = (double)acc;
-    }
-
-    // Last-arriving CTA of this walker reduces.
-    __threadfence();
-    __syncthreads();
-    __shared__ unsigned ticket;
-    if (threadIdx.x == 0) ticket = atomicAdd(&p.arrive[b], 1u);
-    __syncthreads();
-    if (ticket != (unsigned)(p.nsplit - 1)) return;
-    __threadfence();
-
     __shared__ double red[2 * QMCDU_MAX_K + 1];
-    __shared__ double xs[QMCDU_MAX_K];
-    for (int job = threadIdx.x; job < njobs; job += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < p.nsplit; ++q)
-            s += __ldcg(p.partial + ((size_t)b * p.nsplit + q) * (2 * K + 1) + job);
-        red[job] = s;
-    }
+    __shared__ double ypart[RTHREADS / 32][QMCDU_MAX_K];
+    __shared__ double bx[RTHREADS / 32];
+    for (int job = threadIdx.x; job < njobs; job += RTHREADS)
+        red[job] = p.partial[(size_t)b * (2 * K + 1) + job];
     __syncthreads();
     const double d = red[0];
     const double *bv = red + 1, *cv = red + 1 + k;
     double *rec = p.rs + (size_t)b * rs_stride(K);
     const double *Kb = p.Kinv + (size_t)b * K * K;
-    for (int m = threadIdx.x; m < k; m += blockDim.x) {
-        double x = 0.0, y = 0.0;
-        for (int q = 0; q < k; ++q) {
-            x += Kb[(size_t)m * K + q] * cv[q];
-            y += bv[q] * Kb[(size_t)q * K + m];
+    double *scr = p.scr + ((size_t)b * kparts + part) * (K + 1);
+    constexpr int QL = QMCDU_MAX_K / 32;
+    double yl[QL];
+#pragma unroll
+    for (int s2 = 0; s2 < QL; ++s2) yl[s2] = 0.0;
+    double bxw = 0.0;
+    const int m0 = part * KROWS + warp * 4;
+    if (m0 < k) {
+        double xm[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int s2 = 0; s2 < QL; ++s2) {
+            const int q = lane + 32 * s2;
+            if (q < k) {
+                const double cq = cv[q];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int m = m0 + r;
+                    if (m < k) {
+                        const double kv = __ldg(Kb + (size_t)m * K + q);
+                        xm[r] += kv * cq;
+                        yl[s2] += bv[m] * kv;
+                    }
+                }
+            }
         }
-        xs[m] = x;
-        rec[4 + m] = x;
-        rec[4 + K + m] = y;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double x = warp_sum(xm[r]);
+            if (m0 + r < k) {
+                bxw += bv[m0 + r] * x;
+                if (lane == 0) rec[4 + m0 + r] = x;
+            }
+        }
     }
+#pragma unroll
+    for (int s2 = 0; s2 < QL; ++s2) {
+        const int q = lane + 32 * s2;
+        if (q < k) ypart[warp][q] = yl[s2];
+    }
+    if (lane == 0) bx[warp] = bxw;
     __syncthreads();
-    if (warp == 0) {
+    for (int q = threadIdx.x; q < k; q += RTHREADS) {
+        double y = 0.0;
+#pragma unroll
+        for (int w = 0; w < RTHREADS / 32; ++w) y += ypart[w][q];
+        scr[q] = y;
+    }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RTHREADS / 32; ++w) t += bx[w];
+        scr[K] = t;
+    }
+    // the last CTA of the walker sums the parts
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) ticket = atomicAdd(&p.arrive[b], 1u);
+    __syncthreads();
+    if (ticket != (unsigned)(kparts - 1)) return;
+    __threadfence();
+    const double *s0 = p.scr + (size_t)b * kparts * (K + 1);
+    for (int q = threadIdx.x; q < k; q += RTHREADS) {
+        double y = 0.0;
+        for (int pp = 0; pp < kparts; ++pp) y += __ldcg(s0 + (size_t)pp * (K + 1) + q);
+        rec[4 + K + q] = y;
+    }
+    if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int m = lane; m < k; m += 32) s += bv[m] * xs[m];
-        s = warp_sum(s);
-        if (lane == 0) {
-            const double r = d - s;
-            rec[0] = d;
-            rec[1] = r;
-            rec[2] = (double)k;
-            rec[3] = (double)j;
-            if (p.ratio_out) p.ratio_out[b] = r;
-            p.arrive[b] = 0u;
-        }
+        for (int pp = 0; pp < kparts; ++pp) s += __ldcg(s0 + (size_t)pp * (K + 1) + K);
+        const double r = d - s;
+        rec[0] = d;
+        rec[1] = r;
+        rec[2] = (double)k;
+        rec[3] = (double)j;
+        if (p.ratio_out) p.ratio_out[b] = r;
+        p.arrive[b] = 0u;
     }
 }
 
@@ -325,15 +528,29 @@ template <typename T>
 static cudaError_t launch_ratio_t(Ctx &c, const RatioLaunch &L)
 {
     RatioParams<T> p;
-    p.N = c.N; p.K = c.K; p.ld = c.ld; p.nsplit = c.nsplit;
+    p.N = c.N; p.K = c.K; p.ld = c.ld; p.jsplit = 1;
     p.A = c.A; p.Ainv = (const T *)c.Ainv; p.P = (T *)c.P; p.V = (T *)c.V;
     p.vstash = c.vstash; p.Kinv = c.Kinv; p.kcount = c.kcount; p.rs = c.rs;
-    p.partial = c.partial; p.arrive = c.arrive; p.status = c.status;
+    p.partial = c.partial; p.scr = c.ratio_scr; p.arrive = c.arrive; p.status = c.status;
     p.v_in = L.v_in; p.elec = L.elec; p.uniform_elec = L.uniform_elec;
     p.generate = L.generate; p.seed = L.seed; p.sweep = L.sweep; p.sigma = L.sigma;
     p.ratio_out = L.ratio_out;
-    dim3 grid(c.nsplit, c.batch);
-    ratio_kernel<T><<<grid, RTHREADS, 0, c.stream>>>(p);
+    ratio_stage_kernel<T><<<dim3((c.N + 2 * RTHREADS - 1) / (2 * RTHREADS), c.batch), RTHREADS, 0,
+                            c.stream>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // units of TRU rows sharing a vector, from the largest queue the host knows of
+    const int kmax = L.kmax >= 0 ? std::min(L.kmax, c.K - 1) : c.K - 1;
+    const int U = 2 * ((kmax + 1 + TRU - 1) / TRU);
+    const size_t smem = dots_smem_bytes((size_t)c.ld * sizeof(T));
+    e = cudaFuncSetAttribute(ratio_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    ratio_dots_kernel<T><<<dim3(U, c.batch), TTHREADS, smem, c.stream>>>(p, U, c.opt_budget_ns);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int kparts = std::max(1, (kmax + KROWS - 1) / KROWS);
+    ratio_finish_kernel<T><<<dim3(kparts, c.batch), RTHREADS, 0, c.stream>>>(p, kparts);
     return cudaGetLastError();
 }
 

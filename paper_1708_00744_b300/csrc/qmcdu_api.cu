@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -81,6 +82,7 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
     AL(c->sign, B * sizeof(int));
     AL(c->rs, B * rs_stride(K) * sizeof(double));
     AL(c->partial, B * c->nsplit * (2 * K + 1) * sizeof(double));
+    AL(c->ratio_scr, B * ((K + 31) / 32) * (K + 1) * sizeof(double));
     AL(c->arrive, B * sizeof(unsigned));
     AL(c->acc, B);
     AL(c->elec_d, B * sizeof(int));
@@ -132,10 +134,55 @@ static void release(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
-                    c->d_wseed, c->d_wsweep, c->d_lseed};
+                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr};
     for (void *p : more)
         if (p) cudaFree(p);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->pin_buf) cudaFreeHost(c->pin_buf);
+    for (cudaEvent_t e : c->pin_ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// Small host-to-device argument copies through a ring of pinned slots: each
+// part is copied into the next slot on the host, then asynchronously to the
+// device; the slot's event marks when the device has read it, and the host
+// waits on it only when the ring wraps.
+struct H2D {
+    void *dst;
+    const void *src;
+    size_t bytes;
+};
+
+static int stage_h2d(Ctx *c, std::initializer_list<H2D> parts)
+{
+    size_t total = 0;
+    for (const H2D &x : parts) total += (x.bytes + 15) / 16 * 16;
+    if (total > c->pin_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->pin_buf) cudaFreeHost(c->pin_buf);
+        c->pin_buf = nullptr;
+        const size_t cap = std::max<size_t>(total, (size_t)16 * c->batch + 64);
+        CK(cudaMallocHost(&c->pin_buf, cap * Ctx::NPIN));
+        c->pin_cap = cap;
+        for (int i = 0; i < Ctx::NPIN; ++i) {
+            if (!c->pin_ev[i]) CK(cudaEventCreateWithFlags(&c->pin_ev[i], cudaEventDisableTiming));
+            c->pin_used[i] = false;
+        }
+    }
+    const int slot = c->pin_next;
+    c->pin_next = (slot + 1) % Ctx::NPIN;
+    if (c->pin_used[slot]) CK(cudaEventSynchronize(c->pin_ev[slot]));
+    char *h = c->pin_buf + (size_t)slot * c->pin_cap;
+    size_t off = 0;
+    for (const H2D &x : parts) {
+        if (x.bytes == 0) continue;
+        memcpy(h + off, x.src, x.bytes);
+        CK(cudaMemcpyAsync(x.dst, h + off, x.bytes, cudaMemcpyHostToDevice, c->stream));
+        off += (x.bytes + 15) / 16 * 16;
+    }
+    CK(cudaEventRecord(c->pin_ev[slot], c->stream));
+    c->pin_used[slot] = true;
+    return QMCDU_OK;
 }
 
 static bool is_device_ptr(const void *p)
@@ -210,7 +257,7 @@ static int do_recompute(Ctx *c, int have_old)
 static int do_ratio(Ctx *c, const RatioLaunch &L)
 {
     CK(launch_ratio(*c, L));
-    c->n_launch += 1;
+    c->n_launch += 3;          // stage, dots, finish
     c->n_ratio += 1;
     return QMCDU_OK;
 }
@@ -375,11 +422,13 @@ int qmcdu_ratio(qmcdu_t h, const int *elec, const double *v, double *ratio_out)
         int st = flush_all(c);
         if (st) return st;
     }
-    CK(cudaMemcpyAsync(c->elec_d, elec, c->batch * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    int st0 = stage_h2d(c, {{c->elec_d, elec, c->batch * sizeof(int)}});
+    if (st0) return st0;
     RatioLaunch L{};
     L.v_in = v;
     L.elec = c->elec_d;
     L.ratio_out = ratio_out;
+    L.kmax = *std::max_element(c->h_k.begin(), c->h_k.end());
     int st = do_ratio(c, L);
     if (st) return st;
     std::copy(elec, elec + c->batch, c->h_elec.begin());
@@ -392,7 +441,8 @@ int qmcdu_accept(qmcdu_t h, const unsigned char *mask)
     if (!h || !mask) return QMCDU_ERR_ARG;
     Ctx *c = reinterpret_cast<Ctx *>(h);
     if (!c->pending) return fail(c, QMCDU_ERR_STATE, "accept without a pending ratio%s");
-    CK(cudaMemcpyAsync(c->mask_d, mask, c->batch, cudaMemcpyHostToDevice, c->stream));
+    int st0 = stage_h2d(c, {{c->mask_d, mask, (size_t)c->batch}});
+    if (st0) return st0;
     AcceptLaunch L{};
     L.mode = 0;
     L.mask = c->mask_d;
@@ -497,6 +547,7 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
     for (int j = 0; j < N; ++j) {
         RatioLaunch R{};
         R.uniform_elec = j;
+        R.kmax = K == 1 ? 0 : std::min(kub, K - 1);
         R.generate = 1;
         R.seed = base_seed;
         R.sweep = sweep_index;
@@ -937,10 +988,8 @@ int qmcdu_load_walkers(qmcdu_t h, int first, int count, const double *A,
                              N * sizeof(double), N * sizeof(double), N * count, cudaMemcpyDefault,
                              c->stream));
     } else {
-        // staged through pageable memory: the caller's array may change on return
-        std::vector<unsigned long long> hs(seeds, seeds + count);
-        CK(cudaMemcpyAsync(c->d_lseed, hs.data(), count * sizeof(unsigned long long),
-                           cudaMemcpyHostToDevice, c->stream));
+        st = stage_h2d(c, {{c->d_lseed, seeds, count * sizeof(unsigned long long)}});
+        if (st) return st;
         CK(launch_init_matrix(*c, first, count, c->d_lseed));
         c->n_launch += 1;
     }
@@ -989,13 +1038,11 @@ int qmcdu_sweep_walkers(qmcdu_t h, int count, const int *walkers, const unsigned
     int st = flush_all(c);
     if (st) return st;
     c->pending = false;
-    // staged through pageable memory: the caller's arrays may change on return
-    std::vector<int> hl(walkers, walkers + count), hw(sweeps, sweeps + count);
-    std::vector<unsigned long long> hs(seeds, seeds + count);
-    CK(cudaMemcpyAsync(c->d_wlist, hl.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_wseed, hs.data(), count * sizeof(unsigned long long),
-                       cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_wsweep, hw.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    // copied into pinned staging before the call returns: the caller's arrays may change
+    st = stage_h2d(c, {{c->d_wlist, walkers, count * sizeof(int)},
+                       {c->d_wseed, seeds, count * sizeof(unsigned long long)},
+                       {c->d_wsweep, sweeps, count * sizeof(int)}});
+    if (st) return st;
     CK(cudaMemsetAsync(c->sw_ties, 0, count * sizeof(long long), c->stream));
     SweepLaunch S{};
     S.sigma = sigma;

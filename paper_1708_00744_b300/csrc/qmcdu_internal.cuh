@@ -44,6 +44,7 @@ struct Ctx {
     int *sign = nullptr;        // batch
     double *rs = nullptr;       // batch x rs_stride(K)
     double *partial = nullptr;  // batch x nsplit x (2K+1)
+    double *ratio_scr = nullptr; // batch x ceil(K/32) x (K+1): shares of the ratio's k x k pass
     unsigned *arrive = nullptr; // batch
     unsigned char *acc = nullptr; // batch: decision of the last resolved proposal
     int *elec_d = nullptr;      // batch
@@ -101,6 +102,14 @@ struct Ctx {
     unsigned long long *d_wseed = nullptr;
     int *d_wsweep = nullptr;
     unsigned long long *d_lseed = nullptr;   // keys of qmcdu_load_walkers' draws
+    // pinned staging ring for small host-to-device argument copies (a copy
+    // from pageable memory would make the host wait for the stream first)
+    static constexpr int NPIN = 16;
+    char *pin_buf = nullptr;
+    size_t pin_cap = 0;                      // bytes per slot
+    int pin_next = 0;
+    cudaEvent_t pin_ev[NPIN] = {};
+    bool pin_used[NPIN] = {};
     // qmcdu_step: device parameter block and per-sweep outputs, graph cache
     unsigned long long *d_params = nullptr;   // [0] base seed, [1] first sweep index
     unsigned char *step_acc = nullptr;        // nsweeps x batch x N
@@ -148,6 +157,7 @@ struct RatioLaunch {
     int sweep;
     double sigma;
     double *ratio_out;          // device [batch] or null
+    int kmax = -1;              // largest queue length of any walker (-1: K - 1)
 };
 cudaError_t launch_ratio(Ctx &c, const RatioLaunch &L);
 
