@@ -350,8 +350,13 @@ int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v, c
  *   B  device, N x K with B(n, k) at B[n*ldb + k]; or, b_trans = 1, K x N with
  *      B(n, k) at B[k*ldb + n]
  *   C  device, M x N, C(m, n) at C[m*ldc + n]
- * Asynchronous on `stream`. ERR_ARG for negative sizes, short leading
- * dimensions or null pointers (text at qmcdu_last_error(NULL)).
+ * Asynchronous on `stream`. For N > 128 and K > 0 the operands are first split
+ * once into bf16 planes laid out as tensor-core tiles (a workspace of
+ * 4 (M + N) K bytes, rounded up to whole 128 x 32 / 256 x 32 tiles, from a
+ * memory pool the library keeps per device and never shrinks), then streamed
+ * by bulk copies through a 4-stage pipeline; narrower products split on the
+ * fly. ERR_ARG for negative sizes, short leading dimensions or null pointers
+ * (text at qmcdu_last_error(NULL)).
  */
 int qmcdu_gemm_bf16x3(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
                       int b_trans, float *C, int ldc, float alpha, float beta, void *stream);

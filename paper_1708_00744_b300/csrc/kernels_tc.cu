@@ -19,6 +19,10 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "qmcdu_internal.cuh"
 
 namespace qmcdu {
@@ -288,6 +292,283 @@ static cudaError_t launch_bn(const Args &g, int batch, cudaStream_t s)
 
 }  // namespace tc
 
+// ---------------------------------------------------------------------------
+// The plain contraction (one matrix, no per-batch k) with operands split once:
+//   * tc2_split_kernel writes each fp32 operand as bf16 hi and lo planes,
+//     already in the tensor cores' K-major core-matrix layout, tile by tile
+//     (A: 128-row tiles, B: 256-row tiles, 32 columns of K each; a tile's hi
+//     plane, then its lo plane, contiguous), zero-padded to whole tiles;
+//   * tc2_gemm_kernel streams those tiles into a 4-stage shared-memory ring
+//     with one bulk copy per operand per stage (producer warp, "full"
+//     mbarriers counting bytes), one thread issues the three MMAs per K-step of
+//     16 into a 128 x 256 fp32 accumulator in tensor memory and commits each
+//     stage to its "empty" mbarrier, and four warps apply alpha / beta.
+namespace tc2 {
+
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
+constexpr int THREADS = 192;    // warp 0 producer, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t A_TILE = BM * BK * 2;          // bytes of one bf16 plane of an A tile
+constexpr uint32_t B_TILE = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256;
+
+// Split rows x cols of X (row r, column k at X[r * ldr + k * ldc]) into tiles of
+// R rows: tile (r / R, k / BK) at ((r / R) * nkb + k / BK) * 2 * R * BK * 2 bytes.
+// One thread per 8 consecutive k of a row: one 16-byte row of a core matrix
+// in each plane, written with one vector store.
+template <int R>
+__global__ void tc2_split_kernel(const float *X, long long ldr, long long ldc, int rows, int cols,
+                                 int nkb, unsigned char *out, long long total)
+{
+    const long long per_row = (long long)nkb * (BK / 8);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / per_row);
+        const int k0 = (int)(e - (long long)r * per_row) * 8;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const int k = k0 + j;
+            const float x0 = (r < rows && k < cols) ? __ldg(X + r * ldr + (long long)k * ldc) : 0.f;
+            const float x1 = (r < rows && k + 1 < cols) ? __ldg(X + r * ldr + (long long)(k + 1) * ldc) : 0.f;
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            hw[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const int rt = r / R, rr = r - rt * R, kt = k0 / BK, kk = k0 - kt * BK;
+        unsigned char *tile = out + ((size_t)rt * nkb + kt) * (size_t)(2 * R * BK * 2);
+        const uint32_t o = tc::core_off(rr, kk);
+        *reinterpret_cast<uint4 *>(tile + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(tile + R * BK * 2 + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+struct Args2 {
+    int M, N, K, nkb;
+    const __nv_bfloat16 *At, *Bt;     // split tiles
+    float *C;
+    long long ldc;
+    float alpha, beta;
+    int *status;
+    long long budget_ns;
+};
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(tc::su32(dst)), "l"(src), "r"(bytes), "r"(tc::su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(tc::su32(bar)), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1) tc2_gemm_kernel(Args2 g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *ring = smem_raw;                                        // [STAGES][STAGE_BYTES]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_s = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int abort_s, issued_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = g.nkb;
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tc::su32(tmem_s)), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::bar_init(&full[s], 1);
+            tc::bar_init(&empty[s], 1);
+        }
+        tc::bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+        issued_s = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_s;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        const unsigned char *Ab = reinterpret_cast<const unsigned char *>(g.At) +
+                                  (size_t)blockIdx.x * nk * (2 * A_TILE);
+        const unsigned char *Bb = reinterpret_cast<const unsigned char *>(g.Bt) +
+                                  (size_t)blockIdx.y * nk * (2 * B_TILE);
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !tc::bar_wait(&empty[s], ((kb / STAGES) - 1) & 1, g.budget_ns)) {
+                abort_s = 1;
+                break;
+            }
+            if (*(volatile int *)&abort_s) break;
+            unsigned char *st = ring + (size_t)s * STAGE_BYTES;
+            expect_tx(&full[s], STAGE_BYTES);
+            bulk_copy(st, Ab + (size_t)kb * (2 * A_TILE), 2 * A_TILE, &full[s]);
+            bulk_copy(st + 2 * A_TILE, Bb + (size_t)kb * (2 * B_TILE), 2 * B_TILE, &full[s]);
+        }
+        issued_s = kb;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = tc::idesc_bf16(BM, BN);
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!tc::bar_wait(&full[s], (kb / STAGES) & 1, g.budget_ns) || *(volatile int *)&abort_s) {
+                abort_s = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = tc::su32(ring + (size_t)s * STAGE_BYTES);
+            const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = bh + B_TILE;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint32_t koff = (uint32_t)(2 * ks) * 128u;
+                const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                tc::mma_bf16(tmem, tc::sdesc(ah + koff, tc::LBO, tc::SBO),
+                             tc::sdesc(bh + koff, tc::LBO, tc::SBO), idesc, first);
+                tc::mma_bf16(tmem, tc::sdesc(ah + koff, tc::LBO, tc::SBO),
+                             tc::sdesc(bl + koff, tc::LBO, tc::SBO), idesc, 1u);
+                tc::mma_bf16(tmem, tc::sdesc(al + koff, tc::LBO, tc::SBO),
+                             tc::sdesc(bh + koff, tc::LBO, tc::SBO), idesc, 1u);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(done);      // arrives once every MMA issued above has completed
+    }
+
+    // epilogue warps wait for the accumulator; everyone then meets
+    bool ok = true;
+    if (warp >= 2) ok = tc::bar_wait(done, 0, g.budget_ns);
+    __syncthreads();
+    if (!ok || abort_s) {
+        // let every issued copy and MMA finish (bounded) before the memory goes away
+        if (threadIdx.x == 0) {
+            const int n = issued_s;
+            for (int kb = (n > STAGES ? n - STAGES : 0); kb < n; ++kb)
+                tc::bar_wait(&full[kb % STAGES], (kb / STAGES) & 1, g.budget_ns);
+            tc::bar_wait(done, 0, g.budget_ns);
+            if (g.status) atomicOr(g.status, ST_TIMEOUT);
+        }
+    } else if (warp >= 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int q = warp & 3;                    // TMEM lanes 32q .. 32q+31
+        const int row = m0 + q * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            if (n0 + c0 >= g.N) break;
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                  "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < g.M) {
+                float *dst = g.C + (size_t)row * g.ldc + n0 + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (n0 + c0 + j >= g.N) break;
+                    float v = g.alpha * __uint_as_float(r[j]);
+                    if (g.beta != 0.f) v += g.beta * dst[j];
+                    dst[j] = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+// Workspace of the split operands: a memory pool of the library's own per device
+// that keeps what it has reserved (release threshold unbounded), so that
+// repeated calls neither synchronise nor map memory again.
+static cudaError_t workspace_pool(cudaMemPool_t *out)
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+static cudaError_t launch(int M, int N, int K, const float *A, long long lda, const float *B,
+                          long long ldb, int b_trans, float *C, long long ldc, float alpha,
+                          float beta, int *status, long long budget_ns, cudaStream_t s)
+{
+    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN, nkb = (K + BK - 1) / BK;
+    const size_t a_elems = (size_t)mt * nkb * 2 * BM * BK, b_elems = (size_t)nt * nkb * 2 * BN * BK;
+    __nv_bfloat16 *ws = nullptr;
+    cudaMemPool_t pool;
+    cudaError_t e = workspace_pool(&pool);
+    if (e == cudaSuccess)
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ws),
+                                    (a_elems + b_elems) * sizeof(__nv_bfloat16), pool, s);
+    if (e != cudaSuccess) return e;
+    // one thread per 8 elements of a row
+    const long long at = (long long)mt * BM * nkb * (BK / 8), bt = (long long)nt * BN * nkb * (BK / 8);
+    unsigned char *wa = reinterpret_cast<unsigned char *>(ws);
+    unsigned char *wb = reinterpret_cast<unsigned char *>(ws + a_elems);
+    tc2_split_kernel<BM><<<(int)std::min<long long>((at + 255) / 256, 148 * 16), 256, 0, s>>>(
+        A, lda, 1, M, K, nkb, wa, at);
+    if (b_trans)    // B(n, k) at B[k * ldb + n]
+        tc2_split_kernel<BN><<<(int)std::min<long long>((bt + 255) / 256, 148 * 16), 256, 0, s>>>(
+            B, 1, ldb, N, K, nkb, wb, bt);
+    else
+        tc2_split_kernel<BN><<<(int)std::min<long long>((bt + 255) / 256, 148 * 16), 256, 0, s>>>(
+            B, ldb, 1, N, K, nkb, wb, bt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc2_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SMEM);
+    if (e == cudaSuccess) {
+        Args2 g{M, N, K, nkb, ws, ws + a_elems, C, ldc, alpha, beta, status, budget_ns};
+        tc2_gemm_kernel<<<dim3(mt, nt), THREADS, SMEM, s>>>(g);
+        e = cudaGetLastError();
+    }
+    cudaError_t f = cudaFreeAsync(ws, s);
+    return e != cudaSuccess ? e : f;
+}
+
+}  // namespace tc2
+
 // C = alpha A B' + beta C in split-bf16 x3 on tcgen05 (see the file comment).
 cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long lda, long long sA,
                                const float *B, long long ldb, long long sB, int b_trans, float *C,
@@ -305,6 +586,10 @@ cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long ld
     g.fix_idx = fix_idx; g.fix_stride = fix_stride;
     g.status = status; g.budget_ns = budget_ns;
     if (M <= 0 || N <= 0 || K < 0 || batch <= 0) return cudaSuccess;
+    // one plain matrix: operands split once, a TMA-fed pipeline
+    if (batch == 1 && !kdyn && !fix_idx && K > 0 && N > 128)
+        return tc2::launch(M, N, K, A, lda, B, ldb, b_trans, C, ldc, alpha, beta, status,
+                           budget_ns, s);
     // narrow N (a short queue) takes a narrower tile
     if (N <= 64) return tc::launch_bn<64>(g, batch, s);
     if (N <= 128) return tc::launch_bn<128>(g, batch, s);
