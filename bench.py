@@ -99,8 +99,9 @@ def parse():
 
 def workload_name(a):
     if a.workload == "ksweep":
-        return ("one fp64 walker, N in {%s}, K in {1, 16, 32, 64, 128, 256}, sigma 0.1 and 1.0 "
-                "and forced acceptance; median of %d single sweeps per point" % (a.ksweep_N, a.reps))
+        return ("one %s walker, N in {%s}, K in {1, 16, 32, 64, 128, 256}, sigma 0.1 and 1.0 "
+                "and forced acceptance; median of %d single sweeps per point"
+                % (a.precision, a.ksweep_N, a.reps))
     if a.workload == "kernels":
         return "kernel microbenchmarks: batched ratio, split-bf16 GEMM, fp64 recompute"
     if a.workload == "serve":
@@ -405,7 +406,7 @@ def run_ksweep(a):
             for K in (1, 16, 32, 64, 128, 256):
                 if K > N:
                     continue
-                W = Walkers(N, K, "fp64", 1, stream=st)
+                W = Walkers(N, K, a.precision, 1, stream=st)
                 W.set_matrix(A0)
                 ov = ones if mode == "forced" else None
                 W.sweep(a.seed, 0, sigma, override=ov, accepted_out=acc)     # warm-up
