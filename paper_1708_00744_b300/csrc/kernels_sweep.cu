@@ -141,13 +141,17 @@ __device__ __forceinline__ T warp_allsum(T v)
     return v;
 }
 
-// Flush for a short queue (k < SMALL_K, including Sherman-Morrison at K = 1):
-// one warp per column, a dot-product pass and an update pass over the column
-// in global memory (no staging).
+// Flush for a short queue (k < SMALL_K, including Sherman-Morrison at K = 1).
+// The CTA takes its columns in batches of SCB: every thread walks rows
+// i = tid, tid + STHREADS, ... of all the batch's columns, so that each V and W
+// element is read once per batch and the reads of the batch's columns are in
+// flight together; the column sums are reduced over the warps in shared
+// memory, then every thread updates its rows of the batch's columns.
 constexpr int SMALL_K = 4;
+constexpr int SCB = 8;
 
-template <typename T>
-__device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c_begin, int c_end)
+template <typename T, int KK>
+__device__ void flush_columns_small_k(const SweepParams<T> &p, int w, int c_begin, int c_end)
 {
     const int N = p.N, ld = p.ld, K = p.K;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
@@ -156,33 +160,76 @@ __device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c
     const T *Wb = p.W + (size_t)w * wK;
     const int *idxw = p.idx + (size_t)w * K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c = c_begin + warp; c < c_end; c += SWARPS) {
-        T *xc = Ab + (size_t)c * ld;
-        T t[SMALL_K];
+    __shared__ T part[SWARPS][SCB * SMALL_K];
+    __shared__ T tsum[SCB * SMALL_K];
+    for (int cb = c_begin; cb < c_end; cb += SCB) {
+        const int nc = min(SCB, c_end - cb);
+        T t[SCB][KK];
 #pragma unroll
-        for (int m = 0; m < SMALL_K; ++m) t[m] = 0;
-#pragma unroll 4
-        for (int i = lane; i < N; i += 32) {
-            const T x = __ldcg(xc + i);
+        for (int c = 0; c < SCB; ++c)
 #pragma unroll
-            for (int m = 0; m < SMALL_K; ++m)
-                if (m < k) t[m] += __ldcg(Vb + (size_t)m * ld + i) * x;
+            for (int m = 0; m < KK; ++m) t[c][m] = 0;
+#pragma unroll 2
+        for (int i = threadIdx.x; i < N; i += STHREADS) {
+            T vv[KK];
+#pragma unroll
+            for (int m = 0; m < KK; ++m) vv[m] = __ldcg(Vb + (size_t)m * ld + i);
+#pragma unroll
+            for (int c = 0; c < SCB; ++c) {
+                if (c < nc) {
+                    const T x = __ldcg(Ab + (size_t)(cb + c) * ld + i);
+#pragma unroll
+                    for (int m = 0; m < KK; ++m) t[c][m] += vv[m] * x;
+                }
+            }
         }
 #pragma unroll
-        for (int m = 0; m < SMALL_K; ++m) {
-            t[m] = warp_allsum(t[m]);
-            if (m < k && __ldcg(idxw + m) == c) t[m] -= (T)1;
-        }
-#pragma unroll 4
-        for (int i = lane; i < N; i += 32) {
-            T acc = 0;
+        for (int c = 0; c < SCB; ++c)
 #pragma unroll
-            for (int m = 0; m < SMALL_K; ++m)
-                if (m < k) acc += t[m] * __ldcg(Wb + (size_t)m * ld + i);
-            xc[i] = __ldcg(xc + i) - acc;
+            for (int m = 0; m < KK; ++m)
+                if (c < nc) {
+                    const T v = warp_allsum(t[c][m]);
+                    if (lane == 0) part[warp][c * SMALL_K + m] = v;
+                }
+        __syncthreads();
+        if (threadIdx.x < SCB * SMALL_K) {
+            const int c = threadIdx.x / SMALL_K, m = threadIdx.x - c * SMALL_K;
+            T sum = 0;
+            if (c < nc && m < KK) {
+#pragma unroll
+                for (int q = 0; q < SWARPS; ++q) sum += part[q][threadIdx.x];
+                if (__ldcg(idxw + m) == cb + c) sum -= (T)1;
+            }
+            tsum[threadIdx.x] = sum;
         }
+        __syncthreads();
+#pragma unroll 2
+        for (int i = threadIdx.x; i < N; i += STHREADS) {
+            T ww[KK];
+#pragma unroll
+            for (int m = 0; m < KK; ++m) ww[m] = __ldcg(Wb + (size_t)m * ld + i);
+#pragma unroll
+            for (int c = 0; c < SCB; ++c) {
+                if (c < nc) {
+                    T acc = 0;
+#pragma unroll
+                    for (int m = 0; m < KK; ++m) acc += ww[m] * tsum[c * SMALL_K + m];
+                    T *xc = Ab + (size_t)(cb + c) * ld + i;
+                    *xc = __ldcg(xc) - acc;
+                }
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
+}
+
+// k = 1, 2 or 3 queued moves: the arithmetic for exactly k terms
+template <typename T>
+__device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c_begin, int c_end)
+{
+    if (k == 1) flush_columns_small_k<T, 1>(p, w, c_begin, c_end);
+    else if (k == 2) flush_columns_small_k<T, 2>(p, w, c_begin, c_end);
+    else flush_columns_small_k<T, 3>(p, w, c_begin, c_end);
 }
 
 // Flush of walker w on columns [c_begin, c_end): tiles of nc <= cb columns.
