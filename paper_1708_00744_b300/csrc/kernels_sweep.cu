@@ -70,6 +70,7 @@ struct SweepParams {
     int stall;              // test hook: the first ratio barrier waits for one CTA too many
     int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm, off_bar;
     int kp;                         // tensor-core flush: K rounded up to 16 (<= 64)
+    int block_ok;                   // the xs region holds flush_block's tiles
     unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
     const int *wlist;               // optional [nw]: the walkers this launch sweeps (else 0..nw)
     int nw;
@@ -230,6 +231,115 @@ __device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c
     if (k == 1) flush_columns_small_k<T, 1>(p, w, c_begin, c_end);
     else if (k == 2) flush_columns_small_k<T, 2>(p, w, c_begin, c_end);
     else flush_columns_small_k<T, 3>(p, w, c_begin, c_end);
+}
+
+// Flush of walker w on a wide column block [c_begin, c_end) (fp64, K <= 64): a
+// register-tiled GEMM in two phases per tile of BT = 64 columns, so that the
+// queue panels V and W are read once per 64 columns (not once per few columns).
+//   T' = V A^{-1}[:, tile]: rows i in chunks of BI1 = 32, V^t and the tile's rows
+//        staged in shared memory (row stride BT + 1: the transposing stores hit
+//        distinct banks), each thread a 4 x 4 block of (m, c);
+//   T  = T' - E^t (selector), kept in shared memory;
+//   A^{-1}[:, tile] -= W^t T: rows i in chunks of BI2 = 64, W staged, each thread
+//        a 4 x 4 block of (i, c) with the lanes along i, so that a half-warp's
+//        read-modify-write of a column is 64 consecutive rows.
+// Shared memory: 2 * 64 * 64 elements of T at off_xs.
+constexpr int BT = 64, BI1 = 32, BI2 = 64, SLD = BT + 1;
+
+template <typename T>
+__device__ void flush_block(const SweepParams<T> &p, int w, int k, int c_begin, int c_end,
+                            unsigned char *smem)
+{
+    const int N = p.N, ld = p.ld, K = p.K;
+    const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
+    T *Ab = p.Ainv + (size_t)w * wN;
+    const T *Vb = p.V + (size_t)w * wK;
+    const T *Wb = p.W + (size_t)w * wK;
+    const int *idxw = p.idx + (size_t)w * K;
+    T *Vs = (T *)(smem + p.off_xs);        // [BI1][SLD] : V^t chunk, Vs[ci][m]
+    T *As = Vs + BI1 * SLD;                // [BI1][SLD] : A^{-1} chunk, As[ci][c]
+    T *Ts = Vs;                            // [BT][BT]   : T[m][c] (after phase 1)
+    T *Ws = Vs + BT * BT;                  // [BT][BI2]  : W chunk, Ws[m][ii]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads
+    for (int c0 = c_begin; c0 < c_end; c0 += BT) {
+        const int nc = min(BT, c_end - c0);
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+        // ---- phase 1: T'[m][c] = sum_i V[m][i] A^{-1}[i][c0 + c]   (m = ty*4+u, c = tx*4+v)
+        for (int i0 = 0; i0 < N; i0 += BI1) {
+            __syncthreads();
+            // stage: consecutive threads take consecutive i of one row / column
+            for (int e = threadIdx.x; e < BT * BI1; e += STHREADS) {
+                const int r = e / BI1, ci = e - r * BI1, i = i0 + ci;
+                Vs[ci * SLD + r] = (r < k && i < N) ? __ldcg(Vb + (size_t)r * ld + i) : (T)0;
+                As[ci * SLD + r] = (r < nc && i < N) ? __ldcg(Ab + (size_t)(c0 + r) * ld + i) : (T)0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int ci = 0; ci < BI1; ++ci) {
+                T a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = Vs[ci * SLD + ty * 4 + q];
+                    b[q] = As[ci * SLD + tx * 4 + q];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+            }
+        }
+        __syncthreads();
+        // ---- T = T' - E^t into shared memory
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = ty * 4 + u;
+            const int im = m < k ? __ldcg(idxw + m) : -1;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int c = tx * 4 + v;
+                Ts[m * BT + c] = (m < k && c < nc) ? acc[u][v] - (im == c0 + c ? (T)1 : (T)0) : (T)0;
+            }
+        }
+        // ---- phase 2: A^{-1}[i][c0 + c] -= sum_m W[m][i] T[m][c]   (i = tx*4+u, c = ty*4+v)
+        for (int i0 = 0; i0 < N; i0 += BI2) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < BT * BI2; e += STHREADS) {
+                const int m = e / BI2, ii = e - m * BI2, i = i0 + ii;
+                Ws[m * BI2 + ii] = (m < k && i < N) ? __ldcg(Wb + (size_t)m * ld + i) : (T)0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+            for (int m = 0; m < k; ++m) {
+                T a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = Ws[m * BI2 + tx * 4 + q];
+                    b[q] = Ts[m * BT + ty * 4 + q];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int c = ty * 4 + v;
+                if (c >= nc) continue;
+                T *col = Ab + (size_t)(c0 + c) * ld + i0 + tx * 4;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + tx * 4 + u < N) col[u] = __ldcg(col + u) - acc[u][v];
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // Flush of walker w on columns [c_begin, c_end): tiles of nc <= cb columns.
@@ -590,6 +700,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
                 } else if (k > 0 && k < SMALL_K) {
                     flush_columns_small(p, w, k, fc0, fc1);
+                } else if (k > 0 && p.block_ok && fc1 - fc0 >= BT) {
+                    flush_block(p, w, k, fc0, fc1, smem);
                 } else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) {
                     return;
                 }
@@ -853,6 +965,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
             } else if (k > 0 && k < SMALL_K) {
                 flush_columns_small(p, w, k, fc0, fc1);
+            } else if (k > 0 && p.block_ok && fc1 - fc0 >= BT) {
+                flush_block(p, w, k, fc0, fc1, smem);
             } else if (k > 0 && !flush_columns(p, w, k, fc0, fc1, smem, bar_phase)) {
                 return;
             }
@@ -970,7 +1084,7 @@ __global__ void sweep_logdet_kernel(int N, const int *wlist, const unsigned char
 static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 template <typename T>
-static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, int *offs)
+static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, bool block, int *offs)
 {
     size_t o = 0;
     offs[8] = (int)o; o = align16(o + 16);                                   // mbarrier
@@ -980,7 +1094,9 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, in
     offs[3] = (int)o; o = align16(o + (size_t)(2 * K + 1) * sizeof(double)); // red
     offs[4] = (int)o; o = align16(o + (size_t)std::max(K * cb, 2 * K + chunk) * sizeof(T));  // ts
     offs[5] = (int)o;                                                        // xs / tc region
-    o = align16(o + (tc ? tcf::region_bytes((K + 15) / 16 * 16) : (size_t)cb * ld * sizeof(T)));
+    size_t xs_bytes = (size_t)cb * ld * sizeof(T);
+    if (block) xs_bytes = std::max(xs_bytes, (size_t)std::max(2 * BT * BT, 2 * BI1 * SLD) * sizeof(T));
+    o = align16(o + (tc ? tcf::region_bytes((K + 15) / 16 * 16) : xs_bytes));
     offs[6] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Wsm
     offs[7] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Vsm
     return o;
@@ -995,10 +1111,23 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     const int K = c.K;
     int offs[9];
     int cb = MAX_CB;
-    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, offs);
+    // the wide-block flush (fp64, K <= 64) when its tiles fit beside everything
+    // else: fp64 arithmetic hides its staging; in fp32 (one CTA of 8 warps per SM)
+    // the staging latency does not hide and the column tiles are as fast
+    bool block = !TC && K <= BT && std::is_same<T, double>::value;
+    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
     while (cb > 1 && smem > SMEM_BUDGET) {
         cb >>= 1;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+    }
+    if (smem > SMEM_BUDGET && block) {
+        block = false;
+        cb = MAX_CB;
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+        while (cb > 1 && smem > SMEM_BUDGET) {
+            cb >>= 1;
+            smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+        }
     }
     if (smem > SMEM_BUDGET) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, TC>,
@@ -1029,6 +1158,7 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.off_ts = offs[4]; p.off_xs = offs[5]; p.off_wsm = offs[6]; p.off_vsm = offs[7];
     p.off_bar = offs[8];
     p.kp = (K + 15) / 16 * 16;
+    p.block_ok = block ? 1 : 0;
     p.phase_ns = c.prof ? c.sw_phase : nullptr;
     p.wlist = L.wlist;
     p.nw = nw;
