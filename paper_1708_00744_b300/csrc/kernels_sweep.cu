@@ -514,14 +514,41 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t *r)
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// shared-memory region of the tensor-core flush, for kp = K rounded up to 16
+// shared-memory region of the tensor-core flush, for kp = K rounded up to 16:
+// two stages of the T' operands (A^{-1} and V blocks), T as the update's B
+// operand, two stages of the update's W block, four mbarriers
 __host__ __device__ inline size_t region_bytes(int kp)
 {
-    return (size_t)2 * 2 * BM * BK * 2 + (size_t)2 * 2 * kp * BK * 2 + (size_t)2 * BM * kp * 2 * 2 +
-           4 * sizeof(unsigned long long);
+    return (size_t)2 * 2 * BM * BK * 2 + (size_t)2 * 2 * kp * BK * 2 + (size_t)2 * BM * kp * 2 +
+           (size_t)2 * 2 * BM * kp * 2 + 4 * sizeof(unsigned long long);
+}
+// eight floats as bf16 hi and lo, packed for one 16-byte store per plane
+__device__ __forceinline__ void split8(const float *x, uint4 &hi, uint4 &lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * j]), h1 = __float2bfloat16_rn(x[2 * j + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * j] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * j + 1] - __bfloat162float(h1));
+        h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 }  // namespace tcf
 
+// Eq. 4 on the tensor cores for walker w's columns [c_begin, c_end), tiles of
+// BM = 128 columns (split-bf16 x3, fp32 accumulators in tensor memory):
+//   T'[c][m] = sum_i A^{-1}[i][c] V[m][i]   M = 128 columns, N = kp, K = N in
+//       blocks of 32; the CTA splits the next block's operands (eight elements per
+//       thread, 16-byte stores) while the MMAs of the current one run;
+//   T = T' - E^t, read back from tensor memory into the B operand of
+//   D[i][c] = sum_m W[m][i] T[m][c]        M = 128 rows i, N = 128 columns, K = kp;
+//       the W block of the next 128 rows is split while the MMAs run, and with
+//       the rows of A^{-1} along the tensor-memory lanes the read-modify-write
+//       A^{-1}[c][i] -= D[i][c] is coalesced across each warp.
 // Returns false after a wait ran out of budget (ST_TIMEOUT recorded).
 template <typename T>
 __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int c_end,
@@ -530,15 +557,15 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
     using namespace tcf;
     const int N = p.N, ld = p.ld, K = p.K, KP = p.kp;
     unsigned char *reg = smem + p.off_xs;
-    __nv_bfloat16 *a1h = (__nv_bfloat16 *)reg;                    // [2][BM*BK]
+    __nv_bfloat16 *a1h = (__nv_bfloat16 *)reg;                    // [2][BM*BK]  A^{-1} block
     __nv_bfloat16 *a1l = a1h + 2 * BM * BK;
-    __nv_bfloat16 *b1h = a1l + 2 * BM * BK;                      // [2][KP*BK]
+    __nv_bfloat16 *b1h = a1l + 2 * BM * BK;                      // [2][KP*BK]  V block
     __nv_bfloat16 *b1l = b1h + 2 * KP * BK;
-    __nv_bfloat16 *a2h = b1l + 2 * KP * BK;                      // [BM*KP]
-    __nv_bfloat16 *a2l = a2h + BM * KP;
-    __nv_bfloat16 *b2h = a2l + BM * KP;                          // [BM*KP]
-    __nv_bfloat16 *b2l = b2h + BM * KP;
-    unsigned long long *bars = (unsigned long long *)(b2l + BM * KP);
+    __nv_bfloat16 *tbh = b1l + 2 * KP * BK;                      // [BM*KP]     T (rows c)
+    __nv_bfloat16 *tbl = tbh + BM * KP;
+    __nv_bfloat16 *wah = tbl + BM * KP;                          // [2][BM*KP]  W block (rows i)
+    __nv_bfloat16 *wal = wah + 2 * BM * KP;
+    unsigned long long *bars = (unsigned long long *)(wal + 2 * BM * KP);
     __shared__ int ok_s;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     T *Ab = p.Ainv + (size_t)w * wN;
@@ -549,30 +576,93 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
     const int kp = (k + 15) / 16 * 16;
     const uint32_t id1 = idesc(BM, kp), id2 = idesc(BM, BM);
     const int nk = (N + BK - 1) / BK;
+    const uint32_t sbo2 = (uint32_t)(KP / 8) * 128u;
+
+    // staging of T' block kb: thread t covers 8 consecutive i of A^{-1} column
+    // (t / 4 + 64 h) and of V row t / 4 (t % 4 selects the 8-element part)
+    auto load1 = [&](int kb, float (&xa)[2][8], float (&xv)[8], int c0, int nrows) {
+        const int i = kb * BK + (threadIdx.x & 3) * 8;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = (threadIdx.x >> 2) + 64 * h;
+            const bool in = c < nrows && i < ld;     // rows past N are zero padding
+            const float4 *src = reinterpret_cast<const float4 *>(Ab + (size_t)(c0 + c) * ld + i);
+            const float4 u = in ? __ldcg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v = in ? __ldcg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xa[h][0] = u.x; xa[h][1] = u.y; xa[h][2] = u.z; xa[h][3] = u.w;
+            xa[h][4] = v.x; xa[h][5] = v.y; xa[h][6] = v.z; xa[h][7] = v.w;
+        }
+        const int m = threadIdx.x >> 2;
+        const bool in = m < k && i < ld;
+        const float4 *src = reinterpret_cast<const float4 *>(Vb + (size_t)m * ld + i);
+        const float4 u = in ? __ldcg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = in ? __ldcg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xv[0] = u.x; xv[1] = u.y; xv[2] = u.z; xv[3] = u.w;
+        xv[4] = v.x; xv[5] = v.y; xv[6] = v.z; xv[7] = v.w;
+    };
+    auto store1 = [&](int s, const float (&xa)[2][8], const float (&xv)[8]) {
+        const int kk = (threadIdx.x & 3) * 8;
+        uint4 hi, lo;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = (threadIdx.x >> 2) + 64 * h;
+            split8(xa[h], hi, lo);
+            const uint32_t o = coff(c, kk, BK) >> 1;
+            *reinterpret_cast<uint4 *>(a1h + s * BM * BK + o) = hi;
+            *reinterpret_cast<uint4 *>(a1l + s * BM * BK + o) = lo;
+        }
+        const int m = threadIdx.x >> 2;
+        if (m < KP) {
+            split8(xv, hi, lo);
+            const uint32_t o = coff(m, kk, BK) >> 1;
+            *reinterpret_cast<uint4 *>(b1h + s * KP * BK + o) = hi;
+            *reinterpret_cast<uint4 *>(b1l + s * KP * BK + o) = lo;
+        }
+    };
+    // staging of the update's W block (rows i0.., all m): thread t covers 4
+    // consecutive i (t % 32) and 8 consecutive m (t / 32), transposed in registers
+    auto stage2 = [&](int i0, int s) {
+        const int ig = (threadIdx.x & 31) * 4, mg = (threadIdx.x >> 5) * 8;
+        if (mg >= KP) return;
+        float x[4][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int m = mg + j, i = i0 + ig;
+            const bool in = m < k && i < ld;
+            const float4 u = in ? __ldcg(reinterpret_cast<const float4 *>(Wb + (size_t)m * ld + i))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[0][j] = u.x; x[1][j] = u.y; x[2][j] = u.z; x[3][j] = u.w;
+        }
+        uint4 hi, lo;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            split8(x[q], hi, lo);
+            const uint32_t o = coff(ig + q, mg, KP) >> 1;
+            *reinterpret_cast<uint4 *>(wah + s * BM * KP + o) = hi;
+            *reinterpret_cast<uint4 *>(wal + s * BM * KP + o) = lo;
+        }
+    };
+    auto wait_bar = [&](int b) -> bool {
+        if (threadIdx.x == 0) ok_s = mbar_wait(&bars[b], tph[b], p.status, p.budget_ns) ? 1 : 0;
+        __syncthreads();
+        tph[b] ^= 1u;
+        return ok_s != 0;
+    };
+
     for (int c0 = c_begin; c0 < c_end; c0 += BM) {
         const int nrows = min(BM, c_end - c0);
         // ---- T' = X V' over K = N
         int pend[2] = {0, 0};
+        float xa[2][8], xv[8];
+        load1(0, xa, xv, c0, nrows);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb & 1;
             if (pend[s]) {
-                if (threadIdx.x == 0) ok_s = mbar_wait(&bars[s], tph[s], p.status, p.budget_ns) ? 1 : 0;
-                __syncthreads();
-                tph[s] ^= 1u;
+                if (!wait_bar(s)) return false;
                 pend[s] = 0;
-                if (!ok_s) return false;
             }
-            const int k0 = kb * BK;
-            for (int e = threadIdx.x; e < BM * BK; e += STHREADS) {
-                const int r = e / BK, kk = e - r * BK, i = k0 + kk;
-                const float x = (r < nrows && i < N) ? (float)__ldcg(Ab + (size_t)(c0 + r) * ld + i) : 0.f;
-                put(a1h + s * BM * BK, a1l + s * BM * BK, coff(r, kk, BK), x);
-            }
-            for (int e = threadIdx.x; e < kp * BK; e += STHREADS) {
-                const int m = e / BK, kk = e - m * BK, i = k0 + kk;
-                const float x = (m < k && i < N) ? (float)__ldcg(Vb + (size_t)m * ld + i) : 0.f;
-                put(b1h + s * KP * BK, b1l + s * KP * BK, coff(m, kk, BK), x);
-            }
+            store1(s, xa, xv);
+            if (kb + 1 < nk) load1(kb + 1, xa, xv, c0, nrows);    // in flight during the MMAs
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -592,73 +682,75 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
             }
             pend[s] = 1;
         }
-        for (int s = 0; s < 2; ++s) {
-            if (pend[s]) {
-                if (threadIdx.x == 0) ok_s = mbar_wait(&bars[s], tph[s], p.status, p.budget_ns) ? 1 : 0;
-                __syncthreads();
-                tph[s] ^= 1u;
-                if (!ok_s) return false;
-            }
-        }
+        for (int s = 0; s < 2; ++s)
+            if (pend[s] && !wait_bar(s)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- T' (minus the selector E') into shared memory as the A operand of the update
+        // ---- T = T' - E' into shared memory (rows c, K = m): the update's B operand
         if (warp < 4) {
-            const int r = warp * 32 + lane;
+            const int c = warp * 32 + lane;
             for (int m0 = 0; m0 < kp; m0 += 16) {
                 uint32_t v[16];
                 ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)m0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int m = m0 + j;
-                    float t = 0.f;
-                    if (m < k) t = __uint_as_float(v[j]) - (__ldcg(idxw + m) == c0 + r ? 1.f : 0.f);
-                    put(a2h, a2l, coff(r, m, KP), t);
+                for (int half = 0; half < 2; ++half) {
+                    float t[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int m = m0 + half * 8 + j;
+                        t[j] = m < k ? __uint_as_float(v[half * 8 + j]) -
+                                           (__ldcg(idxw + m) == c0 + c ? 1.f : 0.f)
+                                     : 0.f;
+                    }
+                    uint4 hi, lo;
+                    split8(t, hi, lo);
+                    const uint32_t o = coff(c, m0 + half * 8, KP) >> 1;
+                    *reinterpret_cast<uint4 *>(tbh + o) = hi;
+                    *reinterpret_cast<uint4 *>(tbl + o) = lo;
                 }
             }
         }
+        stage2(0, 0);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // ---- X -= T' W, 128 columns of X (entries i of A^{-1}[:, c]) at a time
-        for (int i0 = 0; i0 < N; i0 += BM) {
-            for (int e = threadIdx.x; e < BM * kp; e += STHREADS) {
-                const int m = e / BM, r = e - m * BM, i = i0 + r;
-                const float x = (m < k && i < N) ? (float)__ldcg(Wb + (size_t)m * ld + i) : 0.f;
-                put(b2h, b2l, coff(r, m, KP), x);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+        // ---- X[c][i] -= sum_m W[m][i] T[m][c], 128 rows i at a time
+        const int nblk = (N + BM - 1) / BM;
+        for (int b = 0; b < nblk; ++b) {
+            const int i0 = b * BM, s = b & 1;
             if (threadIdx.x == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sbo = (uint32_t)(KP / 8) * 128u;
                 for (int ks = 0; ks < kp / 16; ++ks) {
                     const uint32_t ko = (uint32_t)ks * 256u;
-                    const uint64_t ah = sdesc(su32(a2h) + ko, 128, sbo);
-                    const uint64_t al = sdesc(su32(a2l) + ko, 128, sbo);
-                    const uint64_t bh = sdesc(su32(b2h) + ko, 128, sbo);
-                    const uint64_t bl = sdesc(su32(b2l) + ko, 128, sbo);
+                    const uint64_t ah = sdesc(su32(wah + s * BM * KP) + ko, 128, sbo2);
+                    const uint64_t al = sdesc(su32(wal + s * BM * KP) + ko, 128, sbo2);
+                    const uint64_t bh = sdesc(su32(tbh) + ko, 128, sbo2);
+                    const uint64_t bl = sdesc(su32(tbl) + ko, 128, sbo2);
                     mma(tmem + 128u, ah, bh, id2, ks == 0 ? 0u : 1u);
                     mma(tmem + 128u, ah, bl, id2, 1u);
                     mma(tmem + 128u, al, bh, id2, 1u);
                 }
                 commit(&bars[2]);
-                ok_s = mbar_wait(&bars[2], tph[2], p.status, p.budget_ns) ? 1 : 0;
             }
-            __syncthreads();
-            tph[2] ^= 1u;
-            if (!ok_s) return false;
+            if (b + 1 < nblk) stage2(i0 + BM, s ^ 1);                // overlaps the MMAs
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (!wait_bar(2)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (warp < 4) {
-                const int r = warp * 32 + lane;
-                T *xrow = Ab + (size_t)(c0 + r) * ld;
-                for (int j0 = 0; j0 < BM; j0 += 16) {
+            // lanes = rows i; warps 0-3 take columns 0..63, warps 4-7 columns 64..127
+            {
+                const int q = warp & 3;
+                const int i = i0 + q * 32 + lane;
+                const int cbeg = (warp >> 2) * 64;
+                for (int j0 = cbeg; j0 < cbeg + 64; j0 += 16) {
                     uint32_t v[16];
-                    ld16(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)j0, v);
-                    if (r < nrows) {
+                    ld16(tmem + ((uint32_t)(q * 32) << 16) + 128u + (uint32_t)j0, v);
+                    if (i < N) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const int i = i0 + j0 + j;
-                            if (i < N) xrow[i] -= (T)__uint_as_float(v[j]);
+                            const int c = j0 + j;
+                            if (c < nrows) {
+                                T *x = Ab + (size_t)(c0 + c) * ld + i;
+                                *x = __ldcg(x) - (T)__uint_as_float(v[j]);
+                            }
                         }
                     }
                 }
@@ -675,7 +767,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 {
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
     if (grp >= p.ngroups) return;
-    unsigned tph[3] = {0, 0, 0};     // phases of the tensor-core flush's mbarriers
+    unsigned tph[4] = {0, 0, 0, 0};  // phases of the tensor-core flush's mbarriers
     const int N = p.N, K = p.K, ld = p.ld, Gf = p.Gf, Gr = p.Gr;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     unsigned *ratio_ctr = p.sync + SYNC_STRIDE * grp + 0;
@@ -986,7 +1078,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 // these CTAs at most share an SM, 2 x 256 = 512 columns), the mbarriers, the
 // sweep, and the release of the tensor memory on every exit path.
 template <typename T, bool RES, bool TC>
-__global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
+__global__ void __launch_bounds__(STHREADS, TC ? 1 : 2) sweep_kernel(SweepParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t tmem_s;
@@ -1000,7 +1092,7 @@ __global__ void __launch_bounds__(STHREADS, 2) sweep_kernel(SweepParams<T> p)
         if (TC) {
             unsigned long long *bars = (unsigned long long *)(smem + p.off_xs + tcf::region_bytes(p.kp) -
                                                               4 * sizeof(unsigned long long));
-            for (int q = 0; q < 3; ++q)
+            for (int q = 0; q < 4; ++q)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
