@@ -1,8 +1,10 @@
 // kernels_move.cu -- per-proposal kernels of the delayed update.
 //
-// ratio_kernel  : determinant ratio of one proposal per walker (Eq. 1 at k = 0,
-//                 Eq. 3 through the queued panels otherwise). HBM-bound GEMV
-//                 class: reads A^{-1}[:, j], v, and the k queued rows of P and V.
+// ratio_stage_kernel, ratio_dots_kernel, ratio_finish_kernel : determinant
+//                 ratio of one proposal per walker (Eq. 1 at k = 0, Eq. 3
+//                 through the queued panels otherwise). GEMV class: reads
+//                 A^{-1}[:, j], v, the k queued rows of P and V (streamed by
+//                 bulk copies) and the k x k Kinv.
 // accept_kernel : Metropolis decision (or a given mask), append to the delay
 //                 queue with the bordered k x k inverse update, new row of A,
 //                 running log|det A|.
@@ -23,7 +25,7 @@ constexpr int RTHREADS = 256;  // 8 warps
 
 template <typename T>
 struct RatioParams {
-    int N, K, ld, jsplit;
+    int N, K, ld;
     const double *A;
     const T *Ainv;
     T *P, *V;
@@ -528,7 +530,7 @@ template <typename T>
 static cudaError_t launch_ratio_t(Ctx &c, const RatioLaunch &L)
 {
     RatioParams<T> p;
-    p.N = c.N; p.K = c.K; p.ld = c.ld; p.jsplit = 1;
+    p.N = c.N; p.K = c.K; p.ld = c.ld;
     p.A = c.A; p.Ainv = (const T *)c.Ainv; p.P = (T *)c.P; p.V = (T *)c.V;
     p.vstash = c.vstash; p.Kinv = c.Kinv; p.kcount = c.kcount; p.rs = c.rs;
     p.partial = c.partial; p.scr = c.ratio_scr; p.arrive = c.arrive; p.status = c.status;

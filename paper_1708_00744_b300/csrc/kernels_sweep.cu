@@ -20,8 +20,11 @@
 //
 // Flush (column c of the column-major A^{-1}, T = V'A^{-1} - E'):
 //   t_m = V[m] . A^{-1}[:, c] - [idx_m == c],   A^{-1}[:, c] -= sum_m t_m W[m].
-// Column tiles are brought into shared memory by bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier).
+// Four implementations, chosen per flush: flush_columns_small (k < 4, K = 1's
+// Sherman-Morrison), flush_block (fp64 column blocks >= 64 wide: a
+// register-tiled GEMM), flush_tc (split-bf16 walkers: tcgen05 with the
+// accumulators in tensor memory), flush_columns (the rest: column tiles brought
+// into shared memory by bulk asynchronous copies, completion on an mbarrier).
 //
 // The proposal Gaussians and Metropolis uniforms of the sweep are drawn up
 // front by a fully parallel kernel (sweep_draw_kernel), and the running
@@ -496,12 +499,6 @@ __device__ __forceinline__ void commit(unsigned long long *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ void put(__nv_bfloat16 *hi, __nv_bfloat16 *lo, uint32_t off, float x)
-{
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[off >> 1] = h;
-    lo[off >> 1] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t *r)
 {
