@@ -219,3 +219,34 @@ def test_server_under_a_tight_budget_evicts_and_finishes():
     assert st["finished"] == len(reqs) and st["failed"] == 0
     assert st["peak_bytes"] <= budget and st["pools_destroyed"] > 0
     srv.close()
+
+
+def test_spin_resolved_walkers_are_two_independent_determinants():
+    """Two determinants per walker (N_up, N_down): each spin's sweep follows
+    the oracle's trajectory for its own matrix and draws, and the walker's
+    log|det| and sign are the sum and the product."""
+    need_gpu()
+    from paper_1708_00744_b300.spin import SpinWalkers
+    n_up, n_down, K, sigma, nsweeps = 96, 80, 16, 0.3, 2
+    seeds = [11, 12]
+    S = SpinWalkers(n_up, n_down, K, "fp64", batch=2)
+    S.load(seeds)
+    acc_u = np.zeros((nsweeps, 2, n_up), dtype=np.uint8)
+    acc_d = np.zeros((nsweeps, 2, n_down), dtype=np.uint8)
+    rat_u = np.zeros((nsweeps, 2, n_up))
+    rat_d = np.zeros((nsweeps, 2, n_down))
+    for s in range(nsweeps):
+        S.sweep(seeds, s, sigma, acc_u[s], acc_d[s], rat_u[s], rat_d[s])
+    la, sg = S.logdet()
+    S.close()
+    for b, seed in enumerate(seeds):
+        tot, sign = 0.0, 1
+        for n, key, acc, rat in ((n_up, seed, acc_u, rat_u), (n_down, seed + (1 << 40), acc_d, rat_d)):
+            A0, U, ref = _oracle_run(key, n, nsweeps, sigma, K)
+            assert _tie_free(ref, U)
+            tol = fp64_tol(A0, ref["A"])
+            assert np.array_equal(acc[:, b].astype(bool), ref["accepted"])
+            assert rel_ratio_err(rat[:, b], ref["ratios"]) < tol
+            tot += ref["logabs"]
+            sign *= ref["sign"]
+        assert sg[b] == sign and logdet_err(la[b], tot) < 1e-9
