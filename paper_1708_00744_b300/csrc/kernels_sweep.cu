@@ -912,20 +912,33 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             tick(1);
             if (!group_wait_for(ratio_ctr, (++n_ratio) * Gr + extra, p.status, p.budget_ns)) return;
             tick(2);
-            // ---- every ratio CTA sums the partials in the same order
+            // ---- every ratio CTA sums the partials in the same order: G
+            // consecutive lanes per job (a power of two up to 8 that the CTA's
+            // threads allow), lane g of the group summing the partials of CTAs
+            // g, g + G, ..., then a fixed shuffle tree over the group
             const double *pb = p.partial + ((size_t)grp * 2 + b) * Gr * nj;
-            for (int job = threadIdx.x; job < 2 * k + 1; job += STHREADS) {
-                double s = 0.0;
-                int q = 0;
-                for (; q + 8 <= Gr; q += 8) {
-                    double x[8];
+            {
+                const int njk = 2 * k + 1;
+                int G = 1;
+                while (G < 8 && 2 * G * njk <= STHREADS) G *= 2;
+                for (int t = threadIdx.x; t < njk * G; t += STHREADS) {
+                    const int job = t / G, g = t - job * G;
+                    double s = 0.0;
+                    int q = g;
+                    for (; q + 7 * G < Gr; q += 8 * G) {
+                        double x[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e) * nj + job);
+                        for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e * G) * nj + job);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) s += x[e];
+                        for (int e = 0; e < 8; ++e) s += x[e];
+                    }
+                    for (; q < Gr; q += G) s += __ldcg(pb + (size_t)q * nj + job);
+                    // groups are whole (njk * G is a multiple of G), so the active
+                    // lanes of the warp hold complete groups
+                    const unsigned act = __activemask();
+                    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(act, s, o, G);
+                    if (g == 0) red[job] = s;
                 }
-                for (; q < Gr; ++q) s += __ldcg(pb + (size_t)q * nj + job);
-                red[job] = s;
             }
             __syncthreads();
             if (warp == 0) {
