@@ -247,6 +247,12 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       most the grid cap). Every walker then gets the same arithmetic, in the
  *       same order, whatever the number of walkers in the launch: its results
  *       are bit-identical alone and in a batch (qmcdu_sweep_walkers, serving)
+ *   QMCDU_OPT_FP64_FLUSH   [0: auto] the persistent sweep's flush (Eq. 4) for
+ *       fp64 walkers: 1 = fp64 arithmetic units only; 2 (and auto) = the
+ *       contraction emulated on the tensor cores (operands cut into six 8-bit
+ *       slices, exact fp32 accumulation of slice products, exact integer
+ *       recombination; about 2^-45 relative to |row| |column|) where it
+ *       applies: K <= 32 and walker groups of two or more CTAs
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {
@@ -256,14 +262,17 @@ enum {
     QMCDU_OPT_WAIT_BUDGET_NS = 4,
     QMCDU_OPT_TEST_STALL = 5,
     QMCDU_OPT_MAX_CTAS = 6,
-    QMCDU_OPT_GROUP_CTAS = 7
+    QMCDU_OPT_GROUP_CTAS = 7,
+    QMCDU_OPT_FP64_FLUSH = 8
 };
 int qmcdu_set_option(qmcdu_t h, int option, long long value);
 
 /*
  * Shape of the last persistent sweep launch (host, 5 ints): CTAs per walker
  * group (flush), ratio CTAs per group, walker groups, rows per ratio CTA,
- * flush column tile.
+ * flush kind: columns per shared-memory tile (> 0 with the queue rows
+ * resident in the ratio CTAs, < 0 without), 1000 for the split-bf16
+ * tensor-core flush, 2000 for the emulated-fp64 tensor-core flush.
  */
 int qmcdu_sweep_shape(qmcdu_t h, int *shape5);
 

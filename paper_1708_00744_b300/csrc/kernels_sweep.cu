@@ -50,6 +50,10 @@ constexpr int STHREADS = 256;
 constexpr int SWARPS = STHREADS / 32;
 constexpr int MAX_CB = 8;
 constexpr int SYNC_STRIDE = 96;   // unsigned words per walker group: three 128-byte lines
+// flush implementations of a sweep kernel instance
+constexpr int FM_SIMT = 0;   // flush_columns_small / flush_block / flush_columns
+constexpr int FM_TC = 1;     // flush_tc (split-bf16 walkers)
+constexpr int FM_OZ = 2;     // flush_oz (fp64 walkers, emulated on the tensor cores)
 
 template <typename T>
 struct SweepParams {
@@ -77,6 +81,9 @@ struct SweepParams {
     unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
     const int *wlist;               // optional [nw]: the walkers this launch sweeps (else 0..nw)
     int nw;
+    unsigned char *oz;              // emulated-fp64 flush: per-group scratch (ozf::layout)
+    size_t oz_stride;               // bytes per walker group
+    int off_tcbar;                  // the tensor-core flush's mbarriers (offset in shared memory)
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -759,7 +766,501 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
     return true;
 }
 
-template <typename T, bool RES, bool TC>
+// ------------------------------------------------------------------------
+// Emulated-fp64 flush on the tensor cores (fp64 walkers).
+//
+// Every fp64 operand x of a contraction is cut into NS = 6 signed 8-bit
+// integer slices relative to a power of two shared by its row or column
+// (Emax: the largest biased exponent of the set):
+//   q = floor(|x| 2^(1070 - Emax)) < 2^48,  q = sum_j s_j 2^(40 - 8j),
+//   x ~ sign(x) 2^(Emax - 1070) q            (48 bits of every operand).
+// A slice is an integer of magnitude <= 255, exact in bf16, and the product of
+// two slices is an integer <= 65025; a tcgen05 MMA with fp32 accumulation sums
+// such products without rounding while every partial sum stays below 2^24.
+// The slice pairs (j, l) with j + l <= 5 (21 products) are accumulated per
+// diagonal d = j + l in tensor memory and recombined exactly in 64-bit
+// integers, which brings the dropped and truncated terms to about 2^-45 of
+// |row| |column| (the order of an fp64 dot product's own rounding bound).
+//
+// The flush of Eq. 4 runs in three phases over all CTAs of the walker group,
+// with a group barrier after each:
+//   A  T'[c][m] = sum_i A^{-1}[i][c] V[m][i]: items of 128 columns x 256 rows
+//      (the contraction split over row chunks); the chunk's column and row
+//      exponents; one product per tensor-memory accumulator for d <= 3 (exact:
+//      256 x 65025 < 2^24), one accumulator each for d = 4 and d = 5 (their
+//      fp32 rounding lies below 2^-53 of the result); partial sums in fp64.
+//   B  T = sum of the partials - E' (fixed order), sliced with one exponent
+//      per column c; W = P Kinv sliced with one exponent per row i; the
+//      slices are written in the tensor cores' K-major tile layout.
+//   C  A^{-1}[i][c] -= sum_m W[m][i] T[m][c]: items of 128 rows x 64 columns,
+//      contraction K <= 32 so that all six diagonals accumulate exactly
+//      (6 x 32 x 65025 < 2^24); S = sum_d D_d 2^(8(5-d)) in int64, then one
+//      fused multiply-add into A^{-1}.
+namespace ozf {
+constexpr int NS = 6;
+constexpr int AM = 128, AR = 256, AK = 32;      // phase A item: columns, rows; rows per K-block
+constexpr int CM = 128, CN = 64;                // phase C item: rows, columns
+constexpr int TMEM_COLS = 512;
+
+struct Layout {
+    size_t part, wsl, tsl, wex, tex, bytes;
+    int nrc, nca, nrb, nct;
+};
+// per walker-group scratch: partial T' [nrc][nca*AM][kp] fp64, slices of W
+// [nrb][NS][CM*kp] and of T [nct][NS][CN*kp] bf16, exponents of W rows and T
+// columns
+__host__ __device__ inline Layout layout(int N, int kp)
+{
+    Layout L;
+    L.nrc = (N + AR - 1) / AR;
+    L.nca = (N + AM - 1) / AM;
+    L.nrb = (N + CM - 1) / CM;
+    L.nct = (N + CN - 1) / CN;
+    size_t o = 0;
+    L.part = o; o += (size_t)L.nrc * L.nca * AM * kp * sizeof(double);
+    L.wsl = o;  o += (size_t)L.nrb * NS * CM * kp * 2;
+    L.tsl = o;  o += (size_t)L.nct * NS * CN * kp * 2;
+    L.wex = o;  o += (size_t)L.nrb * CM * sizeof(int);
+    L.tex = o;  o += (size_t)L.nct * CN * sizeof(int);
+    L.bytes = (o + 255) / 256 * 256;
+    return L;
+}
+// shared memory: two stages of phase A's slices (A^{-1} block and V block);
+// phase C's W and T tiles reuse it; three mbarriers
+__host__ __device__ inline size_t region_bytes(int kp)
+{
+    return (size_t)2 * NS * (AM + kp) * AK * 2 + 4 * sizeof(unsigned long long);
+}
+__host__ __device__ inline size_t bar_offset(int kp) { return region_bytes(kp) - 4 * sizeof(unsigned long long); }
+
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// 48-bit magnitude q of x relative to the set's largest biased exponent emax
+// (|x| < 2^(emax - 1022)), its sign, as two 32-bit words
+__device__ __forceinline__ void mag48(double x, int emax, uint32_t &qhi, uint32_t &qlo, uint32_t &neg)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const int r = emax - E + 5;
+    unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    m = (E == 0 || r >= 64) ? 0ull : (m >> r);
+    qhi = (uint32_t)(m >> 32);
+    qlo = (uint32_t)m;
+    neg = (uint32_t)(b >> 63);
+}
+// byte j (0 = most significant) of the 48-bit magnitude
+__device__ __forceinline__ uint32_t slice_byte(uint32_t qhi, uint32_t qlo, int j)
+{
+    return j == 0 ? (qhi >> 8) : j == 1 ? (qhi & 0xFFu) : ((qlo >> (8 * (5 - j))) & 0xFFu);
+}
+// an integer 0..255 as fp32 bits (exact), whose upper half is its bf16
+__device__ __forceinline__ uint32_t int_f32bits(uint32_t s)
+{
+    return __float_as_uint(__uint_as_float(0x4B000000u | s) - 8388608.0f);
+}
+// eight values with one exponent: plane j of the slices as eight packed bf16
+__device__ __forceinline__ void slice8(const double (&x)[8], int emax, uint4 (&out)[NS])
+{
+    uint32_t qh[8], ql[8], ng[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) mag48(x[e], emax, qh[e], ql[e], ng[e]);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t f0 = int_f32bits(slice_byte(qh[2 * q], ql[2 * q], j));
+            const uint32_t f1 = int_f32bits(slice_byte(qh[2 * q + 1], ql[2 * q + 1], j));
+            w[q] = __byte_perm(f0, f1, 0x7632) | (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
+        }
+        out[j] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+// 2^e as fp64 (0 below the normal range, +inf above it)
+__device__ __forceinline__ double pow2(int e)
+{
+    return e < -1022 ? 0.0 : e > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
+                                      : __longlong_as_double((long long)(e + 1023) << 52);
+}
+// tensor-memory accumulator of phase A for slice pair (j, l)
+__device__ __forceinline__ int acc_a(int j, int l)
+{
+    const int d = j + l;
+    return d <= 3 ? d * (d + 1) / 2 + j : 6 + d;
+}
+// instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M x N
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+}  // namespace ozf
+
+// The emulated-fp64 flush of walker w (all Gf CTAs of the group call it; it
+// takes two group barriers of its own). Returns false after a wait ran out of
+// budget (ST_TIMEOUT recorded).
+template <typename T>
+__device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int rank,
+                         unsigned char *smem, uint32_t tmem, unsigned *tph, unsigned *flush_ctr,
+                         unsigned &n_flush)
+{
+    using namespace tcf;
+    using namespace ozf;
+    const int N = p.N, ld = p.ld, K = p.K, kp = p.kp, Gf = p.Gf;
+    const Layout Ly = layout(N, kp);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    double *part = (double *)(scr + Ly.part);
+    __nv_bfloat16 *wsl = (__nv_bfloat16 *)(scr + Ly.wsl);
+    __nv_bfloat16 *tsl = (__nv_bfloat16 *)(scr + Ly.tsl);
+    int *wex = (int *)(scr + Ly.wex);
+    int *tex = (int *)(scr + Ly.tex);
+    unsigned char *reg = smem + p.off_xs;
+    unsigned long long *bars = (unsigned long long *)(reg + bar_offset(kp));
+    __shared__ int ecol[AM], erow[32], ok_s;
+    const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
+    double *Ab = (double *)p.Ainv + (size_t)w * wN;
+    const double *Vb = (const double *)p.V + (size_t)w * wK;
+    const double *Wb = (const double *)p.W + (size_t)w * wK;
+    const int *idxw = p.idx + (size_t)w * K;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Nc = Ly.nca * AM;     // row stride of the partial T' buffers
+
+    auto wait_bar = [&](int b) -> bool {
+        if (tid == 0) ok_s = mbar_wait(&bars[b], tph[b], p.status, p.budget_ns) ? 1 : 0;
+        __syncthreads();
+        tph[b] ^= 1u;
+        return ok_s != 0;
+    };
+
+    // ------------------------------------------------------------ phase A
+    {
+        const int nA = Ly.nca * Ly.nrc;
+        const uint32_t idA = idesc_bf16(AM, kp);
+        const size_t aplane = (size_t)AM * AK, bplane = (size_t)kp * AK;   // bf16 elements
+        __nv_bfloat16 *sa = (__nv_bfloat16 *)reg;                          // [2][NS][AM*AK]
+        __nv_bfloat16 *sb = sa + 2 * NS * aplane;                          // [2][NS][kp*AK]
+        const int kk = (tid & 3) * 8;
+        const int ca = tid >> 2;               // columns ca and ca + 64 of the item
+        const int mb = tid >> 2;               // V row of this thread (if < kp)
+        for (int it = rank; it < nA; it += Gf) {
+            const int ct = it % Ly.nca, rc = it / Ly.nca;
+            const int c0 = ct * AM, r0 = rc * AR;
+            // exponents of the item: columns of A^{-1}, rows of V, over rows [r0, r0 + AR)
+            int emc[2] = {0, 0}, emv = 0;
+            for (int kb = 0; kb < AR / AK; ++kb) {
+                const int i = r0 + kb * AK + kk;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + ca + 64 * h;
+                    if (c < N && i < ld) {
+                        const double2 *src = reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const double2 u = __ldcg(src + q);
+                            emc[h] = max(emc[h], max(bexp(u.x), bexp(u.y)));
+                        }
+                    }
+                }
+                if (mb < k && i < ld) {
+                    const double2 *src = reinterpret_cast<const double2 *>(Vb + (size_t)mb * ld + i);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const double2 u = __ldcg(src + q);
+                        emv = max(emv, max(bexp(u.x), bexp(u.y)));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                emc[0] = max(emc[0], __shfl_xor_sync(0xffffffffu, emc[0], o));
+                emc[1] = max(emc[1], __shfl_xor_sync(0xffffffffu, emc[1], o));
+                emv = max(emv, __shfl_xor_sync(0xffffffffu, emv, o));
+            }
+            if ((tid & 3) == 0) {
+                ecol[ca] = emc[0];
+                ecol[ca + 64] = emc[1];
+                if (mb < 32) erow[mb] = emv;
+            }
+            // K-blocks: slice block kb into stage kb & 1 while the MMAs of block kb - 1 run
+            int pend[2] = {0, 0};
+            for (int kb = 0; kb < AR / AK; ++kb) {
+                const int s = kb & 1;
+                if (pend[s]) {
+                    if (!wait_bar(s)) return false;
+                    pend[s] = 0;
+                }
+                const int i = r0 + kb * AK + kk;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + ca + 64 * h;
+                    double x[8];
+                    if (c < N && i < ld) {
+                        const double2 *src = reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const double2 u = __ldcg(src + q);
+                            x[2 * q] = u.x;
+                            x[2 * q + 1] = u.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) x[q] = 0.0;
+                    }
+                    uint4 sl[NS];
+                    slice8(x, emc[h], sl);
+                    const uint32_t o = coff(ca + 64 * h, kk, AK) >> 1;
+#pragma unroll
+                    for (int j = 0; j < NS; ++j)
+                        *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = sl[j];
+                }
+                if (mb < kp) {
+                    double x[8];
+                    if (mb < k && i < ld) {
+                        const double2 *src = reinterpret_cast<const double2 *>(Vb + (size_t)mb * ld + i);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const double2 u = __ldcg(src + q);
+                            x[2 * q] = u.x;
+                            x[2 * q + 1] = u.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) x[q] = 0.0;
+                    }
+                    uint4 sl[NS];
+                    slice8(x, emv, sl);
+                    const uint32_t o = coff(mb, kk, AK) >> 1;
+#pragma unroll
+                    for (int j = 0; j < NS; ++j)
+                        *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = sl[j];
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    for (int ks = 0; ks < AK / 16; ++ks) {
+                        const uint32_t ko = (uint32_t)ks * 256u;
+                        for (int d = 0; d < NS; ++d) {
+                            for (int j = 0; j <= d; ++j) {
+                                const int l = d - j;
+                                const uint64_t ad = sdesc(su32(sa + (s * NS + j) * aplane) + ko, 128, (AK / 8) * 128);
+                                const uint64_t bd = sdesc(su32(sb + (s * NS + l) * bplane) + ko, 128, (AK / 8) * 128);
+                                const bool first = kb == 0 && ks == 0 && (d <= 3 || j == 0);
+                                mma(tmem + (uint32_t)(acc_a(j, l) * kp), ad, bd, idA, first ? 0u : 1u);
+                            }
+                        }
+                    }
+                    commit(&bars[s]);
+                }
+                pend[s] = 1;
+            }
+            for (int s = 0; s < 2; ++s)
+                if (pend[s] && !wait_bar(s)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // readout: lanes = columns c, 16 values of m per warp
+            {
+                const int q = warp & 3, m0 = (warp >> 2) * 16;
+                const int c = q * 32 + lane;
+                if (m0 < kp) {
+                    const uint32_t lanebase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)m0;
+                    long long S[16];
+                    float g4[16], g5[16];
+                    uint32_t v[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) S[e] = 0;
+#pragma unroll
+                    for (int d = 0; d <= 3; ++d) {
+                        int Dd[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) Dd[e] = 0;
+                        for (int j = 0; j <= d; ++j) {
+                            ld16(lanebase + (uint32_t)(acc_a(j, d - j) * kp), v);
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) Dd[e] += __float2int_rz(__uint_as_float(v[e]));
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + Dd[e];
+                    }
+                    ld16(lanebase + (uint32_t)(10 * kp), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g4[e] = __uint_as_float(v[e]);
+                    ld16(lanebase + (uint32_t)(11 * kp), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g5[e] = __uint_as_float(v[e]);
+                    const int cg = c0 + c;
+                    if (cg < N) {
+                        const int ec = ecol[c];
+                        double *dst = part + ((size_t)rc * Nc + cg) * kp + m0;
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2) {
+                            double y[2];
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                const float g = g4[e + u] + g5[e + u] * (1.0f / 256.0f);
+                                const double sv = fma((double)g, 1.0 / 256.0, (double)S[e + u]);
+                                y[u] = sv * pow2(ec + erow[m0 + e + u] - 2084);
+                            }
+                            *reinterpret_cast<double2 *>(dst + e) = make_double2(y[0], y[1]);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+
+    // ------------------------------------------------------------ phase B
+    {
+        // T = sum_rc T'_rc - E', eight consecutive m per thread, the kp / 8
+        // threads of a column adjacent in the warp
+        const int ng = kp / 8;
+        const int totT = N * ng;
+        for (int base = rank * STHREADS; base < totT; base += Gf * STHREADS) {
+            const int e = base + tid;
+            const bool in = e < totT;
+            const int c = in ? e / ng : 0, m0 = (e - (e / ng) * ng) * 8;
+            double t[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t[q] = 0.0;
+            if (in) {
+                for (int rc = 0; rc < Ly.nrc; ++rc) {
+                    const double2 *src = reinterpret_cast<const double2 *>(part + ((size_t)rc * Nc + c) * kp + m0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const double2 u = __ldcg(src + q);
+                        t[2 * q] += u.x;
+                        t[2 * q + 1] += u.y;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int m = m0 + q;
+                    if (m < k) t[q] -= (__ldcg(idxw + m) == c) ? 1.0 : 0.0;
+                    else t[q] = 0.0;
+                }
+            }
+            int em = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) em = max(em, bexp(t[q]));
+            for (int o = 1; o < ng; o <<= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+            if (in) {
+                uint4 sl[NS];
+                slice8(t, em, sl);
+                const int ct = c / CN;
+                const uint32_t o = coff(c - ct * CN, m0, kp) >> 1;
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    *reinterpret_cast<uint4 *>(tsl + ((size_t)ct * NS + j) * CN * kp + o) = sl[j];
+                if (m0 == 0) tex[c] = em;
+            }
+        }
+        // W: one thread per row i, all kp values of m
+        for (int i = rank * STHREADS + tid; i < N; i += Gf * STHREADS) {
+            double x[32];
+            int em = 0;
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                x[m] = (m < k) ? __ldcg(Wb + (size_t)m * ld + i) : 0.0;
+                em = max(em, bexp(x[m]));
+            }
+            const int rb = i / CM;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g * 8 < kp) {
+                    double y[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) y[q] = x[g * 8 + q];
+                    uint4 sl[NS];
+                    slice8(y, em, sl);
+                    const uint32_t o = coff(i - rb * CM, g * 8, kp) >> 1;
+#pragma unroll
+                    for (int j = 0; j < NS; ++j)
+                        *reinterpret_cast<uint4 *>(wsl + ((size_t)rb * NS + j) * CM * kp + o) = sl[j];
+                }
+            }
+            wex[i] = em;
+        }
+    }
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+
+    // ------------------------------------------------------------ phase C
+    {
+        const int nC = Ly.nrb * Ly.nct;
+        const uint32_t idC = idesc_bf16(CM, CN);
+        const uint32_t sbo = (uint32_t)(kp / 8) * 128u;
+        __nv_bfloat16 *swt = (__nv_bfloat16 *)reg;                 // [NS][CM*kp]
+        __nv_bfloat16 *stt = swt + NS * CM * kp;                   // [NS][CN*kp]
+        int *tex_s = ecol;                                         // CN column exponents
+        for (int it = rank; it < nC; it += Gf) {
+            const int rb = it % Ly.nrb, ct = it / Ly.nrb;
+            const int i0 = rb * CM, c0 = ct * CN;
+            {
+                const uint4 *srcw = reinterpret_cast<const uint4 *>(wsl + (size_t)rb * NS * CM * kp);
+                const uint4 *srct = reinterpret_cast<const uint4 *>(tsl + (size_t)ct * NS * CN * kp);
+                uint4 *dw = reinterpret_cast<uint4 *>(swt);
+                uint4 *dt = reinterpret_cast<uint4 *>(stt);
+                const int nw4 = NS * CM * kp / 8, nt4 = NS * CN * kp / 8;
+                for (int q = tid; q < nw4; q += STHREADS) dw[q] = __ldcg(srcw + q);
+                for (int q = tid; q < nt4; q += STHREADS) dt[q] = __ldcg(srct + q);
+                if (tid < CN) tex_s[tid] = c0 + tid < N ? __ldcg(tex + c0 + tid) : 0;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int ks = 0; ks < kp / 16; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    for (int d = 0; d < NS; ++d) {
+                        for (int j = 0; j <= d; ++j) {
+                            const int l = d - j;
+                            const uint64_t ad = sdesc(su32(swt + (size_t)j * CM * kp) + ko, 128, sbo);
+                            const uint64_t bd = sdesc(su32(stt + (size_t)l * CN * kp) + ko, 128, sbo);
+                            mma(tmem + (uint32_t)(d * CN), ad, bd, idC, (ks == 0 && j == 0) ? 0u : 1u);
+                        }
+                    }
+                }
+                commit(&bars[2]);
+            }
+            if (!wait_bar(2)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // lanes = rows i; warps 0-3 take columns 0..31, warps 4-7 columns 32..63
+            {
+                const int q = warp & 3;
+                const int i = i0 + q * 32 + lane;
+                const int ei = i < N ? __ldcg(wex + i) : 0;
+                const int cb = (warp >> 2) * 32;
+                for (int j0 = cb; j0 < cb + 32; j0 += 16) {
+                    long long S[16];
+                    uint32_t v[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) S[e] = 0;
+#pragma unroll
+                    for (int d = 0; d < NS; ++d) {
+                        ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * CN + j0), v);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + __float2int_rz(__uint_as_float(v[e]));
+                    }
+                    if (i < N) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int c = c0 + j0 + e;
+                            if (c < N) {
+                                double *x = Ab + (size_t)c * ld + i;
+                                *x = fma(-(double)S[e], pow2(ei + tex_s[j0 + e] - 2100), __ldcg(x));
+                            }
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
+template <typename T, bool RES, int FM>
 __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_t tmem)
 {
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
@@ -785,7 +1286,13 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 ++n_event;
                 if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
                 const int k = __ldcg(p.kglob + w);
-                if (TC) {
+                if (FM == FM_OZ) {
+                    if (k >= SMALL_K) {
+                        if (!flush_oz(p, w, k, grp, rank, smem, tmem, tph, flush_ctr, n_flush)) return;
+                    } else if (k > 0) {
+                        flush_columns_small(p, w, k, fc0, fc1);
+                    }
+                } else if (FM == FM_TC) {
                     if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
                 } else if (k > 0 && k < SMALL_K) {
                     flush_columns_small(p, w, k, fc0, fc1);
@@ -1063,7 +1570,13 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             ++n_event;
             if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return;
             tick(5);
-            if (TC) {
+            if (FM == FM_OZ) {
+                if (k >= SMALL_K) {
+                    if (!flush_oz(p, w, k, grp, rank, smem, tmem, tph, flush_ctr, n_flush)) return;
+                } else if (k > 0) {
+                    flush_columns_small(p, w, k, fc0, fc1);
+                }
+            } else if (FM == FM_TC) {
                 if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
             } else if (k > 0 && k < SMALL_K) {
                 flush_columns_small(p, w, k, fc0, fc1);
@@ -1087,21 +1600,25 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 // The kernel: tensor memory for the tensor-core flush (256 columns: two of
 // these CTAs at most share an SM, 2 x 256 = 512 columns), the mbarriers, the
 // sweep, and the release of the tensor memory on every exit path.
-template <typename T, bool RES, bool TC>
-__global__ void __launch_bounds__(STHREADS, TC ? 1 : 2) sweep_kernel(SweepParams<T> p)
+template <typename T, bool RES, int FM>
+__global__ void __launch_bounds__(STHREADS, FM == FM_SIMT ? 2 : 1) sweep_kernel(SweepParams<T> p)
 {
+    constexpr bool TC = FM != FM_SIMT;
+    // tensor-memory columns: the split-bf16 flush's two accumulators fit in 256
+    // (two such CTAs could share an SM); the emulated-fp64 flush takes the whole
+    // 512, and its shared memory keeps a second CTA off the SM
+    constexpr int TCOLS = FM == FM_OZ ? ozf::TMEM_COLS : 256;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t tmem_s;
     if (TC && threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
-                     ::"r"(tcf::su32(&tmem_s)) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tcf::su32(&tmem_s)), "n"(TCOLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
         mbar_init((unsigned long long *)(smem + p.off_bar));
         if (TC) {
-            unsigned long long *bars = (unsigned long long *)(smem + p.off_xs + tcf::region_bytes(p.kp) -
-                                                              4 * sizeof(unsigned long long));
+            unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
             for (int q = 0; q < 4; ++q)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1110,11 +1627,11 @@ __global__ void __launch_bounds__(STHREADS, TC ? 1 : 2) sweep_kernel(SweepParams
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    sweep_body<T, RES, TC>(p, smem, TC ? tmem_s : 0u);
+    sweep_body<T, RES, FM>(p, smem, TC ? tmem_s : 0u);
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (TC && threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_s) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_s), "n"(TCOLS) : "memory");
 }
 
 // Gaussians (Box-Muller pairs) and Metropolis uniforms of one sweep for every
@@ -1184,9 +1701,10 @@ __global__ void sweep_logdet_kernel(int N, const int *wlist, const unsigned char
 
 // ---------------------------------------------------------------- launcher
 static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+static const size_t OZ_MIN_SMEM = 118 * 1024;
 
 template <typename T>
-static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, bool block, int *offs)
+static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int fm, bool block, int *offs)
 {
     size_t o = 0;
     offs[8] = (int)o; o = align16(o + 16);                                   // mbarrier
@@ -1198,51 +1716,61 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, bool tc, bo
     offs[5] = (int)o;                                                        // xs / tc region
     size_t xs_bytes = (size_t)cb * ld * sizeof(T);
     if (block) xs_bytes = std::max(xs_bytes, (size_t)std::max(2 * BT * BT, 2 * BI1 * SLD) * sizeof(T));
-    o = align16(o + (tc ? tcf::region_bytes((K + 15) / 16 * 16) : xs_bytes));
+    const int kp = (K + 15) / 16 * 16;
+    const size_t region = fm == FM_TC ? tcf::region_bytes(kp) : fm == FM_OZ ? ozf::region_bytes(kp) : xs_bytes;
+    offs[9] = (int)(o + (fm == FM_TC ? tcf::region_bytes(kp) - 4 * sizeof(unsigned long long)
+                                     : fm == FM_OZ ? ozf::bar_offset(kp) : 0));
+    o = align16(o + region);
     offs[6] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Wsm
     offs[7] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Vsm
+    // the emulated-fp64 flush allocates all 512 tensor-memory columns: more than
+    // half of the SM's shared memory keeps a second CTA off the SM
+    if (fm == FM_OZ) o = std::max(o, (size_t)OZ_MIN_SMEM);
     return o;
 }
 
 static const size_t SMEM_BUDGET = 200 * 1024;
 static const size_t RES_BUDGET = 128 * 1024;
 
-template <typename T, bool RES, bool TC>
+template <typename T, bool RES, int FM>
 static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, int chunk)
 {
     const int K = c.K;
-    int offs[9];
+    int offs[10];
     int cb = MAX_CB;
     // the wide-block flush (fp64, K <= 64) when its tiles fit beside everything
     // else: fp64 arithmetic hides its staging; in fp32 (one CTA of 8 warps per SM)
     // the staging latency does not hide and the column tiles are as fast
-    bool block = !TC && K <= BT && std::is_same<T, double>::value;
-    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+    bool block = FM == FM_SIMT && K <= BT && std::is_same<T, double>::value;
+    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
     while (cb > 1 && smem > SMEM_BUDGET) {
         cb >>= 1;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
     }
     if (smem > SMEM_BUDGET && block) {
         block = false;
         cb = MAX_CB;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
         while (cb > 1 && smem > SMEM_BUDGET) {
             cb >>= 1;
-            smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, TC, block, offs);
+            smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
         }
     }
     if (smem > SMEM_BUDGET) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, TC>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, FM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, TC>, STHREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, FM>, STHREADS, smem);
     if (e != cudaSuccess) return e;
+    if (FM == FM_OZ && per_sm > 1) return cudaErrorInvalidConfiguration;   // the TMEM allocation would wait
     int capacity = per_sm * c.num_sms;
     if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
     if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
     const int nw = L.wlist ? L.nlist : c.batch;
-    const int ngroups = std::min(nw, std::max(1, capacity / Gf));
+    int ngroups = std::min(nw, std::max(1, capacity / Gf));
+    if (FM == FM_OZ) ngroups = std::min(ngroups, c.oz_groups);
+    if (ngroups < 1) return cudaErrorInvalidConfiguration;
     if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
     if ((size_t)ngroups * 2 * Gr * (2 * K + 1) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
 
@@ -1264,17 +1792,36 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.phase_ns = c.prof ? c.sw_phase : nullptr;
     p.wlist = L.wlist;
     p.nw = nw;
+    p.oz = FM == FM_OZ ? c.oz : nullptr;
+    p.oz_stride = c.oz_stride;
+    p.off_tcbar = offs[9];
     e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {&p};
-    e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES, TC>, dim3(ngroups * Gf),
+    e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES, FM>, dim3(ngroups * Gf),
                                     dim3(STHREADS), args, smem, c.stream);
     c.last_sweep_shape[0] = Gf;
     c.last_sweep_shape[1] = Gr;
     c.last_sweep_shape[2] = ngroups;
     c.last_sweep_shape[3] = chunk;
-    c.last_sweep_shape[4] = TC ? 1000 : (RES ? cb : -cb);
+    c.last_sweep_shape[4] = FM == FM_TC ? 1000 : FM == FM_OZ ? 2000 : (RES ? cb : -cb);
     return e;
+}
+
+size_t oz_group_bytes(int N, int K)
+{
+    if (K > 32) return 0;
+    return ozf::layout(N, (K + 15) / 16 * 16).bytes;
+}
+
+// The emulated-fp64 flush (flush_oz) for this handle and group size: fp64,
+// SMALL_K <= K <= 32, a walker group of several CTAs, scratch allocated, not
+// switched off. (Queues shorter than SMALL_K still flush with
+// flush_columns_small.)
+static bool use_oz(const Ctx &c, int Gf)
+{
+    return c.prec == QMCDU_FP64 && c.K <= 32 && c.K >= SMALL_K && Gf >= 2 && c.oz && c.oz_groups > 0 &&
+           c.opt_fp64_flush != 1;
 }
 
 template <typename T>
@@ -1308,9 +1855,14 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
     const int cpc = (N + Gf - 1) / Gf;
     const bool tc = std::is_same<T, float>::value && c.prec == QMCDU_FP32_BF16X3 && !res &&
                     K <= 64 && cpc >= 128;
-    if (tc) return launch_shape<T, false, true>(c, L, Gf, Gr, chunk);
-    return res ? launch_shape<T, true, false>(c, L, Gf, Gr, chunk)
-               : launch_shape<T, false, false>(c, L, Gf, Gr, chunk);
+    if (tc) return launch_shape<T, false, FM_TC>(c, L, Gf, Gr, chunk);
+    if constexpr (std::is_same<T, double>::value) {
+        // emulated-fp64 flush: fp64 walkers shared by several CTAs, K <= 32
+        if (use_oz(c, Gf)) return res ? launch_shape<T, true, FM_OZ>(c, L, Gf, Gr, chunk)
+                                      : launch_shape<T, false, FM_OZ>(c, L, Gf, Gr, chunk);
+    }
+    return res ? launch_shape<T, true, FM_SIMT>(c, L, Gf, Gr, chunk)
+               : launch_shape<T, false, FM_SIMT>(c, L, Gf, Gr, chunk);
 }
 
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)

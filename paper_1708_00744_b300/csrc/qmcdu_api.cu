@@ -118,6 +118,12 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
         AL(c->d_wseed, B * sizeof(unsigned long long));
         AL(c->d_wsweep, B * sizeof(int));
         AL(c->d_lseed, B * sizeof(unsigned long long));
+        // emulated-fp64 flush: one scratch block per walker group of >= 2 CTAs
+        if (c->prec == QMCDU_FP64 && oz_group_bytes(N, K) > 0) {
+            c->oz_stride = oz_group_bytes(N, K);
+            c->oz_groups = (int)std::min<size_t>(B, (size_t)std::max(1, c->num_sms / 2));
+            AL(c->oz, (size_t)c->oz_groups * c->oz_stride);
+        }
     }
 #undef AL
     return e;
@@ -134,7 +140,7 @@ static void release(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
-                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr};
+                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz};
     for (void *p : more)
         if (p) cudaFree(p);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -909,6 +915,10 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value)
     case QMCDU_OPT_TEST_STALL: c->opt_stall = value ? 1 : 0; break;
     case QMCDU_OPT_MAX_CTAS: c->opt_max_ctas = (int)std::min(value, 1LL << 20); break;
     case QMCDU_OPT_GROUP_CTAS: c->opt_group_ctas = (int)std::min(value, 1LL << 20); break;
+    case QMCDU_OPT_FP64_FLUSH:
+        if (value < 0 || value > 2) return QMCDU_ERR_ARG;
+        c->opt_fp64_flush = (int)value;
+        break;
     default: return fail(c, QMCDU_ERR_ARG, "unknown option%s");
     }
     return QMCDU_OK;

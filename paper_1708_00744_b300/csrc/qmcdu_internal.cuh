@@ -97,6 +97,12 @@ struct Ctx {
     int opt_stall = 0;
     int opt_max_ctas = 0;            // cap on the persistent sweep's grid (0: whole GPU)
     int opt_group_ctas = 0;          // fixed CTAs per walker group (0: from the batch)
+    int opt_fp64_flush = 0;          // 0: auto, 1: fp64 arithmetic only, 2: emulated on the tensor cores
+    // emulated-fp64 flush of the persistent sweep (kernels_sweep.cu): scratch of
+    // oz_groups walker groups, oz_stride bytes each
+    unsigned char *oz = nullptr;
+    size_t oz_stride = 0;
+    int oz_groups = 0;
     // walker subsets (qmcdu_sweep_walkers): list, keys and sweep numbers
     int *d_wlist = nullptr;
     unsigned long long *d_wseed = nullptr;
@@ -139,6 +145,8 @@ struct SweepLaunch {
     const int *wsweep;
 };
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L);
+// Scratch bytes of one walker group of the emulated-fp64 flush (0: not used for N, K).
+size_t oz_group_bytes(int N, int K);
 cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
 cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
 
