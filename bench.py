@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 SMS, SM_MHZ = 148, 2032.0
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.203
 OZ_FLUSH_KIND = 2000      # sweep_shape()["col_tile"] of the emulated-fp64 tensor-core flush
-OZ_PRODUCTS = 21          # bf16 slice products per emulated fp64 product (slice pairs j + l <= 5)
+OZ_PRODUCTS = 28          # fp16 slice products per emulated fp64 product (slice pairs j + l <= 6)
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 77.0
 HBM_PEAK_FALLBACK_GBS = 6400.0
 
@@ -647,10 +647,11 @@ def roofline_for(a, res):
            "avg_launch_ms": ms / nlaunch_per_class,
            "share_of_step": ms / res["total_ms"] if res["total_ms"] else None}
     if a.precision == "fp64" and kinds and all(k == OZ_FLUSH_KIND for k in kinds):
-        # the flush's fp64 contraction runs on the tensor cores as 21 bf16 slice
-        # products per fp64 product: its ceiling is the measured bf16 rate / 21
+        # the flush's fp64 contraction runs on the tensor cores as OZ_PRODUCTS
+        # fp16 slice products per fp64 product: its ceiling is the measured
+        # 16-bit tensor rate / OZ_PRODUCTS
         bf16 = measured_peaks().get("bf16_tflops_sustained")
-        src_ = "measured bf16 sustained (MEASURED_PEAKS.json) / %d slice products" % OZ_PRODUCTS
+        src_ = "measured bf16 sustained (MEASURED_PEAKS.json) / %d fp16 slice products (fp16 and bf16 share the tensor rate)" % OZ_PRODUCTS
         if not bf16:
             bf16, src_ = 1400.0, "fallback bf16 sustained 1.4 PFLOP/s / %d slice products" % OZ_PRODUCTS
         peak = bf16 / OZ_PRODUCTS

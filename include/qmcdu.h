@@ -217,7 +217,7 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
  * Profiling. While enabled, the library records CUDA events on the handle's
  * stream around every flush (Eq. 4) and every recompute, and counts its
  * kernel launches. qmcdu_profile_enable(h, 1) resets the counters; 0 stops.
- * qmcdu_profile_read synchronises and writes n <= 18 values to out (host):
+ * qmcdu_profile_read synchronises and writes n <= 21 values to out (host):
  *   [0] kernel launches  [1] flushes   [2] flush time (ms)
  *   [3] recomputes       [4] recompute time (ms)   [5] stream syncs inside
  *   sweeps  [6] ratio launches  [7] accept launches
@@ -226,6 +226,9 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
  *   decision, accept, the flush's first barrier, the flush arithmetic, the
  *   flush's second barrier (host-driven sweeps time [2] instead)
  *   [16] persistent sweep kernel launches  [17] their total time (ms)
+ *   [18..20] the emulated-fp64 flush's phases (walker 0's lead CTA, barrier
+ *   waits included), time (ms): T' = V'A^{-1} over row chunks; the reduction
+ *   and slicing of T and W; the update of A^{-1}
  */
 int qmcdu_profile_enable(qmcdu_t h, int enable);
 int qmcdu_profile_read(qmcdu_t h, double *out, int n);
@@ -249,10 +252,11 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       are bit-identical alone and in a batch (qmcdu_sweep_walkers, serving)
  *   QMCDU_OPT_FP64_FLUSH   [0: auto] the persistent sweep's flush (Eq. 4) for
  *       fp64 walkers: 1 = fp64 arithmetic units only; 2 (and auto) = the
- *       contraction emulated on the tensor cores (operands cut into six 8-bit
- *       slices, exact fp32 accumulation of slice products, exact integer
- *       recombination; about 2^-45 relative to |row| |column|) where it
- *       applies: K <= 32 and walker groups of two or more CTAs
+ *       contraction emulated on the tensor cores (operands cut into seven
+ *       8-bit slices, exact fp32 accumulation of slice products, exact integer
+ *       recombination; near 2^-53 relative to |row| |column|, the error of
+ *       fp64 arithmetic) where it applies: 4 <= K <= 32 and walker groups of
+ *       two or more CTAs
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {

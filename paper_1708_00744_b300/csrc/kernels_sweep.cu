@@ -35,6 +35,7 @@
 // ST_TIMEOUT in the status word and returns. Data written by other CTAs is read
 // with ld.global.cg (L2, not the SM's L1).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -78,7 +79,7 @@ struct SweepParams {
     int off_vs, off_as, off_vd, off_red, off_ts, off_xs, off_wsm, off_vsm, off_bar;
     int kp;                         // tensor-core flush: K rounded up to 16 (<= 64)
     int block_ok;                   // the xs region holds flush_block's tiles
-    unsigned long long *phase_ns;   // optional [8]: time per phase, group 0 rank 0 thread 0
+    unsigned long long *phase_ns;   // optional [11]: time per phase, group 0 rank 0 thread 0
     const int *wlist;               // optional [nw]: the walkers this launch sweeps (else 0..nw)
     int nw;
     unsigned char *oz;              // emulated-fp64 flush: per-group scratch (ozf::layout)
@@ -769,46 +770,55 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
 // ------------------------------------------------------------------------
 // Emulated-fp64 flush on the tensor cores (fp64 walkers).
 //
-// Every fp64 operand x of a contraction is cut into NS = 6 signed 8-bit
+// Every fp64 operand x of a contraction is cut into NS = 7 signed 8-bit
 // integer slices relative to a power of two shared by its row or column
 // (Emax: the largest biased exponent of the set):
-//   q = floor(|x| 2^(1070 - Emax)) < 2^48,  q = sum_j s_j 2^(40 - 8j),
-//   x ~ sign(x) 2^(Emax - 1070) q            (48 bits of every operand).
-// A slice is an integer of magnitude <= 255, exact in bf16, and the product of
+//   q = round(|x| 2^(1078 - Emax)) < 2^56,  q = sum_j s_j 2^(48 - 8j),
+//   x ~ sign(x) 2^(Emax - 1078) q            (56 bits of every operand).
+// A slice is an integer of magnitude <= 255, exact in fp16, and the product of
 // two slices is an integer <= 65025; a tcgen05 MMA with fp32 accumulation sums
 // such products without rounding while every partial sum stays below 2^24.
-// The slice pairs (j, l) with j + l <= 5 (21 products) are accumulated per
-// diagonal d = j + l in tensor memory and recombined exactly in 64-bit
-// integers, which brings the dropped and truncated terms to about 2^-45 of
-// |row| |column| (the order of an fp64 dot product's own rounding bound).
+// The slice pairs (j, l) with j + l <= 6 (28 products, issued as 9 or 10 MMAs
+// per K-step with the slices of one operand stacked along N) are accumulated
+// per diagonal d = j + l in tensor memory and recombined exactly in 64-bit
+// integers. The dropped (j + l >= 7) and rounded terms stay near 2^-53 of
+// |row| |column|: one flush matches fp64 arithmetic's own error (about 1e-15
+// relative for a 200 x 200 walker, against 3e-13 with six slices).
 //
 // The flush of Eq. 4 runs in three phases over all CTAs of the walker group,
 // with a group barrier after each:
 //   A  T'[c][m] = sum_i A^{-1}[i][c] V[m][i]: items of 128 columns x 256 rows
-//      (the contraction split over row chunks); the chunk's column and row
-//      exponents; one product per tensor-memory accumulator for d <= 3 (exact:
-//      256 x 65025 < 2^24), one accumulator each for d = 4 and d = 5 (their
-//      fp32 rounding lies below 2^-53 of the result); partial sums in fp64.
-//   B  T = sum of the partials - E' (fixed order), sliced with one exponent
-//      per column c; W = P Kinv sliced with one exponent per row i; the
-//      slices are written in the tensor cores' K-major tile layout.
+//      (the contraction split over row chunks), raw K-blocks of 16 rows
+//      brought in by asynchronous copies two blocks ahead and sliced with the
+//      column exponents of A^{-1} and the row exponents of V (kept up to date
+//      by phase C and by the accepts); one pair per tensor-memory block for
+//      d <= 3 (exact: 256 x 65025 < 2^24), d = 4..6 spread over two blocks
+//      each (their fp32 rounding lies below 2^-53 of the result); partials as
+//      an exact int64 and an fp32 tail.
+//   B  T = sum of the partials (integers, fixed order) - E', sliced with one
+//      exponent per column c; W = P Kinv sliced with one exponent per row i;
+//      the slices are written in the tensor cores' K-major tile layout.
 //   C  A^{-1}[i][c] -= sum_m W[m][i] T[m][c]: items of 128 rows x 64 columns,
-//      contraction K <= 32 so that all six diagonals accumulate exactly
-//      (6 x 32 x 65025 < 2^24); S = sum_d D_d 2^(8(5-d)) in int64, then one
-//      fused multiply-add into A^{-1}.
+//      contraction K <= 32 so that all seven diagonals accumulate exactly
+//      (7 x 32 x 65025 < 2^24); S = sum_d D_d 2^(8(5-d)) in int64 with the
+//      seventh diagonal folded in, turned into fp64 by integer operations, and
+//      one fp64 subtraction per element of A^{-1}. The tiles arrive by bulk
+//      copies, the next item's T tile while the current one computes.
 namespace ozf {
-constexpr int NS = 6;
-constexpr int AM = 128, AR = 256, AK = 32;      // phase A item: columns, rows; rows per K-block
+constexpr int NS = 7;
+constexpr int AM = 128, AR = 256, AK = 16;      // phase A item: columns, rows; rows per K-block
+constexpr int NSLOT = 3;                        // phase A: raw fp64 K-blocks in flight
 constexpr int CM = 128, CN = 64;                // phase C item: rows, columns
 constexpr int TMEM_COLS = 512;
 
 struct Layout {
-    size_t part, wsl, tsl, wex, tex, bytes;
+    size_t part, partg, wsl, tsl, wex, tex, cex, vex, bytes;
     int nrc, nca, nrb, nct;
 };
-// per walker-group scratch: partial T' [nrc][nca*AM][kp] fp64, slices of W
-// [nrb][NS][CM*kp] and of T [nct][NS][CN*kp] bf16, exponents of W rows and T
-// columns
+// per walker-group scratch: partial T' [nrc][nca*AM][kp] as exact int64 sums
+// of the d <= 3 diagonals and fp32 sums of d = 4, 5; slices of W
+// [nrb][NS][CM*kp] and of T [nct][NS][CN*kp] fp16; exponents of W rows, T
+// columns, A^{-1} columns (cex) and V rows (vex)
 __host__ __device__ inline Layout layout(int N, int kp)
 {
     Layout L;
@@ -817,64 +827,103 @@ __host__ __device__ inline Layout layout(int N, int kp)
     L.nrb = (N + CM - 1) / CM;
     L.nct = (N + CN - 1) / CN;
     size_t o = 0;
-    L.part = o; o += (size_t)L.nrc * L.nca * AM * kp * sizeof(double);
+    L.part = o;  o += (size_t)L.nrc * L.nca * AM * kp * sizeof(long long);
+    L.partg = o; o += (size_t)L.nrc * L.nca * AM * kp * sizeof(float);
     L.wsl = o;  o += (size_t)L.nrb * NS * CM * kp * 2;
     L.tsl = o;  o += (size_t)L.nct * NS * CN * kp * 2;
     L.wex = o;  o += (size_t)L.nrb * CM * sizeof(int);
     L.tex = o;  o += (size_t)L.nct * CN * sizeof(int);
+    L.cex = o;  o += (size_t)L.nca * AM * sizeof(int);
+    L.vex = o;  o += 64 * sizeof(int);
     L.bytes = (o + 255) / 256 * 256;
     return L;
 }
-// shared memory: two stages of phase A's slices (A^{-1} block and V block);
-// phase C's W and T tiles reuse it; three mbarriers
-__host__ __device__ inline size_t region_bytes(int kp)
+// shared memory: phase A's NSLOT raw fp64 K-blocks (A^{-1} columns, then V
+// rows) and two stages of their slices; phase C reuses it for one W tile, two
+// T tiles and two blocks of column exponents; then eight mbarriers (0, 1:
+// phase A stages; 2: phase C MMAs; 3: W tile; 4, 5: T tiles)
+constexpr int NBAR = 8;
+__host__ __device__ inline size_t raw_bytes(int kp) { return (size_t)(AM + kp) * AK * sizeof(double); }
+__host__ __device__ inline size_t phase_a_bytes(int kp)
 {
-    return (size_t)2 * NS * (AM + kp) * AK * 2 + 4 * sizeof(unsigned long long);
+    return NSLOT * raw_bytes(kp) + (size_t)2 * NS * (AM + kp) * AK * 2;
 }
-__host__ __device__ inline size_t bar_offset(int kp) { return region_bytes(kp) - 4 * sizeof(unsigned long long); }
+__host__ __device__ inline size_t phase_c_bytes(int kp)
+{
+    return (size_t)NS * (CM + 2 * CN) * kp * 2 + 2 * CN * sizeof(int);
+}
+__host__ __device__ inline size_t bar_offset(int kp)
+{
+    const size_t a = phase_a_bytes(kp), c = phase_c_bytes(kp);
+    return ((a > c ? a : c) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t region_bytes(int kp) { return bar_offset(kp) + NBAR * sizeof(unsigned long long); }
 
 __device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
-// 48-bit magnitude q of x relative to the set's largest biased exponent emax
-// (|x| < 2^(emax - 1022)), its sign, as two 32-bit words
-__device__ __forceinline__ void mag48(double x, int emax, uint32_t &qhi, uint32_t &qlo, uint32_t &neg)
+// 56-bit magnitude q = round(|x| 2^(1078 - emax)) of x relative to the set's
+// largest biased exponent emax (|x| < 2^(emax - 1022)), clamped to 2^56 - 1,
+// and its sign, as two 32-bit words (bits 32..55 and 0..31). Rounding to
+// nearest keeps the slicing error unbiased.
+__device__ __forceinline__ void mag56(double x, int emax, uint32_t &qhi, uint32_t &qlo, uint32_t &neg)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
-    const int r = emax - E + 5;
-    unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    m = (E == 0 || r >= 64) ? 0ull : (m >> r);
-    qhi = (uint32_t)(m >> 32);
-    qlo = (uint32_t)m;
+    const int s = E - emax + 3;                 // q = m 2^s, s <= 3
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int r = -s;
+    unsigned long long q = s >= 0 ? (m << (s & 63))
+                                  : (r > 54 ? 0ull : ((m + (1ull << ((r - 1) & 63))) >> (r & 63)));
+    q = E == 0 ? 0ull : (q > 0xFFFFFFFFFFFFFFull ? 0xFFFFFFFFFFFFFFull : q);
+    qhi = (uint32_t)(q >> 32);
+    qlo = (uint32_t)q;
     neg = (uint32_t)(b >> 63);
 }
-// byte j (0 = most significant) of the 48-bit magnitude
-__device__ __forceinline__ uint32_t slice_byte(uint32_t qhi, uint32_t qlo, int j)
+// slice j (0 = most significant byte) of two magnitudes as a packed pair of
+// fp16: the bytes are placed under the exponent of 1024 (1024 + b is exact in
+// fp16 for b < 1024) and 1024 is subtracted from both halves at once
+__device__ __forceinline__ uint32_t slice_pair(uint32_t qh0, uint32_t ql0, uint32_t qh1, uint32_t ql1,
+                                               int j, uint32_t sgn)
 {
-    return j == 0 ? (qhi >> 8) : j == 1 ? (qhi & 0xFFu) : ((qlo >> (8 * (5 - j))) & 0xFFu);
+    const bool hi = j < 3;
+    const uint32_t a = hi ? qh0 : ql0, b = hi ? qh1 : ql1;
+    const uint32_t idx = hi ? (uint32_t)(2 - j) : (uint32_t)(6 - j);      // byte index in the word
+    const uint32_t w = (__byte_perm(a, b, idx | ((4u + idx) << 8)) & 0x00FF00FFu) | 0x64006400u;
+    __half2 h = *reinterpret_cast<const __half2 *>(&w);
+    h = __hsub2(h, __half2half2(__ushort_as_half((unsigned short)0x6400u)));
+    return *reinterpret_cast<const uint32_t *>(&h) ^ sgn;
 }
-// an integer 0..255 as fp32 bits (exact), whose upper half is its bf16
-__device__ __forceinline__ uint32_t int_f32bits(uint32_t s)
-{
-    return __float_as_uint(__uint_as_float(0x4B000000u | s) - 8388608.0f);
-}
-// eight values with one exponent: plane j of the slices as eight packed bf16
+// eight values with one exponent: plane j of the slices as eight packed fp16
 __device__ __forceinline__ void slice8(const double (&x)[8], int emax, uint4 (&out)[NS])
 {
     uint32_t qh[8], ql[8], ng[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) mag48(x[e], emax, qh[e], ql[e], ng[e]);
+    for (int e = 0; e < 8; ++e) mag56(x[e], emax, qh[e], ql[e], ng[e]);
+    uint32_t sg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sg[q] = (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
         uint32_t w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t f0 = int_f32bits(slice_byte(qh[2 * q], ql[2 * q], j));
-            const uint32_t f1 = int_f32bits(slice_byte(qh[2 * q + 1], ql[2 * q + 1], j));
-            w[q] = __byte_perm(f0, f1, 0x7632) | (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
-        }
+        for (int q = 0; q < 4; ++q) w[q] = slice_pair(qh[2 * q], ql[2 * q], qh[2 * q + 1], ql[2 * q + 1], j, sg[q]);
         out[j] = make_uint4(w[0], w[1], w[2], w[3]);
     }
+}
+// S 2^e as fp64 (S rounded to 53 significant bits, halves away from zero),
+// built with integer operations: 0 for S = 0 or below the normal range, +-inf
+// above it (a carry out of the rounding moves into the exponent field)
+__device__ __forceinline__ double scaled_i64(long long S, int e)
+{
+    const unsigned long long neg = (unsigned long long)S & 0x8000000000000000ull;
+    const unsigned long long M = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+    const int lz = __clzll((long long)M);
+    const int be = 63 - lz + e + 1023;                  // biased exponent of the leading bit
+    const unsigned long long Mn = M << (lz & 63);
+    const unsigned long long frac = (Mn >> 11) + ((Mn >> 10) & 1ull);   // rounded to 53 bits
+    unsigned long long bits = neg | (((unsigned long long)(be - 1) << 52) + frac);
+    bits = (M == 0 || be <= 0) ? neg : (be >= 2047 ? (neg | 0x7FF0000000000000ull) : bits);
+    return __longlong_as_double((long long)bits);
 }
 // 2^e as fp64 (0 below the normal range, +inf above it)
 __device__ __forceinline__ double pow2(int e)
@@ -882,48 +931,89 @@ __device__ __forceinline__ double pow2(int e)
     return e < -1022 ? 0.0 : e > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
                                       : __longlong_as_double((long long)(e + 1023) << 52);
 }
-// tensor-memory accumulator of phase A for slice pair (j, l)
-__device__ __forceinline__ int acc_a(int j, int l)
+// instruction descriptor: fp16 x fp16 -> fp32, K-major A and B, M x N
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N)
 {
-    const int d = j + l;
-    return d <= 3 ? d * (d + 1) / 2 + j : 6 + d;
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-// instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M x N
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+// Phase A's MMAs per K-step. The V slices are stacked along N in shared
+// memory, so one MMA multiplies A^{-1} slice j by the V slices l_lo .. l_lo +
+// nl - 1, and its accumulator block b + t (units of kp columns) receives the
+// pair (j, l_lo + t), of diagonal d = j + l_lo + t. Four banks place the
+// blocks so that every diagonal d <= 3 block holds exactly one pair (exact
+// over 256 rows); the d = 4..6 blocks of banks 0 and 1 take several.
+//   bank 0: blocks 0..6 = d 0..6; bank 1: blocks 7..12 = d 1..6;
+//   bank 2: blocks 13, 14 = d 2, 3; bank 3: block 15 = d 3.
+// (16 blocks of kp <= 32 columns: the 512 columns of tensor memory.)
+constexpr int NMMA_A = 9, NMMA_C = 10;
+struct MmaA { int j, l, nl, blk, fresh; };
+__device__ constexpr MmaA kMmaA[NMMA_A] = {
+    {0, 0, 7, 0, 1}, {1, 0, 6, 7, 1}, {2, 0, 2, 13, 1}, {2, 2, 3, 4, 0}, {3, 0, 1, 15, 1},
+    {3, 1, 3, 10, 0}, {4, 0, 3, 4, 0}, {5, 0, 2, 11, 0}, {6, 0, 1, 6, 0}};
+// Phase C's MMAs per K-step: W slice j times the T slices l .. l + nl - 1,
+// accumulator block (units of 64 columns) = diagonal d = j + l; every block
+// is exact (at most 7 pairs x 32 terms: 7 x 32 x 65025 < 2^24).
+struct MmaC { int j, l, nl, fresh; };
+__device__ constexpr MmaC kMmaC[NMMA_C] = {
+    {0, 0, 4, 1}, {0, 4, 3, 1}, {1, 0, 4, 0}, {1, 4, 2, 0}, {2, 0, 4, 0},
+    {2, 4, 1, 0}, {3, 0, 4, 0}, {4, 0, 3, 0}, {5, 0, 2, 0}, {6, 0, 1, 0}};
 }  // namespace ozf
+
+// Column exponents of walker w's A^{-1} (largest biased exponent per column),
+// computed by all CTAs of the group at the start of the walker's sweep; every
+// emulated flush then keeps them up to date (phase C). A flush by
+// flush_columns_small, which does not, only ends a sweep.
+template <typename T>
+__device__ void oz_colexp_init(const SweepParams<T> &p, int w, int grp, int rank)
+{
+    const int N = p.N, ld = p.ld;
+    const ozf::Layout Ly = ozf::layout(N, p.kp);
+    int *cex = (int *)(p.oz + (size_t)grp * p.oz_stride + Ly.cex);
+    const double *Ab = (const double *)p.Ainv + (size_t)w * N * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = rank * SWARPS + warp; c < N; c += p.Gf * SWARPS) {
+        unsigned e = 0;
+        for (int i = 2 * lane; i < N; i += 64) {
+            const double2 u = __ldcg(reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i));
+            e = max(e, (unsigned)max(ozf::bexp(u.x), ozf::bexp(u.y)));
+        }
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) cex[c] = (int)e;
+    }
+}
+template <typename T>
+__device__ __forceinline__ int *oz_vex(const SweepParams<T> &p, int grp)
+{
+    return (int *)(p.oz + (size_t)grp * p.oz_stride + ozf::layout(p.N, p.kp).vex);
+}
 
 // The emulated-fp64 flush of walker w (all Gf CTAs of the group call it; it
 // takes two group barriers of its own). Returns false after a wait ran out of
 // budget (ST_TIMEOUT recorded).
+// Phase A of flush_oz (a function of its own: its register allocation does not
+// compete with the rest of the sweep kernel's).
 template <typename T>
-__device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int rank,
-                         unsigned char *smem, uint32_t tmem, unsigned *tph, unsigned *flush_ctr,
-                         unsigned &n_flush)
+__device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, int grp, int rank, unsigned char *smem,
+                                uint32_t tmem, unsigned *tph)
 {
     using namespace tcf;
     using namespace ozf;
     const int N = p.N, ld = p.ld, K = p.K, kp = p.kp, Gf = p.Gf;
     const Layout Ly = layout(N, kp);
     unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
-    double *part = (double *)(scr + Ly.part);
-    __nv_bfloat16 *wsl = (__nv_bfloat16 *)(scr + Ly.wsl);
-    __nv_bfloat16 *tsl = (__nv_bfloat16 *)(scr + Ly.tsl);
-    int *wex = (int *)(scr + Ly.wex);
-    int *tex = (int *)(scr + Ly.tex);
+    int *cex = (int *)(scr + Ly.cex);
+    int *vex = (int *)(scr + Ly.vex);
+    long long *partS = (long long *)(scr + Ly.part);
+    float *partG = (float *)(scr + Ly.partg);
     unsigned char *reg = smem + p.off_xs;
     unsigned long long *bars = (unsigned long long *)(reg + bar_offset(kp));
     __shared__ int ecol[AM], erow[32], ok_s;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     double *Ab = (double *)p.Ainv + (size_t)w * wN;
     const double *Vb = (const double *)p.V + (size_t)w * wK;
-    const double *Wb = (const double *)p.W + (size_t)w * wK;
     const int *idxw = p.idx + (size_t)w * K;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Nc = Ly.nca * AM;     // row stride of the partial T' buffers
-
     auto wait_bar = [&](int b) -> bool {
         if (tid == 0) ok_s = mbar_wait(&bars[b], tph[b], p.status, p.budget_ns) ? 1 : 0;
         __syncthreads();
@@ -933,121 +1023,106 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
 
     // ------------------------------------------------------------ phase A
     {
+        // T'[c][m] partial over rows [r0, r0 + AR) of column tile c0: raw fp64
+        // K-blocks of AK rows arrive by asynchronous copies NSLOT - 1 blocks
+        // ahead; each block
+        // is cut into slices with the column exponents of A^{-1} (cex) and the
+        // row exponents of V (vex), which every row chunk shares, so that the
+        // partials add up exactly as integers
         const int nA = Ly.nca * Ly.nrc;
-        const uint32_t idA = idesc_bf16(AM, kp);
-        const size_t aplane = (size_t)AM * AK, bplane = (size_t)kp * AK;   // bf16 elements
-        __nv_bfloat16 *sa = (__nv_bfloat16 *)reg;                          // [2][NS][AM*AK]
-        __nv_bfloat16 *sb = sa + 2 * NS * aplane;                          // [2][NS][kp*AK]
-        const int kk = (tid & 3) * 8;
-        const int ca = tid >> 2;               // columns ca and ca + 64 of the item
-        const int mb = tid >> 2;               // V row of this thread (if < kp)
+        const int nkb = AR / AK;
+        const size_t aplane = (size_t)AM * AK, bplane = (size_t)kp * AK;   // fp16 elements
+        double *raw = (double *)reg;                                       // [NSLOT][(AM + kp) * AK]
+        __half *sa = (__half *)(reg + NSLOT * raw_bytes(kp));              // [2][NS][AM*AK]
+        __half *sb = sa + 2 * NS * aplane;                                 // [2][NS][kp*AK]
+        const uint32_t sboA = (AK / 8) * 128;
         for (int it = rank; it < nA; it += Gf) {
             const int ct = it % Ly.nca, rc = it / Ly.nca;
             const int c0 = ct * AM, r0 = rc * AR;
-            // exponents of the item: columns of A^{-1}, rows of V, over rows [r0, r0 + AR)
-            int emc[2] = {0, 0}, emv = 0;
-            for (int kb = 0; kb < AR / AK; ++kb) {
-                const int i = r0 + kb * AK + kk;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = c0 + ca + 64 * h;
-                    if (c < N && i < ld) {
-                        const double2 *src = reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const double2 u = __ldcg(src + q);
-                            emc[h] = max(emc[h], max(bexp(u.x), bexp(u.y)));
-                        }
+            const int ncol = min(AM, N - c0);
+            if (tid < AM) ecol[tid] = tid < ncol ? __ldcg(cex + c0 + tid) : 0;
+            if (tid < 32) erow[tid] = tid < k ? __ldcg(vex + tid) : 0;
+            // raw block kb -> slot kb % NSLOT: 16-byte asynchronous copies by all
+            // threads (zero-filled outside the walker's columns, rows and queue),
+            // one commit group per block
+            auto issue = [&](int kb) {
+                if (kb < nkb) {
+                    const int i = r0 + kb * AK;
+                    double *dst = raw + (size_t)(kb % NSLOT) * (AM + kp) * AK;
+                    for (int u = tid; u < (AM + kp) * (AK / 2); u += STHREADS) {
+                        const int row = u / (AK / 2), part = u - row * (AK / 2);
+                        const bool in = i < ld && (row < AM ? row < ncol : row - AM < k);
+                        const double *s = row < AM ? Ab + (size_t)(c0 + row) * ld + i + 2 * part
+                                                   : Vb + (size_t)(row - AM) * ld + i + 2 * part;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                     ::"r"(su32(dst + (size_t)row * AK + 2 * part)), "l"(in ? s : (const double *)Ab),
+                                       "r"(in ? 16 : 0) : "memory");
                     }
                 }
-                if (mb < k && i < ld) {
-                    const double2 *src = reinterpret_cast<const double2 *>(Vb + (size_t)mb * ld + i);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double2 u = __ldcg(src + q);
-                        emv = max(emv, max(bexp(u.x), bexp(u.y)));
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                emc[0] = max(emc[0], __shfl_xor_sync(0xffffffffu, emc[0], o));
-                emc[1] = max(emc[1], __shfl_xor_sync(0xffffffffu, emc[1], o));
-                emv = max(emv, __shfl_xor_sync(0xffffffffu, emv, o));
-            }
-            if ((tid & 3) == 0) {
-                ecol[ca] = emc[0];
-                ecol[ca + 64] = emc[1];
-                if (mb < 32) erow[mb] = emv;
-            }
-            // K-blocks: slice block kb into stage kb & 1 while the MMAs of block kb - 1 run
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            issue(0);
+            issue(1);
             int pend[2] = {0, 0};
-            for (int kb = 0; kb < AR / AK; ++kb) {
-                const int s = kb & 1;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb & 1, sl = kb % NSLOT;
+                issue(kb + 2);    // its slot was sliced in iteration kb - 1 (an empty group past the end)
                 if (pend[s]) {
-                    if (!wait_bar(s)) return false;
+                    if (!wait_bar(s)) return false;    // (a CTA barrier: also publishes ecol, erow)
                     pend[s] = 0;
                 }
-                const int i = r0 + kb * AK + kk;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = c0 + ca + 64 * h;
+                asm volatile("cp.async.wait_group 2;" ::: "memory");
+                __syncthreads();
+                const int i = r0 + kb * AK;
+                const double *rw = raw + (size_t)sl * (AM + kp) * AK;
+                {
+                    // A^{-1}: thread t cuts rows 8 (t & 1) .. + 7 of column t >> 1
+                    const int c = tid >> 1, kk = (tid & 1) * 8;
                     double x[8];
-                    if (c < N && i < ld) {
-                        const double2 *src = reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i);
+                    const bool in = c < ncol && i < ld;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const double2 u = __ldcg(src + q);
-                            x[2 * q] = u.x;
-                            x[2 * q + 1] = u.y;
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) x[q] = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        const double2 u = in ? *reinterpret_cast<const double2 *>(rw + c * AK + kk + 2 * q)
+                                             : make_double2(0.0, 0.0);
+                        x[2 * q] = u.x;
+                        x[2 * q + 1] = u.y;
                     }
-                    uint4 sl[NS];
-                    slice8(x, emc[h], sl);
-                    const uint32_t o = coff(ca + 64 * h, kk, AK) >> 1;
+                    uint4 out[NS];
+                    slice8(x, ecol[c], out);
+                    const uint32_t o = coff(c, kk, AK) >> 1;
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
-                        *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = sl[j];
+                        *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = out[j];
                 }
-                if (mb < kp) {
+                if (tid < 2 * kp) {
+                    const int m = tid >> 1, kk = (tid & 1) * 8;
                     double x[8];
-                    if (mb < k && i < ld) {
-                        const double2 *src = reinterpret_cast<const double2 *>(Vb + (size_t)mb * ld + i);
+                    const bool in = m < k && i < ld;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const double2 u = __ldcg(src + q);
-                            x[2 * q] = u.x;
-                            x[2 * q + 1] = u.y;
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) x[q] = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + m) * AK + kk + 2 * q)
+                                             : make_double2(0.0, 0.0);
+                        x[2 * q] = u.x;
+                        x[2 * q + 1] = u.y;
                     }
-                    uint4 sl[NS];
-                    slice8(x, emv, sl);
-                    const uint32_t o = coff(mb, kk, AK) >> 1;
+                    uint4 out[NS];
+                    slice8(x, erow[m], out);
+                    const uint32_t o = coff(m, kk, AK) >> 1;
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
-                        *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = sl[j];
+                        *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = out[j];
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    for (int ks = 0; ks < AK / 16; ++ks) {
-                        const uint32_t ko = (uint32_t)ks * 256u;
-                        for (int d = 0; d < NS; ++d) {
-                            for (int j = 0; j <= d; ++j) {
-                                const int l = d - j;
-                                const uint64_t ad = sdesc(su32(sa + (s * NS + j) * aplane) + ko, 128, (AK / 8) * 128);
-                                const uint64_t bd = sdesc(su32(sb + (s * NS + l) * bplane) + ko, 128, (AK / 8) * 128);
-                                const bool first = kb == 0 && ks == 0 && (d <= 3 || j == 0);
-                                mma(tmem + (uint32_t)(acc_a(j, l) * kp), ad, bd, idA, first ? 0u : 1u);
-                            }
-                        }
+#pragma unroll
+                    for (int q = 0; q < NMMA_A; ++q) {
+                        const MmaA mm = kMmaA[q];
+                        const uint64_t ad = sdesc(su32(sa + (s * NS + mm.j) * aplane), 128, sboA);
+                        const uint64_t bd = sdesc(su32(sb + (s * NS + mm.l) * bplane), 128, sboA);
+                        const bool first = kb == 0 && mm.fresh;
+                        mma(tmem + (uint32_t)(mm.blk * kp), ad, bd, idesc_f16(AM, mm.nl * kp), first ? 0u : 1u);
                     }
                     commit(&bars[s]);
                 }
@@ -1056,51 +1131,63 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
             for (int s = 0; s < 2; ++s)
                 if (pend[s] && !wait_bar(s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // readout: lanes = columns c, 16 values of m per warp
+            // readout: lanes = columns c, 16 values of m per warp; the d <= 3
+            // diagonals as one exact int64, d = 4..6 as an fp32 tail in units
+            // of 2^-8 of it
             {
                 const int q = warp & 3, m0 = (warp >> 2) * 16;
                 const int c = q * 32 + lane;
                 if (m0 < kp) {
                     const uint32_t lanebase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)m0;
                     long long S[16];
-                    float g4[16], g5[16];
+                    float g[16], g5[16];
                     uint32_t v[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) S[e] = 0;
+                    // blocks of diagonal d (bank layout of kMmaA): d <= 3 exact
+                    constexpr int nblk[4] = {1, 2, 3, 4};
+                    constexpr int blks[4][4] = {{0, 0, 0, 0}, {1, 7, 0, 0}, {2, 8, 13, 0}, {3, 9, 14, 15}};
 #pragma unroll
                     for (int d = 0; d <= 3; ++d) {
                         int Dd[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) Dd[e] = 0;
-                        for (int j = 0; j <= d; ++j) {
-                            ld16(lanebase + (uint32_t)(acc_a(j, d - j) * kp), v);
+#pragma unroll
+                        for (int t = 0; t < nblk[d]; ++t) {
+                            ld16(lanebase + (uint32_t)(blks[d][t] * kp), v);
 #pragma unroll
                             for (int e = 0; e < 16; ++e) Dd[e] += __float2int_rz(__uint_as_float(v[e]));
                         }
 #pragma unroll
                         for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + Dd[e];
                     }
-                    ld16(lanebase + (uint32_t)(10 * kp), v);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) g4[e] = __uint_as_float(v[e]);
-                    ld16(lanebase + (uint32_t)(11 * kp), v);
+                    // the tail: g = D4 + D5 / 2^8 + D6 / 2^16 (blocks 4, 10; 5, 11; 6, 12)
+                    ld16(lanebase + (uint32_t)(6 * kp), v);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) g5[e] = __uint_as_float(v[e]);
-                    const int cg = c0 + c;
-                    if (cg < N) {
-                        const int ec = ecol[c];
-                        double *dst = part + ((size_t)rc * Nc + cg) * kp + m0;
+                    ld16(lanebase + (uint32_t)(12 * kp), v);
 #pragma unroll
-                        for (int e = 0; e < 16; e += 2) {
-                            double y[2];
+                    for (int e = 0; e < 16; ++e) g5[e] = (g5[e] + __uint_as_float(v[e])) * (1.0f / 256.0f);
+                    ld16(lanebase + (uint32_t)(5 * kp), v);
 #pragma unroll
-                            for (int u = 0; u < 2; ++u) {
-                                const float g = g4[e + u] + g5[e + u] * (1.0f / 256.0f);
-                                const double sv = fma((double)g, 1.0 / 256.0, (double)S[e + u]);
-                                y[u] = sv * pow2(ec + erow[m0 + e + u] - 2084);
-                            }
-                            *reinterpret_cast<double2 *>(dst + e) = make_double2(y[0], y[1]);
-                        }
+                    for (int e = 0; e < 16; ++e) g5[e] += __uint_as_float(v[e]);
+                    ld16(lanebase + (uint32_t)(11 * kp), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g5[e] = (g5[e] + __uint_as_float(v[e])) * (1.0f / 256.0f);
+                    ld16(lanebase + (uint32_t)(4 * kp), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g[e] = g5[e] + __uint_as_float(v[e]);
+                    ld16(lanebase + (uint32_t)(10 * kp), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) g[e] += __uint_as_float(v[e]);
+                    if (c < ncol) {
+                        const size_t o = ((size_t)rc * Nc + c0 + c) * kp + m0;
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2)
+                            *reinterpret_cast<longlong2 *>(partS + o + e) = make_longlong2(S[e], S[e + 1]);
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4)
+                            *reinterpret_cast<float4 *>(partG + o + e) = make_float4(g[e], g[e + 1], g[e + 2], g[e + 3]);
                     }
                 }
             }
@@ -1108,7 +1195,32 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
             __syncthreads();
         }
     }
-    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+    return true;
+}
+
+// Phase B of flush_oz.
+template <typename T>
+__device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, int grp, int rank, unsigned char *smem,
+                                uint32_t tmem, unsigned *tph)
+{
+    using namespace tcf;
+    using namespace ozf;
+    const int N = p.N, ld = p.ld, K = p.K, kp = p.kp, Gf = p.Gf;
+    const Layout Ly = layout(N, kp);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    int *cex = (int *)(scr + Ly.cex);
+    int *vex = (int *)(scr + Ly.vex);
+    long long *partS = (long long *)(scr + Ly.part);
+    float *partG = (float *)(scr + Ly.partg);
+    __half *wsl = (__half *)(scr + Ly.wsl);
+    __half *tsl = (__half *)(scr + Ly.tsl);
+    int *wex = (int *)(scr + Ly.wex);
+    int *tex = (int *)(scr + Ly.tex);
+    const size_t wK = (size_t)K * ld;
+    const double *Wb = (const double *)p.W + (size_t)w * wK;
+    const int *idxw = p.idx + (size_t)w * K;
+    const int Nc = Ly.nca * AM;     // row stride of the partial T' buffers
+    const int tid = threadIdx.x;
 
     // ------------------------------------------------------------ phase B
     {
@@ -1123,21 +1235,44 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
             double t[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) t[q] = 0.0;
+            const int ec = in ? __ldcg(cex + c) : 0;
+            __syncwarp();
             if (in) {
+                if (m0 == 0) cex[c] = 0;        // phase C records the new column exponents
+                long long S[8];
+                float g[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    S[q] = 0;
+                    g[q] = 0.f;
+                }
                 for (int rc = 0; rc < Ly.nrc; ++rc) {
-                    const double2 *src = reinterpret_cast<const double2 *>(part + ((size_t)rc * Nc + c) * kp + m0);
+                    const size_t o = ((size_t)rc * Nc + c) * kp + m0;
+                    const longlong2 *s2 = reinterpret_cast<const longlong2 *>(partS + o);
+                    const float4 *g4 = reinterpret_cast<const float4 *>(partG + o);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const double2 u = __ldcg(src + q);
-                        t[2 * q] += u.x;
-                        t[2 * q + 1] += u.y;
+                        const longlong2 u = __ldcg(s2 + q);
+                        S[2 * q] += u.x;
+                        S[2 * q + 1] += u.y;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 u = __ldcg(g4 + q);
+                        g[4 * q] += u.x;
+                        g[4 * q + 1] += u.y;
+                        g[4 * q + 2] += u.z;
+                        g[4 * q + 3] += u.w;
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int m = m0 + q;
-                    if (m < k) t[q] -= (__ldcg(idxw + m) == c) ? 1.0 : 0.0;
-                    else t[q] = 0.0;
+                    if (m < k) {
+                        const int e = ec + __ldcg(vex + m) - 2084;
+                        t[q] = fma((double)g[q], pow2(e - 8), (double)S[q] * pow2(e));
+                        t[q] -= (__ldcg(idxw + m) == c) ? 1.0 : 0.0;
+                    }
                 }
             }
             int em = 0;
@@ -1182,75 +1317,149 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
             wex[i] = em;
         }
     }
-    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+    return true;
+}
+
+// Phase C of flush_oz.
+template <typename T>
+__device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, int grp, int rank, unsigned char *smem,
+                                uint32_t tmem, unsigned *tph)
+{
+    using namespace tcf;
+    using namespace ozf;
+    const int N = p.N, ld = p.ld, K = p.K, kp = p.kp, Gf = p.Gf;
+    const Layout Ly = layout(N, kp);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    int *cex = (int *)(scr + Ly.cex);
+    int *vex = (int *)(scr + Ly.vex);
+    __half *wsl = (__half *)(scr + Ly.wsl);
+    __half *tsl = (__half *)(scr + Ly.tsl);
+    int *wex = (int *)(scr + Ly.wex);
+    int *tex = (int *)(scr + Ly.tex);
+    __shared__ int ok_s;
+    unsigned char *reg = smem + p.off_xs;
+    unsigned long long *bars = (unsigned long long *)(reg + bar_offset(kp));
+    const size_t wN = (size_t)N * ld;
+    double *Ab = (double *)p.Ainv + (size_t)w * wN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto wait_bar = [&](int b) -> bool {
+        if (tid == 0) ok_s = mbar_wait(&bars[b], tph[b], p.status, p.budget_ns) ? 1 : 0;
+        __syncthreads();
+        tph[b] ^= 1u;
+        return ok_s != 0;
+    };
 
     // ------------------------------------------------------------ phase C
     {
+        // each CTA takes a contiguous run of items, row-block major, so that
+        // consecutive items share the W tile; the next item's T tile and column
+        // exponents arrive by bulk copy while the current one computes
         const int nC = Ly.nrb * Ly.nct;
-        const uint32_t idC = idesc_bf16(CM, CN);
+        const int per = (nC + Gf - 1) / Gf;
+        const int it0 = min(nC, rank * per), it1 = min(nC, it0 + per);
         const uint32_t sbo = (uint32_t)(kp / 8) * 128u;
-        __nv_bfloat16 *swt = (__nv_bfloat16 *)reg;                 // [NS][CM*kp]
-        __nv_bfloat16 *stt = swt + NS * CM * kp;                   // [NS][CN*kp]
-        int *tex_s = ecol;                                         // CN column exponents
-        for (int it = rank; it < nC; it += Gf) {
-            const int rb = it % Ly.nrb, ct = it / Ly.nrb;
+        const unsigned wbytes = (unsigned)(NS * CM * kp * 2), tbytes = (unsigned)(NS * CN * kp * 2);
+        __half *swt = (__half *)reg;                               // [NS][CM*kp]
+        __half *stt = swt + NS * CM * kp;                          // [2][NS][CN*kp]
+        int *stx = (int *)(stt + 2 * NS * CN * kp);                // [2][CN]
+        auto load_t = [&](int it, int b) {
+            const int ct = it % Ly.nct;
+            mbar_expect(&bars[4 + b], tbytes + CN * sizeof(int));
+            bulk_g2s(stt + (size_t)b * NS * CN * kp, tsl + (size_t)ct * NS * CN * kp, tbytes, &bars[4 + b]);
+            bulk_g2s(stx + b * CN, tex + ct * CN, CN * sizeof(int), &bars[4 + b]);
+        };
+        auto load_w = [&](int it) {
+            const int rb = it / Ly.nct;
+            mbar_expect(&bars[3], wbytes);
+            bulk_g2s(swt, wsl + (size_t)rb * NS * CM * kp, wbytes, &bars[3]);
+        };
+        if (rank == 0 && tid < 64) vex[tid] = 0;    // the next queue records its own
+        if (it0 < it1 && tid == 0) {
+            load_w(it0);
+            load_t(it0, 0);
+        }
+        bool wpend = it0 < it1;
+        for (int it = it0; it < it1; ++it) {
+            const int q = it - it0, b = q & 1;
+            const int rb = it / Ly.nct, ct = it - rb * Ly.nct;
             const int i0 = rb * CM, c0 = ct * CN;
-            {
-                const uint4 *srcw = reinterpret_cast<const uint4 *>(wsl + (size_t)rb * NS * CM * kp);
-                const uint4 *srct = reinterpret_cast<const uint4 *>(tsl + (size_t)ct * NS * CN * kp);
-                uint4 *dw = reinterpret_cast<uint4 *>(swt);
-                uint4 *dt = reinterpret_cast<uint4 *>(stt);
-                const int nw4 = NS * CM * kp / 8, nt4 = NS * CN * kp / 8;
-                for (int q = tid; q < nw4; q += STHREADS) dw[q] = __ldcg(srcw + q);
-                for (int q = tid; q < nt4; q += STHREADS) dt[q] = __ldcg(srct + q);
-                if (tid < CN) tex_s[tid] = c0 + tid < N ? __ldcg(tex + c0 + tid) : 0;
+            if (wpend) {
+                if (!wait_bar(3)) return false;
+                wpend = false;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+            if (!wait_bar(4 + b)) return false;
             if (tid == 0) {
+                if (it + 1 < it1) load_t(it + 1, b ^ 1);   // its buffer's last MMAs completed
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int ks = 0; ks < kp / 16; ++ks) {
                     const uint32_t ko = (uint32_t)ks * 256u;
-                    for (int d = 0; d < NS; ++d) {
-                        for (int j = 0; j <= d; ++j) {
-                            const int l = d - j;
-                            const uint64_t ad = sdesc(su32(swt + (size_t)j * CM * kp) + ko, 128, sbo);
-                            const uint64_t bd = sdesc(su32(stt + (size_t)l * CN * kp) + ko, 128, sbo);
-                            mma(tmem + (uint32_t)(d * CN), ad, bd, idC, (ks == 0 && j == 0) ? 0u : 1u);
-                        }
+#pragma unroll
+                    for (int u = 0; u < NMMA_C; ++u) {
+                        const MmaC mm = kMmaC[u];
+                        const uint64_t ad = sdesc(su32(swt + (size_t)mm.j * CM * kp) + ko, 128, sbo);
+                        const uint64_t bd = sdesc(su32(stt + ((size_t)b * NS + mm.l) * CN * kp) + ko, 128, sbo);
+                        mma(tmem + (uint32_t)((mm.j + mm.l) * CN), ad, bd, idesc_f16(CM, mm.nl * CN),
+                            (ks == 0 && mm.fresh) ? 0u : 1u);
                     }
                 }
                 commit(&bars[2]);
             }
+            // lanes = rows i; warps 0-3 take columns 0..31, warps 4-7 columns 32..63;
+            // the first 16 values of A^{-1} are read while the MMAs run
+            const int qw = warp & 3;
+            const int i = i0 + qw * 32 + lane;
+            const int cb = (warp >> 2) * 32;
+            const bool rowin = i < N;
+            const int ei = rowin ? __ldcg(wex + i) : 0;
+            double xa[16];
+            auto load_x = [&](int j0) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = c0 + j0 + e;
+                    xa[e] = (rowin && c < N) ? __ldcg(Ab + (size_t)c * ld + i) : 0.0;
+                }
+            };
+            load_x(cb);
             if (!wait_bar(2)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // lanes = rows i; warps 0-3 take columns 0..31, warps 4-7 columns 32..63
-            {
-                const int q = warp & 3;
-                const int i = i0 + q * 32 + lane;
-                const int ei = i < N ? __ldcg(wex + i) : 0;
-                const int cb = (warp >> 2) * 32;
-                for (int j0 = cb; j0 < cb + 32; j0 += 16) {
-                    long long S[16];
-                    uint32_t v[16];
+            if (it + 1 < it1 && (it + 1) / Ly.nct != rb) {
+                if (tid == 0) load_w(it + 1);              // the W tile's MMAs completed
+                wpend = true;
+            }
+            for (int j0 = cb; j0 < cb + 32; j0 += 16) {
+                long long S[16];
+                uint32_t v[16];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) S[e] = 0;
+                for (int e = 0; e < 16; ++e) S[e] = 0;
 #pragma unroll
-                    for (int d = 0; d < NS; ++d) {
-                        ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * CN + j0), v);
+                for (int d = 0; d < NS - 1; ++d) {
+                    ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(d * CN + j0), v);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + __float2int_rz(__uint_as_float(v[e]));
-                    }
-                    if (i < N) {
+                    for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + __float2int_rz(__uint_as_float(v[e]));
+                }
+                // S = sum_{d <= 5} D_d 2^(8(5 - d)) < 2^61.02; the d = 6 diagonal
+                // joins as 2 S + round(D_6 / 2^7) (an error of 2^-63 of the leading term)
+                ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((NS - 1) * CN + j0), v);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int c = c0 + j0 + e;
-                            if (c < N) {
-                                double *x = Ab + (size_t)c * ld + i;
-                                *x = fma(-(double)S[e], pow2(ei + tex_s[j0 + e] - 2100), __ldcg(x));
-                            }
-                        }
-                    }
+                for (int e = 0; e < 16; ++e) S[e] = 2 * S[e] + ((__float2int_rz(__uint_as_float(v[e])) + 64) >> 7);
+                double y[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) y[e] = xa[e] - scaled_i64(S[e], ei + stx[b * CN + j0 + e] - 2101);
+                if (j0 == cb) load_x(cb + 16);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = c0 + j0 + e;
+                    if (rowin && c < N) Ab[(size_t)c * ld + i] = y[e];
+                }
+                // exponents of the new columns for the next flush's phase A
+                unsigned mx[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    mx[e] = __reduce_max_sync(0xffffffffu, (rowin && c0 + j0 + e < N) ? (unsigned)bexp(y[e]) : 0u);
+                if (lane == 0) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + j0 + e < N) atomicMax(cex + c0 + j0 + e, (int)mx[e]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1260,12 +1469,41 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
     return true;
 }
 
+template <typename T>
+__device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int rank,
+                         unsigned char *smem, uint32_t tmem, unsigned *tph, unsigned *flush_ctr,
+                         unsigned &n_flush)
+{
+    const int Gf = p.Gf, tid = threadIdx.x;
+    // wall time of the three phases (barrier waits included) as seen by
+    // group 0's first CTA, into the profile's phase timers 8..10
+    const bool timed = p.phase_ns && grp == 0 && rank == 0 && tid == 0;
+    unsigned long long tp = timed ? globaltimer() : 0ull;
+    auto tick = [&](int slot) {
+        if (timed) {
+            const unsigned long long t = globaltimer();
+            p.phase_ns[slot] += t - tp;
+            tp = t;
+        }
+    };
+
+    if (!oz_phase_a(p, w, k, grp, rank, smem, tmem, tph)) return false;
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+    tick(8);
+    if (!oz_phase_b(p, w, k, grp, rank, smem, tmem, tph)) return false;
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+    tick(9);
+    if (!oz_phase_c(p, w, k, grp, rank, smem, tmem, tph)) return false;
+    tick(10);
+    return true;
+}
+
 template <typename T, bool RES, int FM>
 __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_t tmem)
 {
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
     if (grp >= p.ngroups) return;
-    unsigned tph[4] = {0, 0, 0, 0};  // phases of the tensor-core flush's mbarriers
+    unsigned tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // phases of the tensor-core flush's mbarriers
     const int N = p.N, K = p.K, ld = p.ld, Gf = p.Gf, Gr = p.Gr;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     unsigned *ratio_ctr = p.sync + SYNC_STRIDE * grp + 0;
@@ -1280,6 +1518,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
         // Helper CTA: take part in every flush of every walker of the group.
         for (int t = grp; t < p.nw; t += p.ngroups) {
             const int w = p.wlist ? __ldg(p.wlist + t) : t;
+            if (FM == FM_OZ) oz_colexp_init(p, w, grp, rank);
             for (;;) {
                 if (!group_wait_for(cmd, 2u * (n_event + 1), p.status, p.budget_ns, 128)) return;
                 const bool last = (ld_acquire(cmd) & 1u) != 0;
@@ -1317,7 +1556,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     T *Wsm = (T *)(smem + p.off_wsm);                  // RES: [K][LP]
     T *Vsm = (T *)(smem + p.off_vsm);                  // RES: [K][LP]
     __shared__ double rr_s, u_s[2];
-    __shared__ int acc_s;
+    __shared__ int acc_s, vx_s[2];
     const int chunk = p.chunk, LP = chunk + 1;
     const int i0 = rank * chunk;
     const int L = max(0, min(chunk, N - i0));
@@ -1332,8 +1571,13 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
         const double *Uw = p.unif + (size_t)w * N;
         T *Ww = p.W + (size_t)w * wK;
         T *Vw = p.V + (size_t)w * wK;
+        if (FM == FM_OZ) {
+            oz_colexp_init(p, w, grp, rank);
+            if (threadIdx.x < 2) vx_s[threadIdx.x] = 0;
+        }
 
-        // proposed row of electron jj (v = a_jj + sigma g) and column jj of A^{-1}
+        // proposed row of electron jj (v = a_jj + sigma g) and column jj of A^{-1};
+        // with the emulated flush also the largest exponent of the CTA's part of v
         auto stage = [&](int jj, int bb, bool row, bool col) {
             if (row) {
                 const double *arow = Aw + (size_t)jj * ld + i0;
@@ -1342,6 +1586,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     const double v = arow[t] + p.sigma * __ldcg(grow + t);
                     vs[bb * chunk + t] = (T)v;
                     vd[bb * chunk + t] = v;
+                    if (FM == FM_OZ) atomicMax(&vx_s[bb], ozf::bexp(v));
                 }
                 if (threadIdx.x == 0) u_s[bb] = __ldcg(Uw + jj);
             }
@@ -1368,6 +1613,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             const T *vsb = vs + b * chunk, *asb = as + b * chunk;
             const double *vdb = vd + b * chunk;
             __syncthreads();
+            if (FM == FM_OZ && threadIdx.x == 0) vx_s[b ^ 1] = 0;   // staged below (after a barrier)
             // ---- partial dot products over the chunk: d, y_m = W[m].v, c_m = V[m].a
             double *part = p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
             if (RES) {
@@ -1548,6 +1794,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         }
                     }
                 }
+                if (FM == FM_OZ && threadIdx.x == 0) atomicMax(oz_vex(p, grp) + k, vx_s[b]);
                 ++k;
             }
             tick(4);
@@ -1575,6 +1822,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     if (!flush_oz(p, w, k, grp, rank, smem, tmem, tph, flush_ctr, n_flush)) return;
                 } else if (k > 0) {
                     flush_columns_small(p, w, k, fc0, fc1);
+                    if (rank == 0 && threadIdx.x < 64) oz_vex(p, grp)[threadIdx.x] = 0;
                 }
             } else if (FM == FM_TC) {
                 if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
@@ -1619,7 +1867,7 @@ __global__ void __launch_bounds__(STHREADS, FM == FM_SIMT ? 2 : 1) sweep_kernel(
         mbar_init((unsigned long long *)(smem + p.off_bar));
         if (TC) {
             unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < (FM == FM_OZ ? ozf::NBAR : 4); ++q)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
@@ -1857,9 +2105,14 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
                     K <= 64 && cpc >= 128;
     if (tc) return launch_shape<T, false, FM_TC>(c, L, Gf, Gr, chunk);
     if constexpr (std::is_same<T, double>::value) {
-        // emulated-fp64 flush: fp64 walkers shared by several CTAs, K <= 32
-        if (use_oz(c, Gf)) return res ? launch_shape<T, true, FM_OZ>(c, L, Gf, Gr, chunk)
+        // emulated-fp64 flush: fp64 walkers shared by several CTAs, K <= 32;
+        // where its shared memory does not fit beside the resident queue rows
+        // (launch_shape refuses before launching), the fp64-unit flush
+        if (use_oz(c, Gf)) {
+            const cudaError_t e = res ? launch_shape<T, true, FM_OZ>(c, L, Gf, Gr, chunk)
                                       : launch_shape<T, false, FM_OZ>(c, L, Gf, Gr, chunk);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
     }
     return res ? launch_shape<T, true, FM_SIMT>(c, L, Gf, Gr, chunk)
                : launch_shape<T, false, FM_SIMT>(c, L, Gf, Gr, chunk);

@@ -110,7 +110,7 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
         c->sync_words = (int)(cap * 96);
         AL(c->sw_partial, c->sw_partial_len * sizeof(double));
         AL(c->sw_sync, cap * 96 * sizeof(unsigned));
-        AL(c->sw_phase, 8 * sizeof(unsigned long long));
+        AL(c->sw_phase, 11 * sizeof(unsigned long long));
         AL(c->sw_gauss, B * NN * sizeof(double));
         AL(c->sw_unif, B * N * sizeof(double));
         AL(c->d_params, 2 * sizeof(unsigned long long));
@@ -1134,7 +1134,7 @@ int qmcdu_profile_enable(qmcdu_t h, int enable)
     drop_events(c);
     c->prof = enable != 0;
     c->n_launch = c->n_flush = c->n_recompute = c->n_sync = c->n_ratio = c->n_accept = 0;
-    CK(cudaMemsetAsync(c->sw_phase, 0, 8 * sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(c->sw_phase, 0, 11 * sizeof(unsigned long long), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return QMCDU_OK;
 }
@@ -1160,16 +1160,17 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n)
         CK(cudaEventElapsedTime(&ms, p.first, p.second));
         ms_rec += ms;
     }
-    unsigned long long ph[8];
+    unsigned long long ph[11];
     CK(cudaMemcpyAsync(ph, c->sw_phase, sizeof ph, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const double vals[18] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
+    const double vals[21] = {(double)c->n_launch, (double)c->n_flush, ms_flush,
                              (double)c->n_recompute, ms_rec, (double)c->n_sync,
                              (double)c->n_ratio, (double)c->n_accept,
                              ph[0] * 1e-6, ph[1] * 1e-6, ph[2] * 1e-6, ph[3] * 1e-6,
                              ph[4] * 1e-6, ph[5] * 1e-6, ph[6] * 1e-6, ph[7] * 1e-6,
-                             (double)c->ev_sweep.size(), ms_sweep};
-    for (int i = 0; i < n && i < 18; ++i) out[i] = vals[i];
+                             (double)c->ev_sweep.size(), ms_sweep,
+                             ph[8] * 1e-6, ph[9] * 1e-6, ph[10] * 1e-6};
+    for (int i = 0; i < n && i < 21; ++i) out[i] = vals[i];
     return QMCDU_OK;
 }
 

@@ -84,7 +84,7 @@ struct Ctx {
     double *sw_partial = nullptr;   // capacity x 2 x (2K+1)
     size_t sw_partial_len = 0;
     unsigned *sw_sync = nullptr;    // capacity x 4
-    unsigned long long *sw_phase = nullptr;  // 8 phase timers of the persistent sweep
+    unsigned long long *sw_phase = nullptr;  // 11 phase timers of the persistent sweep
     double *sw_gauss = nullptr;     // batch x N x ld proposal Gaussians of the current sweep
     double *sw_unif = nullptr;      // batch x N Metropolis uniforms of the current sweep
     int sync_words = 0;

@@ -315,7 +315,8 @@ def qmcdu_sweep_shape(h):
 PROFILE_FIELDS = ("launches", "flushes", "flush_ms", "recomputes", "recompute_ms", "sweep_syncs",
                   "ratio_launches", "accept_launches", "sweep_dots_ms", "sweep_stage_ms",
                   "sweep_barrier_ms", "sweep_decide_ms", "sweep_accept_ms", "sweep_flushbar1_ms",
-                  "sweep_flush_ms", "sweep_flushbar2_ms", "sweep_kernels", "sweep_kernel_ms")
+                  "sweep_flush_ms", "sweep_flushbar2_ms", "sweep_kernels", "sweep_kernel_ms",
+                  "sweep_oz_products_ms", "sweep_oz_slicing_ms", "sweep_oz_update_ms")
 
 
 def qmcdu_profile_enable(h, enable=True):
