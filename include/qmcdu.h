@@ -257,6 +257,14 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       recombination; near 2^-53 relative to |row| |column|, the error of
  *       fp64 arithmetic) where it applies: 4 <= K <= 32 and walker groups of
  *       two or more CTAs
+ *   QMCDU_OPT_CLUSTER      [0: off] persistent sweeps of fp64 walkers (at
+ *       most 4 walkers, N >= 1024, no fixed group shape, ratio or flush CTA
+ *       counts left automatic): 2 = the 16 ratio CTAs of a walker form one
+ *       thread-block cluster and exchange the partial dot products of every
+ *       proposal through distributed shared memory (sweep_shape then reports
+ *       16 ratio CTAs); results agree with the global-memory exchange to
+ *       rounding (other sums of the same terms). Slower than the default at
+ *       N = 2048 (fp64 work on 16 CTAs instead of 64); 0 and 1 = off
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {
@@ -267,7 +275,8 @@ enum {
     QMCDU_OPT_TEST_STALL = 5,
     QMCDU_OPT_MAX_CTAS = 6,
     QMCDU_OPT_GROUP_CTAS = 7,
-    QMCDU_OPT_FP64_FLUSH = 8
+    QMCDU_OPT_FP64_FLUSH = 8,
+    QMCDU_OPT_CLUSTER = 9
 };
 int qmcdu_set_option(qmcdu_t h, int option, long long value);
 

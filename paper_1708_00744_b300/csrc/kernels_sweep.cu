@@ -85,6 +85,7 @@ struct SweepParams {
     unsigned char *oz;              // emulated-fp64 flush: per-group scratch (ozf::layout)
     size_t oz_stride;               // bytes per walker group
     int off_tcbar;                  // the tensor-core flush's mbarriers (offset in shared memory)
+    int off_cl;                     // cluster mode: [2][2K+1] partial dot products, then a flag
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -143,6 +144,58 @@ __device__ __forceinline__ bool group_barrier(unsigned *ctr, unsigned target, in
 {
     group_arrive(ctr);
     return group_wait_for(ctr, target, status, budget_ns);
+}
+
+// ---- distributed shared memory of a thread-block cluster (cluster mode: the
+// ratio CTAs of a walker form one cluster and exchange their partial dot
+// products through each other's shared memory)
+__device__ __forceinline__ uint32_t cl_map(const void *local, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ unsigned cl_ld_acquire(uint32_t addr)
+{
+    unsigned v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ double cl_ld_f64(uint32_t addr)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st_release(unsigned *local, unsigned v)
+{
+    asm volatile("st.release.cluster.shared::cta.u32 [%0], %1;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(local)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Wait until the flags of cluster ranks 0 .. n - 1 reach `target` (threads
+// 0 .. n - 1 poll one each), with a time budget; uniform result for the CTA.
+__device__ bool cl_wait_flags(const unsigned *flag, unsigned target, int n, int *status,
+                              long long budget_ns)
+{
+    bool ok = true;
+    if ((int)threadIdx.x < n) {
+        const uint32_t a = cl_map(flag, threadIdx.x);
+        const unsigned long long t0 = globaltimer();
+        unsigned spins = 0;
+        while (cl_ld_acquire(a) < target) {
+            if ((++spins & 63u) == 0 && (long long)(globaltimer() - t0) > budget_ns) {
+                atomicOr(status, ST_TIMEOUT);
+                ok = false;
+                break;
+            }
+        }
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
 template <typename T>
@@ -1498,7 +1551,7 @@ __device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int ran
     return true;
 }
 
-template <typename T, bool RES, int FM>
+template <typename T, bool RES, int FM, bool CL>
 __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_t tmem)
 {
     const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
@@ -1555,8 +1608,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     T *coef = (T *)(smem + p.off_ts);                  // accept: [0,K) c_m, [K,2K) y_m/r, [2K,..) z
     T *Wsm = (T *)(smem + p.off_wsm);                  // RES: [K][LP]
     T *Vsm = (T *)(smem + p.off_vsm);                  // RES: [K][LP]
-    __shared__ double rr_s, u_s[2];
-    __shared__ int acc_s, vx_s[2];
+    __shared__ double u_s[2];
+    __shared__ int vx_s[2];
     const int chunk = p.chunk, LP = chunk + 1;
     const int i0 = rank * chunk;
     const int L = max(0, min(chunk, N - i0));
@@ -1614,21 +1667,48 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             const double *vdb = vd + b * chunk;
             __syncthreads();
             if (FM == FM_OZ && threadIdx.x == 0) vx_s[b ^ 1] = 0;   // staged below (after a barrier)
+            // ---- the next proposal's inputs (row j + 1 of A and its Gaussians,
+            // column j + 1 of A^{-1}, u): loaded now, so that their latency
+            // overlaps the dot products, and staged after the arrival below
+            const bool pf = L <= STHREADS && j + 1 < N;
+            double pa = 0.0, pg = 0.0, pu = 0.0;
+            T pc = 0;
+            if (pf) {
+                if (threadIdx.x < L) {
+                    pa = Aw[(size_t)(j + 1) * ld + i0 + threadIdx.x];
+                    pg = __ldcg(Gw + (size_t)(j + 1) * ld + i0 + threadIdx.x);
+                    pc = __ldcg(Ainv + (size_t)(j + 1) * ld + i0 + threadIdx.x);
+                }
+                if (threadIdx.x == 0) pu = __ldcg(Uw + j + 1);
+            }
             // ---- partial dot products over the chunk: d, y_m = W[m].v, c_m = V[m].a
-            double *part = p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
+            // (cluster mode: into this CTA's shared memory, for the siblings to read)
+            double *clp = (double *)(smem + p.off_cl);
+            unsigned *clflag = (unsigned *)(clp + 2 * nj);
+            double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
             if (RES) {
-                for (int job = threadIdx.x; job < 2 * k + 1; job += STHREADS) {
+                // G consecutive lanes per job (a power of two up to 8 that the
+                // CTA's threads allow), lane g taking elements g, g + G, ...,
+                // then a fixed shuffle tree over the group
+                const int njk = 2 * k + 1;
+                int G = 1;
+                while (G < 8 && 2 * G * njk <= STHREADS) G *= 2;
+                for (int t0 = threadIdx.x; t0 < njk * G; t0 += STHREADS) {
+                    const int job = t0 / G, g = t0 - job * G;
                     const T *src = job == 0 ? asb : (job <= k ? Wsm + (job - 1) * LP : Vsm + (job - 1 - k) * LP);
                     const T *with = job <= k ? vsb : asb;
                     T acc0 = 0, acc1 = 0;
-                    int t = 0;
+                    int t = g;
 #pragma unroll 4
-                    for (; t + 1 < L; t += 2) {
+                    for (; t + G < L; t += 2 * G) {
                         acc0 += src[t] * with[t];
-                        acc1 += src[t + 1] * with[t + 1];
+                        acc1 += src[t + G] * with[t + G];
                     }
                     if (t < L) acc0 += src[t] * with[t];
-                    part[job] = (double)acc0 + (double)acc1;
+                    double s = (double)acc0 + (double)acc1;
+                    const unsigned act = __activemask();
+                    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(act, s, o, G);
+                    if (g == 0) part[job] = s;
                 }
             } else {
                 // queue rows in global memory: four jobs per warp at a time, so that
@@ -1660,10 +1740,30 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             tick(0);
             // ---- arrive, stage the next proposal (its column speculatively), wait
             const unsigned extra = (p.stall && n_ratio == 0) ? 1u : 0u;
-            group_arrive(ratio_ctr);
-            if (j + 1 < N) stage(j + 1, b ^ 1, true, true);
+            if (CL) {
+                __syncthreads();                       // every partial written
+                if (threadIdx.x == 0) cl_st_release(clflag, n_ratio + 1);
+            } else {
+                group_arrive(ratio_ctr);
+            }
+            if (pf) {
+                if (threadIdx.x < L) {
+                    const double v = pa + p.sigma * pg;
+                    vs[(b ^ 1) * chunk + threadIdx.x] = (T)v;
+                    vd[(b ^ 1) * chunk + threadIdx.x] = v;
+                    as[(b ^ 1) * chunk + threadIdx.x] = pc;
+                    if (FM == FM_OZ) atomicMax(&vx_s[b ^ 1], ozf::bexp(v));
+                }
+                if (threadIdx.x == 0) u_s[b ^ 1] = pu;
+            } else if (j + 1 < N) {
+                stage(j + 1, b ^ 1, true, true);
+            }
             tick(1);
-            if (!group_wait_for(ratio_ctr, (++n_ratio) * Gr + extra, p.status, p.budget_ns)) return;
+            if (CL) {
+                if (!cl_wait_flags(clflag, ++n_ratio, Gr, p.status, p.budget_ns)) return;
+            } else if (!group_wait_for(ratio_ctr, (++n_ratio) * Gr + extra, p.status, p.budget_ns)) {
+                return;
+            }
             tick(2);
             // ---- every ratio CTA sums the partials in the same order: G
             // consecutive lanes per job (a power of two up to 8 that the CTA's
@@ -1678,14 +1778,27 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     const int job = t / G, g = t - job * G;
                     double s = 0.0;
                     int q = g;
-                    for (; q + 7 * G < Gr; q += 8 * G) {
-                        double x[8];
+                    if (CL) {
+                        // sibling q's partials in its shared memory, same order
+                        const double *mine = clp + b * nj + job;
+                        for (; q + 7 * G < Gr; q += 8 * G) {
+                            double x[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e * G) * nj + job);
+                            for (int e = 0; e < 8; ++e) x[e] = cl_ld_f64(cl_map(mine, q + e * G));
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) s += x[e];
+                            for (int e = 0; e < 8; ++e) s += x[e];
+                        }
+                        for (; q < Gr; q += G) s += cl_ld_f64(cl_map(mine, q));
+                    } else {
+                        for (; q + 7 * G < Gr; q += 8 * G) {
+                            double x[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e * G) * nj + job);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) s += x[e];
+                        }
+                        for (; q < Gr; q += G) s += __ldcg(pb + (size_t)q * nj + job);
                     }
-                    for (; q < Gr; q += G) s += __ldcg(pb + (size_t)q * nj + job);
                     // groups are whole (njk * G is a multiple of G), so the active
                     // lanes of the warp hold complete groups
                     const unsigned act = __activemask();
@@ -1694,55 +1807,67 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 }
             }
             __syncthreads();
-            if (warp == 0) {
+            // ---- the ratio and the Metropolis decision, computed by every warp
+            // alike from the reduced dots (the same values in the same order),
+            // so that no broadcast is needed
+            double r;
+            int a;
+            {
                 double s = 0.0;
                 for (int m = lane; m < k; m += 32) s += red[1 + m] * red[1 + k + m];
                 s = warp_allsum(s);
-                if (lane == 0) {
-                    const double r = red[0] - s;
-                    const double u = u_s[b];
-                    const double prob = fmin(1.0, r * r);
-                    const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
-                    int a = ov == 0 ? 0 : (ov == 1 ? 1 : (u < prob ? 1 : 0));
-                    if (a && !(r != 0.0 && isfinite(r))) {
-                        a = 0;
-                        if (rank == 0) atomicOr(p.status, ST_SINGULAR);
-                    }
-                    rr_s = r;
-                    acc_s = a;
-                    if (rank == 0) {
-                        p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
-                        p.ratio_out[(size_t)orow * N + j] = r;
-                        if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
-                        if (a) p.idx[(size_t)w * K + k] = j;
-                    }
+                r = red[0] - s;
+                const double u = u_s[b];
+                const double prob = fmin(1.0, r * r);
+                const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
+                a = ov == 0 ? 0 : (ov == 1 ? 1 : (u < prob ? 1 : 0));
+                const bool bad = a && !(r != 0.0 && isfinite(r));
+                if (bad) a = 0;
+                if (rank == 0 && threadIdx.x == 0) {
+                    if (bad) atomicOr(p.status, ST_SINGULAR);
+                    p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
+                    p.ratio_out[(size_t)orow * N + j] = r;
+                    if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
+                    if (a) p.idx[(size_t)w * K + k] = j;
                 }
             }
-            __syncthreads();
             tick(3);
-            if (acc_s) {
+            if (a) {
                 // ---- accept: z = a - W c, W <- [W - z y'/r, z/r], V[k] = v, A[j] = v
-                const double rinv = 1.0 / rr_s;
+                const double rinv = 1.0 / r;
                 T *cT = coef, *yT = coef + K, *zs = coef + 2 * K;
                 for (int m = threadIdx.x; m < k; m += STHREADS) {
                     cT[m] = (T)red[1 + k + m];
                     yT[m] = (T)(red[1 + m] * rinv);
                 }
-                __syncthreads();
+                if (!RES) __syncthreads();
                 double *arow_w = Aw + (size_t)j * ld;
                 if (RES) {
-                    for (int t = threadIdx.x; t < L; t += STHREADS) {
-                        T z0 = asb[t], z1 = 0;
-                        int m = 0;
-#pragma unroll 4
-                        for (; m + 1 < k; m += 2) {
-                            z0 -= cT[m] * Wsm[m * LP + t];
-                            z1 -= cT[m + 1] * Wsm[(m + 1) * LP + t];
+                    // z = a - W c: ZG consecutive lanes per row, lane g taking
+                    // m = g, g + ZG, ..., then a fixed shuffle tree
+                    constexpr int ZG = 8;
+                    for (int t0 = threadIdx.x; t0 < ((L + 31) / 32) * 32 * ZG; t0 += STHREADS) {
+                        const int t = t0 / ZG, g = t0 - t * ZG;
+                        T z0 = 0, z1 = 0;
+                        if (t < L) {
+                            // c_m straight from the reduction (cT is written in this same step)
+                            const double *cr = red + 1 + k;
+                            int m = g;
+#pragma unroll 2
+                            for (; m + ZG < k; m += 2 * ZG) {
+                                z0 += (T)cr[m] * Wsm[m * LP + t];
+                                z1 += (T)cr[m + ZG] * Wsm[(m + ZG) * LP + t];
+                            }
+                            if (m < k) z0 += (T)cr[m] * Wsm[m * LP + t];
                         }
-                        if (m < k) z0 -= cT[m] * Wsm[m * LP + t];
-                        zs[t] = z0 + z1;
-                        Vsm[k * LP + t] = vsb[t];
-                        arow_w[i0 + t] = vdb[t];
+                        T z = z0 + z1;
+#pragma unroll
+                        for (int o = ZG / 2; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o, ZG);
+                        if (g == 0 && t < L) {
+                            zs[t] = asb[t] - z;
+                            Vsm[k * LP + t] = vsb[t];
+                            arow_w[i0 + t] = vdb[t];
+                        }
                     }
                     __syncthreads();
                     const T rT = (T)rinv;
@@ -1848,7 +1973,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 // The kernel: tensor memory for the tensor-core flush (256 columns: two of
 // these CTAs at most share an SM, 2 x 256 = 512 columns), the mbarriers, the
 // sweep, and the release of the tensor memory on every exit path.
-template <typename T, bool RES, int FM>
+template <typename T, bool RES, int FM, bool CL>
 __global__ void __launch_bounds__(STHREADS, FM == FM_SIMT ? 2 : 1) sweep_kernel(SweepParams<T> p)
 {
     constexpr bool TC = FM != FM_SIMT;
@@ -1872,10 +1997,16 @@ __global__ void __launch_bounds__(STHREADS, FM == FM_SIMT ? 2 : 1) sweep_kernel(
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
+    if (CL && threadIdx.x == 0) *(unsigned *)(smem + p.off_cl + 2 * (2 * p.K + 1) * sizeof(double)) = 0u;
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    sweep_body<T, RES, FM>(p, smem, TC ? tmem_s : 0u);
+    // cluster mode: every CTA's flag is set before any sibling reads it, and
+    // every CTA's shared memory stays in place until no sibling reads it
+    // (the only unbounded waits, both at fixed points every CTA reaches)
+    if (CL) cl_barrier();
+    sweep_body<T, RES, FM, CL>(p, smem, TC ? tmem_s : 0u);
+    if (CL) cl_barrier();
     if (TC) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (TC && threadIdx.x < 32)
@@ -1952,7 +2083,8 @@ static size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 static const size_t OZ_MIN_SMEM = 118 * 1024;
 
 template <typename T>
-static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int fm, bool block, int *offs)
+static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int fm, bool block, int *offs,
+                         bool cl = false)
 {
     size_t o = 0;
     offs[8] = (int)o; o = align16(o + 16);                                   // mbarrier
@@ -1971,6 +2103,7 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int fm, boo
     o = align16(o + region);
     offs[6] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Wsm
     offs[7] = (int)o; if (res) o = align16(o + (size_t)K * (chunk + 1) * sizeof(T));  // Vsm
+    offs[10] = (int)o; if (cl) o = align16(o + (size_t)2 * (2 * K + 1) * sizeof(double) + 16);  // partials, flag
     // the emulated-fp64 flush allocates all 512 tensor-memory columns: more than
     // half of the SM's shared memory keeps a second CTA off the SM
     if (fm == FM_OZ) o = std::max(o, (size_t)OZ_MIN_SMEM);
@@ -1980,45 +2113,81 @@ static size_t sweep_smem(int ld, int K, int chunk, int cb, bool res, int fm, boo
 static const size_t SMEM_BUDGET = 200 * 1024;
 static const size_t RES_BUDGET = 128 * 1024;
 
-template <typename T, bool RES, int FM>
+// Cluster mode: the Gr = CLS ratio CTAs of a walker are one thread-block
+// cluster; every walker group is a whole number of clusters.
+constexpr int CLS = 16;
+static const size_t CL_SMEM_BUDGET = 216 * 1024;
+
+template <typename T, bool RES, int FM, bool CL>
 static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, int chunk)
 {
     const int K = c.K;
-    int offs[10];
+    int offs[11];
+    const size_t budget = CL ? CL_SMEM_BUDGET : SMEM_BUDGET;
     int cb = MAX_CB;
     // the wide-block flush (fp64, K <= 64) when its tiles fit beside everything
     // else: fp64 arithmetic hides its staging; in fp32 (one CTA of 8 warps per SM)
     // the staging latency does not hide and the column tiles are as fast
     bool block = FM == FM_SIMT && K <= BT && std::is_same<T, double>::value;
-    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
-    while (cb > 1 && smem > SMEM_BUDGET) {
+    size_t smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs, CL);
+    while (cb > 1 && smem > budget) {
         cb >>= 1;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs, CL);
     }
-    if (smem > SMEM_BUDGET && block) {
+    if (smem > budget && block) {
         block = false;
         cb = MAX_CB;
-        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
-        while (cb > 1 && smem > SMEM_BUDGET) {
+        smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs, CL);
+        while (cb > 1 && smem > budget) {
             cb >>= 1;
-            smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs);
+            smem = sweep_smem<T>(c.ld, K, chunk, cb, RES, FM, block, offs, CL);
         }
     }
-    if (smem > SMEM_BUDGET) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, FM>,
+    if (smem > budget) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, RES, FM, CL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, FM>, STHREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, FM, CL>, STHREADS, smem);
     if (e != cudaSuccess) return e;
     if (FM == FM_OZ && per_sm > 1) return cudaErrorInvalidConfiguration;   // the TMEM allocation would wait
-    int capacity = per_sm * c.num_sms;
-    if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
-    if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
     const int nw = L.wlist ? L.nlist : c.batch;
-    int ngroups = std::min(nw, std::max(1, capacity / Gf));
-    if (FM == FM_OZ) ngroups = std::min(ngroups, c.oz_groups);
-    if (ngroups < 1) return cudaErrorInvalidConfiguration;
+    int ngroups = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    if (CL) {
+        // as many co-resident clusters as fit, split evenly over the walker groups
+        e = cudaFuncSetAttribute(sweep_kernel<T, RES, FM, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CLS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeCooperative;
+        attr[1].val.cooperative = 1;
+        cfg.gridDim = dim3(CLS);
+        cfg.blockDim = dim3(STHREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c.stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        e = cudaOccupancyMaxActiveClusters(&ncl, (const void *)sweep_kernel<T, RES, FM, CL>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (c.opt_max_ctas > 0) ncl = std::min(ncl, c.opt_max_ctas / CLS);
+        ngroups = std::min(nw, ncl);
+        if (FM == FM_OZ) ngroups = std::min(ngroups, c.oz_groups);
+        if (ngroups < 1) return cudaErrorInvalidConfiguration;
+        Gf = CLS * (ncl / ngroups);
+        Gr = CLS;
+    } else {
+        int capacity = per_sm * c.num_sms;
+        if (c.opt_max_ctas > 0) capacity = std::min(capacity, c.opt_max_ctas);
+        if (capacity < 1 || Gf > capacity) return cudaErrorCooperativeLaunchTooLarge;
+        ngroups = std::min(nw, std::max(1, capacity / Gf));
+        if (FM == FM_OZ) ngroups = std::min(ngroups, c.oz_groups);
+        if (ngroups < 1) return cudaErrorInvalidConfiguration;
+    }
     if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
     if ((size_t)ngroups * 2 * Gr * (2 * K + 1) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
 
@@ -2043,16 +2212,24 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.oz = FM == FM_OZ ? c.oz : nullptr;
     p.oz_stride = c.oz_stride;
     p.off_tcbar = offs[9];
+    p.off_cl = offs[10];
     e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
-    void *args[] = {&p};
-    e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES, FM>, dim3(ngroups * Gf),
-                                    dim3(STHREADS), args, smem, c.stream);
+    if (CL) {
+        cfg.gridDim = dim3(ngroups * Gf);
+        cfg.numAttrs = 2;
+        e = cudaLaunchKernelEx(&cfg, sweep_kernel<T, RES, FM, CL>, p);
+    } else {
+        void *args[] = {&p};
+        e = cudaLaunchCooperativeKernel((const void *)sweep_kernel<T, RES, FM, CL>, dim3(ngroups * Gf),
+                                        dim3(STHREADS), args, smem, c.stream);
+    }
     c.last_sweep_shape[0] = Gf;
     c.last_sweep_shape[1] = Gr;
     c.last_sweep_shape[2] = ngroups;
     c.last_sweep_shape[3] = chunk;
     c.last_sweep_shape[4] = FM == FM_TC ? 1000 : FM == FM_OZ ? 2000 : (RES ? cb : -cb);
+    c.last_cluster = CL ? CLS : 0;
     return e;
 }
 
@@ -2099,23 +2276,47 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
     Gr = std::min(Gr, (N + chunk - 1) / chunk);
     Gf = std::max(Gf, Gr);
     const bool res = chunk <= 256 && 2 * (size_t)K * (chunk + 1) * sizeof(T) <= RES_BUDGET;
+    if constexpr (std::is_same<T, double>::value) {
+        // cluster mode (on request): fp64, a few large walkers with the GPU to
+        // themselves and no fixed group shape; the CLS ratio CTAs of a walker
+        // form one cluster and exchange their partial dot products through
+        // distributed shared memory instead of global memory. The exchange is
+        // faster, but 16 CTAs do the fp64 dot products and the queue update of
+        // 64, and the flush runs on the 112 CTAs that 16-CTA clusters leave
+        // co-resident: at N = 2048, K = 32 a sweep takes 29.5 ms against
+        // 21.8 ms. Any refusal before the launch falls through to the
+        // global-memory exchange below.
+        const int cchunk = ((N + CLS - 1) / CLS + 31) / 32 * 32;
+        const bool cres = cchunk <= 256 && 2 * (size_t)K * (cchunk + 1) * sizeof(T) <= RES_BUDGET;
+        if (c.prec == QMCDU_FP64 && c.opt_cluster == 2 && c.opt_group_ctas == 0 && c.opt_ratio_ctas == 0 &&
+            c.opt_flush_ctas == 0 && !c.opt_stall && N >= 1024 && nw <= 4 && cres) {
+            cudaError_t e = cudaErrorInvalidConfiguration;
+            if (use_oz(c, 2 * CLS)) e = launch_shape<T, true, FM_OZ, true>(c, L, 0, CLS, cchunk);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                e = launch_shape<T, true, FM_SIMT, true>(c, L, 0, CLS, cchunk);
+            }
+            if (e == cudaSuccess) return e;
+            cudaGetLastError();
+        }
+    }
     // tensor-core flush: split-bf16 precision, flush blocks of >= 128 columns, K <= 64
     const int cpc = (N + Gf - 1) / Gf;
     const bool tc = std::is_same<T, float>::value && c.prec == QMCDU_FP32_BF16X3 && !res &&
                     K <= 64 && cpc >= 128;
-    if (tc) return launch_shape<T, false, FM_TC>(c, L, Gf, Gr, chunk);
+    if (tc) return launch_shape<T, false, FM_TC, false>(c, L, Gf, Gr, chunk);
     if constexpr (std::is_same<T, double>::value) {
         // emulated-fp64 flush: fp64 walkers shared by several CTAs, K <= 32;
         // where its shared memory does not fit beside the resident queue rows
         // (launch_shape refuses before launching), the fp64-unit flush
         if (use_oz(c, Gf)) {
-            const cudaError_t e = res ? launch_shape<T, true, FM_OZ>(c, L, Gf, Gr, chunk)
-                                      : launch_shape<T, false, FM_OZ>(c, L, Gf, Gr, chunk);
+            const cudaError_t e = res ? launch_shape<T, true, FM_OZ, false>(c, L, Gf, Gr, chunk)
+                                      : launch_shape<T, false, FM_OZ, false>(c, L, Gf, Gr, chunk);
             if (e != cudaErrorInvalidConfiguration) return e;
         }
     }
-    return res ? launch_shape<T, true, FM_SIMT>(c, L, Gf, Gr, chunk)
-               : launch_shape<T, false, FM_SIMT>(c, L, Gf, Gr, chunk);
+    return res ? launch_shape<T, true, FM_SIMT, false>(c, L, Gf, Gr, chunk)
+               : launch_shape<T, false, FM_SIMT, false>(c, L, Gf, Gr, chunk);
 }
 
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)

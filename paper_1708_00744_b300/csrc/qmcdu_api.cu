@@ -915,6 +915,10 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value)
     case QMCDU_OPT_TEST_STALL: c->opt_stall = value ? 1 : 0; break;
     case QMCDU_OPT_MAX_CTAS: c->opt_max_ctas = (int)std::min(value, 1LL << 20); break;
     case QMCDU_OPT_GROUP_CTAS: c->opt_group_ctas = (int)std::min(value, 1LL << 20); break;
+    case QMCDU_OPT_CLUSTER:
+        if (value < 0 || value > 2) return QMCDU_ERR_ARG;
+        c->opt_cluster = (int)value;
+        break;
     case QMCDU_OPT_FP64_FLUSH:
         if (value < 0 || value > 2) return QMCDU_ERR_ARG;
         c->opt_fp64_flush = (int)value;

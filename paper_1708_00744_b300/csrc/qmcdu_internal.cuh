@@ -98,6 +98,8 @@ struct Ctx {
     int opt_max_ctas = 0;            // cap on the persistent sweep's grid (0: whole GPU)
     int opt_group_ctas = 0;          // fixed CTAs per walker group (0: from the batch)
     int opt_fp64_flush = 0;          // 0: auto, 1: fp64 arithmetic only, 2: emulated on the tensor cores
+    int opt_cluster = 0;             // 0, 1: global-memory exchange; 2: cluster mode where it applies
+    int last_cluster = 0;            // cluster size of the last persistent sweep (0: none)
     // emulated-fp64 flush of the persistent sweep (kernels_sweep.cu): scratch of
     // oz_groups walker groups, oz_stride bytes each
     unsigned char *oz = nullptr;

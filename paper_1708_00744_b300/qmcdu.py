@@ -299,7 +299,8 @@ def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
 
 
 OPTIONS = {"sweep_persistent": 1, "ratio_ctas": 2, "flush_ctas": 3, "wait_budget_ns": 4,
-           "test_stall": 5, "max_ctas": 6, "group_ctas": 7, "fp64_flush": 8}
+           "test_stall": 5, "max_ctas": 6, "group_ctas": 7, "fp64_flush": 8,
+           "cluster": 9}
 
 
 def qmcdu_set_option(h, option, value):
