@@ -444,8 +444,10 @@ def run_ksweep(a):
 def run_kernels(a):
     """Microbenchmarks of single kernels, timed with CUDA events: the batched
     per-call ratio (Eq. 3 through a queue of k = 128 moves; HBM-bound), the
-    split-bf16 x3 tensor-core GEMM, and the fp64 recompute."""
+    per-call fp64 flush (Eq. 4) emulated on the tensor cores and on the fp64
+    units, the split-bf16 x3 tensor-core GEMM, and the fp64 recompute."""
     import torch
+    from paper_1708_00744_b300 import inputs
     from paper_1708_00744_b300.qmcdu import Walkers, qmcdu_gemm_bf16x3
     torch.cuda.set_device(0)
     st = torch.cuda.Stream()
@@ -504,6 +506,46 @@ def run_kernels(a):
                                 "TFLOP_per_s": flops / (ms * 1e-3) / 1e12,
                                 "note": "one qmcdu_ratio call (three kernels) with its host "
                                         "argument copy"}
+    # flush of Eq. 4 through the per-call API: one fp64 walker of N = 2048,
+    # K = 32, with k = 31 accepted moves queued (refilled, untimed, before each
+    # call); the contraction emulated on the tensor cores vs the fp64 units
+    Nf, Kf = 2048, 32
+    A0h = np.asarray(inputs.initial_matrix(inputs.walker_seed(a.seed + 11, 0), Nf))
+    A0 = torch.from_numpy(A0h).cuda()
+    for mode, name in ((2, "flush_fp64_emulated"), (1, "flush_fp64_units")):
+        W = Walkers(Nf, Kf, "fp64", 1, stream=st)
+        W.set_option("fp64_flush", mode)
+        W.set_matrix(A0h[None])
+        r = torch.zeros(1, dtype=torch.float64, device="cuda")
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(a.seed + 1)
+        ms_l = []
+        for rep in range(6):
+            for m in range(Kf - 1):     # K accepts would flush inside the last accept
+                j = m + Kf * rep          # distinct electrons, each row still the initial one
+                with torch.cuda.stream(st):
+                    # a proposal close to the current row keeps the ratio O(1)
+                    v = A0[j:j + 1] + 0.05 * torch.randn(1, Nf, dtype=torch.float64, device="cuda",
+                                                         generator=gen)
+                W.ratio(np.array([j], dtype=np.int32), v, r)
+                W.accept(np.ones(1, dtype=np.uint8))
+            flush_buf.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            W.flush()
+            e1.record(st)
+            e1.synchronize()
+            if rep > 0:
+                ms_l.append(e0.elapsed_time(e1))
+        W.sync()
+        W.close()
+        ms = float(np.median(ms_l))
+        fl = 4.0 * Nf * Nf * (Kf - 1)
+        out[name] = {"N": Nf, "k": Kf - 1, "ms": ms, "fp64_equivalent_TFLOP_per_s": fl / (ms * 1e-3) / 1e12,
+                     "note": "one qmcdu_flush call: W = P Kinv (fp64 GEMM) and the two N x N x k "
+                             "contractions"}
     # split-bf16 x3 GEMM on tcgen05: C = A B', 4096^3
     M = Nn = Kk = 4096
     Ag = torch.randn(M, Kk, device="cuda")

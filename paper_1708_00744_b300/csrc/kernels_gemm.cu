@@ -10,6 +10,8 @@
 //   A^{-1} -= W T          (N x N, inner dimension k)
 // 4 N^2 k flops per flush of k moves (the same 4 N^2 per accepted move as
 // Sherman-Morrison, now as matrix-matrix products).
+#include <type_traits>
+
 #include "qmcdu_internal.cuh"
 
 namespace qmcdu {
@@ -126,6 +128,31 @@ static cudaError_t launch_flush_t(Ctx &c, int kthresh)
     T *Ainv = (T *)c.Ainv;
     T *Tb = (T *)c.Tbuf;
     T *Wb = (T *)c.Wbuf;
+    // W = P Kinv:  W(m, i) = sum_q Kinv[q][m] P[q][i]   (stored W[m][i])
+    {
+        GemmArgs<double, T, T> g{};
+        g.A = c.Kinv; g.sAb = (long long)K * K; g.sAm = 1; g.sAl = K;
+        g.B = (const T *)c.P; g.sBb = wK; g.sBl = ld; g.sBn = 1;
+        g.C = Wb; g.sCb = wK; g.sCm = ld; g.sCn = 1;
+        g.M = K; g.Nn = N; g.Kd = K;
+        g.kdyn = c.kcount; g.dyn = 3; g.kthresh = kthresh;
+        g.alpha = 1.0; g.accumulate = 0;
+        dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
+        gemm_tile_kernel<double, T, T, T, 32, 32, false, true><<<grid, GTHREADS, 0, c.stream>>>(g);
+    }
+    if (std::is_same<T, double>::value) {
+        // fp64 walkers, K <= 32: the two N x N x k contractions on the tensor
+        // cores (emulated fp64, kernels_sweep.cu)
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_flush_oz(c, kthresh);
+        if (e == cudaSuccess) {
+            flush_reset_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.kcount, kthresh);
+            return cudaGetLastError();
+        }
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
     // T = V' A^{-1} - E':  T(m, n) = sum_i V[m][i] A^{-1}[i][n] - [n == idx_m]
     {
         GemmArgs<T, T, T> g{};
@@ -138,18 +165,6 @@ static cudaError_t launch_flush_t(Ctx &c, int kthresh)
         g.fix_idx = c.idx; g.fix_stride = K;
         dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
         gemm_tile_kernel<T, T, T, T, 32, 32, true, false><<<grid, GTHREADS, 0, c.stream>>>(g);
-    }
-    // W = P Kinv:  W(m, i) = sum_q Kinv[q][m] P[q][i]   (stored W[m][i])
-    {
-        GemmArgs<double, T, T> g{};
-        g.A = c.Kinv; g.sAb = (long long)K * K; g.sAm = 1; g.sAl = K;
-        g.B = (const T *)c.P; g.sBb = wK; g.sBl = ld; g.sBn = 1;
-        g.C = Wb; g.sCb = wK; g.sCm = ld; g.sCn = 1;
-        g.M = K; g.Nn = N; g.Kd = K;
-        g.kdyn = c.kcount; g.dyn = 3; g.kthresh = kthresh;
-        g.alpha = 1.0; g.accumulate = 0;
-        dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
-        gemm_tile_kernel<double, T, T, T, 32, 32, false, true><<<grid, GTHREADS, 0, c.stream>>>(g);
     }
     // A^{-1} -= W T:  stored Ainv[c][i] (column c) -= sum_m T[m][c] W[m][i]
     {

@@ -2319,6 +2319,99 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
                : launch_shape<T, false, FM_SIMT, false>(c, L, Gf, Gr, chunk);
 }
 
+// ---------------------------------------------------------------- per-call flush
+// qmcdu_flush of fp64 walkers (K <= 32): the two N x N x k contractions of
+// Eq. 4 emulated on the tensor cores by flush_oz, one walker at a time per
+// group of CTAs, for the walkers whose queue holds at least kthresh moves.
+// W = P Kinv is already in c.Wbuf. The exponents that the persistent sweep
+// keeps up to date are computed here: columns of A^{-1}, rows of V.
+__global__ void __launch_bounds__(STHREADS, 1) oz_flush_kernel(SweepParams<double> p, const int *kcount,
+                                                              int kthresh)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_s;
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tcf::su32(&tmem_s)), "n"(ozf::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
+        for (int q = 0; q < ozf::NBAR; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+        const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
+        unsigned *flush_ctr = p.sync + SYNC_STRIDE * grp + 32;
+        unsigned n_flush = 0, tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int w = grp; w < p.batch; w += p.ngroups) {
+            const int k = __ldcg(kcount + w);
+            if (k < kthresh || k < 1) continue;           // uniform for the group
+            oz_colexp_init(p, w, grp, rank);
+            if (rank == 0) {
+                // exponents of V's rows (warp m: row m)
+                int *vex = oz_vex(p, grp);
+                const double *Vb = p.V + (size_t)w * p.K * p.ld;
+                for (int m = warp; m < 64; m += SWARPS) {
+                    unsigned e = 0;
+                    if (m < k)
+                        for (int i = lane; i < p.N; i += 32) e = max(e, (unsigned)ozf::bexp(__ldcg(Vb + (size_t)m * p.ld + i)));
+                    e = __reduce_max_sync(0xffffffffu, e);
+                    if (lane == 0) vex[m] = (int)e;
+                }
+            }
+            if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
+            if (!flush_oz(p, w, k, grp, rank, smem, tmem_s, tph, flush_ctr, n_flush)) break;
+            if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_s), "n"(ozf::TMEM_COLS) : "memory");
+}
+
+// cudaErrorNotSupported when the emulated flush does not apply (the caller
+// then takes the fp64 GEMMs).
+cudaError_t launch_flush_oz(Ctx &c, int kthresh)
+{
+    const int K = c.K;
+    if (c.prec != QMCDU_FP64 || K > 32 || K < SMALL_K || !c.oz || c.oz_groups < 1 || c.opt_fp64_flush == 1)
+        return cudaErrorNotSupported;
+    const int kp = (K + 15) / 16 * 16;
+    const size_t smem = std::max((size_t)OZ_MIN_SMEM, ozf::region_bytes(kp));
+    cudaError_t e = cudaFuncSetAttribute(oz_flush_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_flush_kernel, STHREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorNotSupported;     // the TMEM allocation would wait
+    const int ngroups = std::min(c.batch, c.oz_groups);
+    const int Gf = c.num_sms / ngroups;
+    if (Gf < 2 || ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorNotSupported;
+    SweepParams<double> p{};
+    p.N = c.N; p.K = K; p.ld = c.ld; p.batch = c.batch;
+    p.Gf = Gf; p.Gr = 1; p.ngroups = ngroups;
+    p.Ainv = (double *)c.Ainv; p.W = (double *)c.Wbuf; p.V = (double *)c.V;
+    p.idx = c.idx; p.kglob = c.kcount;
+    p.sync = c.sw_sync; p.status = c.status;
+    p.budget_ns = c.opt_budget_ns;
+    p.kp = kp; p.oz = c.oz; p.oz_stride = c.oz_stride;
+    p.off_xs = 0;
+    p.off_tcbar = (int)ozf::bar_offset(kp);
+    p.phase_ns = nullptr;
+    e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&p, &c.kcount, &kthresh};
+    return cudaLaunchCooperativeKernel((const void *)oz_flush_kernel, dim3(ngroups * Gf), dim3(STHREADS), args,
+                                       smem, c.stream);
+}
+
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L)
 {
     // the sweep's proposal draws, then the sweep, then the running log-det

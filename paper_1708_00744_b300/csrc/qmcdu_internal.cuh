@@ -149,6 +149,9 @@ struct SweepLaunch {
 cudaError_t launch_sweep(Ctx &c, const SweepLaunch &L);
 // Scratch bytes of one walker group of the emulated-fp64 flush (0: not used for N, K).
 size_t oz_group_bytes(int N, int K);
+// qmcdu_flush of fp64 walkers on the tensor cores (W = P Kinv in c.Wbuf); cudaErrorNotSupported
+// where it does not apply.
+cudaError_t launch_flush_oz(Ctx &c, int kthresh);
 cudaError_t prof_begin(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
 cudaError_t prof_end(Ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v);
 
