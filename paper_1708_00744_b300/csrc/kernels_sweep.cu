@@ -198,6 +198,30 @@ __device__ bool cl_wait_flags(const unsigned *flag, unsigned target, int n, int 
     return __syncthreads_and(ok) != 0;
 }
 
+__device__ __forceinline__ float2 cl_ld_f2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+// ---- double-fp32 pairs (hi + lo): the ratio CTAs each sum all Gr x (2k + 1)
+// partial dot products of a proposal. B300's fp64 pipe retires two lanes per
+// clock per SM (a warp-wide fp64 add costs 16 cycles), so those sums run on
+// the fp32 pipe as error-free two-sums (Knuth's TwoSum) on (hi, lo) pairs:
+// about 48 bits, far below the path's other errors.
+__device__ __forceinline__ float2 df_split(double x)
+{
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_allsum(T v)
 {
@@ -1608,8 +1632,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     T *coef = (T *)(smem + p.off_ts);                  // accept: [0,K) c_m, [K,2K) y_m/r, [2K,..) z
     T *Wsm = (T *)(smem + p.off_wsm);                  // RES: [K][LP]
     T *Vsm = (T *)(smem + p.off_vsm);                  // RES: [K][LP]
-    __shared__ double u_s[2];
-    __shared__ int vx_s[2];
+    __shared__ double rinv_s, u_s[2];
+    __shared__ int acc_s, vx_s[2];
     const int chunk = p.chunk, LP = chunk + 1;
     const int i0 = rank * chunk;
     const int L = max(0, min(chunk, N - i0));
@@ -1685,6 +1709,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             // (cluster mode: into this CTA's shared memory, for the siblings to read)
             double *clp = (double *)(smem + p.off_cl);
             unsigned *clflag = (unsigned *)(clp + 2 * nj);
+            // (partials as double-fp32 pairs)
             double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
             if (RES) {
                 // G consecutive lanes per job (a power of two up to 8 that the
@@ -1708,7 +1733,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     double s = (double)acc0 + (double)acc1;
                     const unsigned act = __activemask();
                     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(act, s, o, G);
-                    if (g == 0) part[job] = s;
+                    if (g == 0) reinterpret_cast<float2 *>(part)[job] = df_split(s);
                 }
             } else {
                 // queue rows in global memory: four jobs per warp at a time, so that
@@ -1733,7 +1758,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const T v = warp_allsum(acc[q]);
-                        if (lane == 0 && j0 + q < nj_k) part[j0 + q] = (double)v;
+                        if (lane == 0 && j0 + q < nj_k) reinterpret_cast<float2 *>(part)[j0 + q] = df_split((double)v);
                     }
                 }
             }
@@ -1776,65 +1801,76 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 while (G < 8 && 2 * G * njk <= STHREADS) G *= 2;
                 for (int t = threadIdx.x; t < njk * G; t += STHREADS) {
                     const int job = t / G, g = t - job * G;
-                    double s = 0.0;
+                    // the partials as double-fp32 pairs, summed with two-sums
+                    float2 s = make_float2(0.f, 0.f);
                     int q = g;
+                    const float2 *pb2 = reinterpret_cast<const float2 *>(pb);
                     if (CL) {
                         // sibling q's partials in its shared memory, same order
                         const double *mine = clp + b * nj + job;
                         for (; q + 7 * G < Gr; q += 8 * G) {
-                            double x[8];
+                            float2 x[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) x[e] = cl_ld_f64(cl_map(mine, q + e * G));
+                            for (int e = 0; e < 8; ++e) x[e] = cl_ld_f2(cl_map(mine, q + e * G));
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) s += x[e];
+                            for (int e = 0; e < 8; ++e) s = df_add(s, x[e]);
                         }
-                        for (; q < Gr; q += G) s += cl_ld_f64(cl_map(mine, q));
+                        for (; q < Gr; q += G) s = df_add(s, cl_ld_f2(cl_map(mine, q)));
                     } else {
                         for (; q + 7 * G < Gr; q += 8 * G) {
-                            double x[8];
+                            float2 x[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb + (size_t)(q + e * G) * nj + job);
+                            for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb2 + (size_t)(q + e * G) * nj + job);
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) s += x[e];
+                            for (int e = 0; e < 8; ++e) s = df_add(s, x[e]);
                         }
-                        for (; q < Gr; q += G) s += __ldcg(pb + (size_t)q * nj + job);
+                        for (; q < Gr; q += G) s = df_add(s, __ldcg(pb2 + (size_t)q * nj + job));
                     }
                     // groups are whole (njk * G is a multiple of G), so the active
                     // lanes of the warp hold complete groups
                     const unsigned act = __activemask();
-                    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(act, s, o, G);
-                    if (g == 0) red[job] = s;
+                    for (int o = G / 2; o > 0; o >>= 1) {
+                        float2 t2;
+                        t2.x = __shfl_down_sync(act, s.x, o, G);
+                        t2.y = __shfl_down_sync(act, s.y, o, G);
+                        s = df_add(s, t2);
+                    }
+                    if (g == 0) red[job] = (double)s.x + (double)s.y;
                 }
             }
             __syncthreads();
-            // ---- the ratio and the Metropolis decision, computed by every warp
-            // alike from the reduced dots (the same values in the same order),
-            // so that no broadcast is needed
-            double r;
-            int a;
-            {
+            // ---- the ratio and the Metropolis decision in warp 0 (fp64 work on
+            // one warp only: the fp64 pipe retires two lanes per clock), then a
+            // broadcast through shared memory
+            if (warp == 0) {
                 double s = 0.0;
                 for (int m = lane; m < k; m += 32) s += red[1 + m] * red[1 + k + m];
                 s = warp_allsum(s);
-                r = red[0] - s;
-                const double u = u_s[b];
-                const double prob = fmin(1.0, r * r);
-                const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
-                a = ov == 0 ? 0 : (ov == 1 ? 1 : (u < prob ? 1 : 0));
-                const bool bad = a && !(r != 0.0 && isfinite(r));
-                if (bad) a = 0;
-                if (rank == 0 && threadIdx.x == 0) {
-                    if (bad) atomicOr(p.status, ST_SINGULAR);
-                    p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
-                    p.ratio_out[(size_t)orow * N + j] = r;
-                    if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
-                    if (a) p.idx[(size_t)w * K + k] = j;
+                if (lane == 0) {
+                    const double r = red[0] - s;
+                    const double u = u_s[b];
+                    const double prob = fmin(1.0, r * r);
+                    const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
+                    int a = ov == 0 ? 0 : (ov == 1 ? 1 : (u < prob ? 1 : 0));
+                    const bool bad = a && !(r != 0.0 && isfinite(r));
+                    if (bad) a = 0;
+                    rinv_s = a ? 1.0 / r : 0.0;      // once, not in every thread
+                    acc_s = a;
+                    if (rank == 0) {
+                        if (bad) atomicOr(p.status, ST_SINGULAR);
+                        p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
+                        p.ratio_out[(size_t)orow * N + j] = r;
+                        if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
+                        if (a) p.idx[(size_t)w * K + k] = j;
+                    }
                 }
             }
+            __syncthreads();
+            const int a = acc_s;
             tick(3);
             if (a) {
                 // ---- accept: z = a - W c, W <- [W - z y'/r, z/r], V[k] = v, A[j] = v
-                const double rinv = 1.0 / r;
+                const double rinv = rinv_s;
                 T *cT = coef, *yT = coef + K, *zs = coef + 2 * K;
                 for (int m = threadIdx.x; m < k; m += STHREADS) {
                     cT[m] = (T)red[1 + k + m];
@@ -1844,8 +1880,9 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 double *arow_w = Aw + (size_t)j * ld;
                 if (RES) {
                     // z = a - W c: ZG consecutive lanes per row, lane g taking
-                    // m = g, g + ZG, ..., then a fixed shuffle tree
-                    constexpr int ZG = 8;
+                    // m = g, g + ZG, ..., then a fixed shuffle tree (fp64: two
+                    // lanes, since every tree step costs a warp-wide fp64 add)
+                    constexpr int ZG = sizeof(T) == 8 ? 2 : 8;
                     for (int t0 = threadIdx.x; t0 < ((L + 31) / 32) * 32 * ZG; t0 += STHREADS) {
                         const int t = t0 / ZG, g = t0 - t * ZG;
                         T z0 = 0, z1 = 0;
