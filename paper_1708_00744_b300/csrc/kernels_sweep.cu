@@ -918,8 +918,11 @@ __host__ __device__ inline Layout layout(int N, int kp)
 // shared memory: phase A's NSLOT raw fp64 K-blocks (A^{-1} columns, then V
 // rows) and two stages of their slices; phase C reuses it for one W tile, two
 // T tiles and two blocks of column exponents; then eight mbarriers (0, 1:
-// phase A stages; 2: phase C MMAs; 3: W tile; 4, 5: T tiles)
+// phase A stages free again; 2: phase C MMAs; 3: W tile; 4, 5: T tiles; 6, 7:
+// phase A stages full)
 constexpr int NBAR = 8;
+// arrivals per phase: 6, 7 are phase A's stage-full barriers (one per warp)
+__host__ __device__ inline unsigned bar_count(int q) { return q >= 6 ? 8u : 1u; }
 __host__ __device__ inline size_t raw_bytes(int kp) { return (size_t)(AM + kp) * AK * sizeof(double); }
 __host__ __device__ inline size_t phase_a_bytes(int kp)
 {
@@ -1119,94 +1122,116 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
             const int ncol = min(AM, N - c0);
             if (tid < AM) ecol[tid] = tid < ncol ? __ldcg(cex + c0 + tid) : 0;
             if (tid < 32) erow[tid] = tid < k ? __ldcg(vex + tid) : 0;
-            // raw block kb -> slot kb % NSLOT: 16-byte asynchronous copies by all
-            // threads (zero-filled outside the walker's columns, rows and queue),
-            // one commit group per block
+            // A pipeline without CTA barriers. Thread t copies, with 16-byte
+            // asynchronous copies NSLOT - 1 blocks ahead, exactly the raw data it
+            // cuts (rows 8 (t & 1) .. + 7 of column t >> 1 of A^{-1}, and of V
+            // row t >> 1 for t < 2 kp), so its own wait_group suffices; each warp
+            // announces its slices of stage s on bars[6 + s] (8 arrivals), thread
+            // 0 issues the stage's MMAs and commits them to bars[s], which every
+            // thread waits on before it cuts into stage s again. A wait that
+            // runs out of budget marks the thread bad; it keeps walking the loop
+            // without work and the CTA leaves together after it.
+            const int ca = tid >> 1, kk = (tid & 1) * 8;
+            const bool hasv = tid < 2 * kp;
             auto issue = [&](int kb) {
                 if (kb < nkb) {
                     const int i = r0 + kb * AK;
                     double *dst = raw + (size_t)(kb % NSLOT) * (AM + kp) * AK;
-                    for (int u = tid; u < (AM + kp) * (AK / 2); u += STHREADS) {
-                        const int row = u / (AK / 2), part = u - row * (AK / 2);
-                        const bool in = i < ld && (row < AM ? row < ncol : row - AM < k);
-                        const double *s = row < AM ? Ab + (size_t)(c0 + row) * ld + i + 2 * part
-                                                   : Vb + (size_t)(row - AM) * ld + i + 2 * part;
+                    const bool ina = i < ld && ca < ncol;
+                    const double *srca = Ab + (size_t)(c0 + (ina ? ca : 0)) * ld + (ina ? i + kk : 0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                     ::"r"(su32(dst + (size_t)row * AK + 2 * part)), "l"(in ? s : (const double *)Ab),
-                                       "r"(in ? 16 : 0) : "memory");
+                                     ::"r"(su32(dst + (size_t)ca * AK + kk + 2 * q)), "l"(ina ? srca + 2 * q : srca),
+                                       "r"(ina ? 16 : 0) : "memory");
+                    if (hasv) {
+                        const bool inv = i < ld && ca < k;
+                        const double *srcv = inv ? Vb + (size_t)ca * ld + i + kk : Vb;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                         ::"r"(su32(dst + (size_t)(AM + ca) * AK + kk + 2 * q)),
+                                           "l"(inv ? srcv + 2 * q : srcv), "r"(inv ? 16 : 0) : "memory");
                     }
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
             };
             issue(0);
             issue(1);
-            int pend[2] = {0, 0};
+            __syncthreads();                       // ecol, erow
+            bool bad = false;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb & 1, sl = kb % NSLOT;
-                issue(kb + 2);    // its slot was sliced in iteration kb - 1 (an empty group past the end)
-                if (pend[s]) {
-                    if (!wait_bar(s)) return false;    // (a CTA barrier: also publishes ecol, erow)
-                    pend[s] = 0;
+                issue(kb + 2);    // this thread's own slot, cut in iteration kb - 1
+                if (kb >= 2) {    // the MMAs of block kb - 2 have read stage s
+                    if (!bad) bad = !mbar_wait(&bars[s], tph[s], p.status, p.budget_ns);
+                    tph[s] ^= 1u;
                 }
                 asm volatile("cp.async.wait_group 2;" ::: "memory");
-                __syncthreads();
                 const int i = r0 + kb * AK;
                 const double *rw = raw + (size_t)sl * (AM + kp) * AK;
-                {
-                    // A^{-1}: thread t cuts rows 8 (t & 1) .. + 7 of column t >> 1
-                    const int c = tid >> 1, kk = (tid & 1) * 8;
-                    double x[8];
-                    const bool in = c < ncol && i < ld;
+                if (!bad) {
+                    {
+                        double x[8];
+                        const bool in = ca < ncol && i < ld;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double2 u = in ? *reinterpret_cast<const double2 *>(rw + c * AK + kk + 2 * q)
-                                             : make_double2(0.0, 0.0);
-                        x[2 * q] = u.x;
-                        x[2 * q + 1] = u.y;
+                        for (int q = 0; q < 4; ++q) {
+                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + ca * AK + kk + 2 * q)
+                                                 : make_double2(0.0, 0.0);
+                            x[2 * q] = u.x;
+                            x[2 * q + 1] = u.y;
+                        }
+                        uint4 out[NS];
+                        slice8(x, ecol[ca], out);
+                        const uint32_t o = coff(ca, kk, AK) >> 1;
+#pragma unroll
+                        for (int j = 0; j < NS; ++j)
+                            *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = out[j];
                     }
-                    uint4 out[NS];
-                    slice8(x, ecol[c], out);
-                    const uint32_t o = coff(c, kk, AK) >> 1;
+                    if (hasv) {
+                        double x[8];
+                        const bool in = ca < k && i < ld;
 #pragma unroll
-                    for (int j = 0; j < NS; ++j)
-                        *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = out[j];
-                }
-                if (tid < 2 * kp) {
-                    const int m = tid >> 1, kk = (tid & 1) * 8;
-                    double x[8];
-                    const bool in = m < k && i < ld;
+                        for (int q = 0; q < 4; ++q) {
+                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + ca) * AK + kk + 2 * q)
+                                                 : make_double2(0.0, 0.0);
+                            x[2 * q] = u.x;
+                            x[2 * q + 1] = u.y;
+                        }
+                        uint4 out[NS];
+                        slice8(x, erow[ca], out);
+                        const uint32_t o = coff(ca, kk, AK) >> 1;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + m) * AK + kk + 2 * q)
-                                             : make_double2(0.0, 0.0);
-                        x[2 * q] = u.x;
-                        x[2 * q + 1] = u.y;
+                        for (int j = 0; j < NS; ++j)
+                            *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = out[j];
                     }
-                    uint4 out[NS];
-                    slice8(x, erow[m], out);
-                    const uint32_t o = coff(m, kk, AK) >> 1;
-#pragma unroll
-                    for (int j = 0; j < NS; ++j)
-                        *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = out[j];
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars[6 + s]);
                 if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (!bad) bad = !mbar_wait(&bars[6 + s], tph[6 + s], p.status, p.budget_ns);
+                    tph[6 + s] ^= 1u;
+                    if (!bad) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                    for (int q = 0; q < NMMA_A; ++q) {
-                        const MmaA mm = kMmaA[q];
-                        const uint64_t ad = sdesc(su32(sa + (s * NS + mm.j) * aplane), 128, sboA);
-                        const uint64_t bd = sdesc(su32(sb + (s * NS + mm.l) * bplane), 128, sboA);
-                        const bool first = kb == 0 && mm.fresh;
-                        mma(tmem + (uint32_t)(mm.blk * kp), ad, bd, idesc_f16(AM, mm.nl * kp), first ? 0u : 1u);
+                        for (int q = 0; q < NMMA_A; ++q) {
+                            const MmaA mm = kMmaA[q];
+                            const uint64_t ad = sdesc(su32(sa + (s * NS + mm.j) * aplane), 128, sboA);
+                            const uint64_t bd = sdesc(su32(sb + (s * NS + mm.l) * bplane), 128, sboA);
+                            const bool first = kb == 0 && mm.fresh;
+                            mma(tmem + (uint32_t)(mm.blk * kp), ad, bd, idesc_f16(AM, mm.nl * kp), first ? 0u : 1u);
+                        }
+                        commit(&bars[s]);
                     }
-                    commit(&bars[s]);
                 }
-                pend[s] = 1;
             }
-            for (int s = 0; s < 2; ++s)
-                if (pend[s] && !wait_bar(s)) return false;
+            for (int kb = nkb - 2; kb < nkb; ++kb) {     // the last two blocks' MMAs
+                const int s = kb & 1;
+                if (!bad) bad = !mbar_wait(&bars[s], tph[s], p.status, p.budget_ns);
+                tph[s] ^= 1u;
+            }
+            if (__syncthreads_or(bad)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // readout: lanes = columns c, 16 values of m per warp; the d <= 3
             // diagonals as one exact int64, d = 4..6 as an fp32 tail in units
@@ -2030,7 +2055,8 @@ __global__ void __launch_bounds__(STHREADS, FM == FM_SIMT ? 2 : 1) sweep_kernel(
         if (TC) {
             unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
             for (int q = 0; q < (FM == FM_OZ ? ozf::NBAR : 4); ++q)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                             ::"r"(tcf::su32(&bars[q])), "r"(FM == FM_OZ ? ozf::bar_count(q) : 1u) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
@@ -2375,7 +2401,8 @@ __global__ void __launch_bounds__(STHREADS, 1) oz_flush_kernel(SweepParams<doubl
     if (threadIdx.x == 0) {
         unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
         for (int q = 0; q < ozf::NBAR; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcf::su32(&bars[q])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                         ::"r"(tcf::su32(&bars[q])), "r"(ozf::bar_count(q)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
