@@ -97,14 +97,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 
 
 
-// Arrival on a group counter (after all of this CTA's prior writes).
+// Arrival on a group counter (after all of this CTA's prior writes): the CTA
+// barrier orders every thread's writes before thread 0's release-add, whose
+// release semantics (cumulative) publish them at gpu scope.
 __device__ __forceinline__ void group_arrive(unsigned *ctr)
 {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-    }
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
 }
 
 // Wait until a group counter reaches `target`. Returns false, uniformly for
@@ -132,7 +132,7 @@ __device__ bool group_wait_for(unsigned *ctr, unsigned target, int *status, long
                 }
             }
         }
-        __threadfence();
+        // (the acquire load orders the CTA's later reads, through the barrier below)
         ok_s = ok;
     }
     __syncthreads();
