@@ -1889,6 +1889,33 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         if (a) p.idx[(size_t)w * K + k] = j;
                     }
                 }
+            } else if (RES) {
+                // meanwhile warps 1.. compute the accept's z = a - W c (it needs
+                // only the reduced dots), discarded if the move is rejected: ZG
+                // consecutive lanes per row, lane g taking m = g, g + ZG, ..., then
+                // a fixed shuffle tree (fp64: two lanes, since every tree step costs
+                // a warp-wide fp64 add)
+                constexpr int ZG = sizeof(T) == 8 ? 2 : 8;
+                T *zs = coef + 2 * K;
+                const int nzt = ((L + 31) / 32) * 32 * ZG;      // whole warps
+                for (int t0 = threadIdx.x - 32; t0 < nzt; t0 += STHREADS - 32) {
+                    const int t = t0 / ZG, g = t0 - t * ZG;
+                    T z0 = 0, z1 = 0;
+                    if (t < L) {
+                        const double *cr = red + 1 + k;
+                        int m = g;
+#pragma unroll 2
+                        for (; m + ZG < k; m += 2 * ZG) {
+                            z0 += (T)cr[m] * Wsm[m * LP + t];
+                            z1 += (T)cr[m + ZG] * Wsm[(m + ZG) * LP + t];
+                        }
+                        if (m < k) z0 += (T)cr[m] * Wsm[m * LP + t];
+                    }
+                    T z = z0 + z1;
+#pragma unroll
+                    for (int o = ZG / 2; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o, ZG);
+                    if (g == 0 && t < L) zs[t] = asb[t] - z;
+                }
             }
             __syncthreads();
             const int a = acc_s;
@@ -1901,35 +1928,12 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     cT[m] = (T)red[1 + k + m];
                     yT[m] = (T)(red[1 + m] * rinv);
                 }
-                if (!RES) __syncthreads();
                 double *arow_w = Aw + (size_t)j * ld;
                 if (RES) {
-                    // z = a - W c: ZG consecutive lanes per row, lane g taking
-                    // m = g, g + ZG, ..., then a fixed shuffle tree (fp64: two
-                    // lanes, since every tree step costs a warp-wide fp64 add)
-                    constexpr int ZG = sizeof(T) == 8 ? 2 : 8;
-                    for (int t0 = threadIdx.x; t0 < ((L + 31) / 32) * 32 * ZG; t0 += STHREADS) {
-                        const int t = t0 / ZG, g = t0 - t * ZG;
-                        T z0 = 0, z1 = 0;
-                        if (t < L) {
-                            // c_m straight from the reduction (cT is written in this same step)
-                            const double *cr = red + 1 + k;
-                            int m = g;
-#pragma unroll 2
-                            for (; m + ZG < k; m += 2 * ZG) {
-                                z0 += (T)cr[m] * Wsm[m * LP + t];
-                                z1 += (T)cr[m + ZG] * Wsm[(m + ZG) * LP + t];
-                            }
-                            if (m < k) z0 += (T)cr[m] * Wsm[m * LP + t];
-                        }
-                        T z = z0 + z1;
-#pragma unroll
-                        for (int o = ZG / 2; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o, ZG);
-                        if (g == 0 && t < L) {
-                            zs[t] = asb[t] - z;
-                            Vsm[k * LP + t] = vsb[t];
-                            arow_w[i0 + t] = vdb[t];
-                        }
+                    // (z is in zs already)
+                    for (int t = threadIdx.x; t < L; t += STHREADS) {
+                        Vsm[k * LP + t] = vsb[t];
+                        arow_w[i0 + t] = vdb[t];
                     }
                     __syncthreads();
                     const T rT = (T)rinv;
@@ -1939,6 +1943,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         else Wsm[k * LP + t] = zs[t] * rT;
                     }
                 } else {
+                    __syncthreads();
                     // queue rows in global memory: four rows per thread, m outermost,
                     // so that loads of different (m, row) are independent
                     const T rT = (T)rinv;
