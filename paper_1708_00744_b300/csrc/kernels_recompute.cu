@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
                                                             double *R, double *lu_logabs,
                                                             int *lu_sign, int *status)
 {
-    extern __shared__ double S[];          // N x nb, row i at S + i*nb
+    extern __shared__ double S[];          // N x nb, column q at S + q*N (the elimination's
+                                           // threads, one row each, hit consecutive banks)
     __shared__ double wval[32];
     __shared__ int widx[32];
     __shared__ double prow[16];
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < N * nbe; e += blockDim.x) {
         const int i = e / nbe, q = e - i * nbe;
-        S[i * nb + q] = X[(size_t)i * ld + c0 + q];
+        S[q * N + i] = X[(size_t)i * ld + c0 + q];
     }
     if (tid == 0) singular = 0;
     __syncthreads();
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
         double best = -1.0;
         int bi = N;
         for (int i = c + tid; i < N; i += blockDim.x) {
-            const double v = fabs(S[i * nb + q]);
+            const double v = fabs(S[q * N + i]);
             if (v > best) { best = v; bi = i; }
         }
 #pragma unroll
@@ -124,9 +125,9 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
         const int p = pivot_row;
         if (p != c) {
             for (int t = tid; t < nbe; t += blockDim.x) {
-                const double s = S[c * nb + t];
-                S[c * nb + t] = S[p * nb + t];
-                S[p * nb + t] = s;
+                const double s = S[t * N + c];
+                S[t * N + c] = S[t * N + p];
+                S[t * N + p] = s;
             }
             for (int x = tid; x < N; x += blockDim.x) {
                 if (x >= c0 && x < c0 + nbe) continue;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
             sg = -sg;
         }
         __syncthreads();
-        const double pv = S[c * nb + q];
+        const double pv = S[q * N + c];
         if (pv == 0.0) {
             if (tid == 0) singular = 1;
             __syncthreads();
@@ -145,16 +146,15 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
         }
         if (tid == 0) la += log(fabs(pv));   // one thread: fp64 log is costly on this part
         if (pv < 0.0) sg = -sg;
-        if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : S[c * nb + tid] / pv;
+        if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : S[tid * N + c] / pv;
         __syncthreads();
         for (int i = tid; i < N; i += blockDim.x) {
-            double *row = S + i * nb;
             if (i == c) {
-                for (int t = 0; t < nbe; ++t) row[t] = prow[t];
+                for (int t = 0; t < nbe; ++t) S[t * N + i] = prow[t];
             } else {
-                const double f = row[q];
-                row[q] = 0.0;
-                for (int t = 0; t < nbe; ++t) row[t] -= f * prow[t];
+                const double f = S[q * N + i];
+                S[q * N + i] = 0.0;
+                for (int t = 0; t < nbe; ++t) S[t * N + i] -= f * prow[t];
             }
         }
         __syncthreads();
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
     double *Rb = R + (size_t)b * nb * ld;
     for (int e = tid; e < N * nbe; e += blockDim.x) {
         const int i = e / nbe, q = e - i * nbe;
-        const double v = S[i * nb + q];
+        const double v = S[q * N + i];
         X[(size_t)i * ld + c0 + q] = v;
         Ltb[(size_t)q * ld + i] = v - (i == c0 + q ? 1.0 : 0.0);
     }
