@@ -11,10 +11,14 @@
 //     permutation of it; X^{-1} = A^{-T} stored row-major is A^{-1} stored
 //     column-major.
 // Blocking: for a panel of nb columns, one CTA per walker eliminates the panel
-// (all N rows, panel staged in shared memory), then every other column gets
-// the panel's transformation as one rank-nb update, X += (Mp - E) X_p, with
-// Mp the eliminated panel and X_p the panel's pivot rows. 2 N^3 flops in all.
+// (all N rows, panel staged in shared memory) -- or, for a few walkers, P CTAs
+// per walker split the rows (gj_panel_mc_kernel, kernels_sweep.cu) -- then every
+// other column gets the panel's transformation as one rank-nb update,
+// X += (Mp - E) X_p, with Mp the eliminated panel and X_p the panel's pivot
+// rows. 2 N^3 flops in all.
 #include <math.h>
+
+#include <algorithm>
 
 #include "qmcdu_internal.cuh"
 #include "philox.cuh"
@@ -31,6 +35,30 @@ int choose_panel_width(int N)
     int nb = 16;
     while (nb > 1 && (size_t)N * nb * sizeof(double) > budget) nb >>= 1;
     return nb;
+}
+
+void configure_recompute(Ctx &c)
+{
+    // a few walkers: each walker's panels over P CTAs (rows split), 32 columns
+    // wide; otherwise, and for handles whose grid is shared out (a serving
+    // pool sets a group shape), one CTA per walker with the panel in its
+    // shared memory (nb1 columns, inside the same Lt / R rows)
+    c.nb1 = choose_panel_width(c.N);
+    if (c.batch <= 4 && c.N >= 256) {
+        c.gj_ctas = std::min(64, std::max(8, c.num_sms / c.batch));
+        c.nb = 32;
+    } else {
+        c.gj_ctas = 0;
+        c.nb = c.nb1;
+    }
+}
+
+// The multi-CTA panels for this launch: configured, and the handle owns the
+// GPU (no group shape, no grid cap: a cooperative panel grid beside other
+// persistent kernels could not be guaranteed co-resident).
+static bool use_gj_mc(const Ctx &c)
+{
+    return c.gj_ctas > 0 && c.opt_group_ctas == 0 && c.opt_max_ctas == 0;
 }
 
 // work[b][i][x] = A[b][x][i]  (X = A'); padding stays zero.
@@ -277,19 +305,26 @@ cudaError_t launch_recompute(Ctx &c, int have_old)
         transpose_kernel<<<grid, dim3(32, 8), 0, c.stream>>>(N, ld, c.A, c.work);
     }
     lu_init_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.lu_logabs, c.lu_sign, c.drift);
-    const size_t smem = (size_t)N * c.nb * sizeof(double);
+    const bool mc = use_gj_mc(c);
+    const int pw = mc ? c.nb : c.nb1;                       // panel width of this launch
+    const size_t smem = (size_t)N * c.nb1 * sizeof(double);
     {
         cudaError_t e = cudaFuncSetAttribute(gj_panel_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
     }
-    for (int c0 = 0; c0 < N; c0 += c.nb) {
-        const int nbe = N - c0 < c.nb ? N - c0 : c.nb;
-        gj_panel_kernel<<<c.batch, PTHREADS, smem, c.stream>>>(N, ld, c.nb, c0, nbe, c.work, c.piv,
-                                                              c.Lt, c.R, c.lu_logabs, c.lu_sign,
-                                                              c.status);
-        cudaError_t e = cudaGetLastError();
+    for (int c0 = 0; c0 < N; c0 += pw) {
+        const int nbe = N - c0 < pw ? N - c0 : pw;
+        cudaError_t e;
+        if (mc) {
+            e = launch_gj_panel_mc(c, c0, nbe);
+        } else {
+            gj_panel_kernel<<<c.batch, PTHREADS, smem, c.stream>>>(N, ld, c.nb, c0, nbe, c.work, c.piv,
+                                                                  c.Lt, c.R, c.lu_logabs, c.lu_sign,
+                                                                  c.status);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return e;
         e = launch_gj_update(c, nbe);
         if (e != cudaSuccess) return e;

@@ -2387,6 +2387,211 @@ static cudaError_t launch_sweep_t(Ctx &c, const SweepLaunch &L)
                : launch_shape<T, false, FM_SIMT, false>(c, L, Gf, Gr, chunk);
 }
 
+// ---------------------------------------------------------------- recompute panel
+// Gauss-Jordan elimination of one panel (columns [c0, c0 + nbe)) of the
+// transposed copy X of walker b, over P CTAs that split the rows: the
+// multi-CTA form of gj_panel_kernel (kernels_recompute.cu) for a few walkers,
+// where one CTA per walker would leave the GPU idle and the panel need not fit
+// one SM's shared memory. Per pivot column, one group barrier: every CTA
+// publishes its best candidate (largest |x| among its rows >= c, first index
+// on ties), that row's panel values, and the owner of row c publishes row c;
+// after the barrier all CTAs take the same winner (largest, then lowest
+// index: partial pivoting as in LU), the owner of the winner's row takes row
+// c's old values, the rows c and p of X outside the panel are swapped in
+// column shares, and every CTA eliminates its own rows. Candidate buffers
+// alternate between two parities, so one barrier per column suffices.
+struct GjScratch { double *candv; int *candi; double *candrow; double *rowc; };
+__host__ __device__ inline size_t gj_scratch_bytes(int P, int nb)
+{
+    return (size_t)2 * P * sizeof(double) + (size_t)2 * P * sizeof(int) + (size_t)2 * P * nb * sizeof(double) +
+           (size_t)2 * nb * sizeof(double) + 64;
+}
+__device__ inline GjScratch gj_scratch(unsigned char *base, int P, int nb)
+{
+    GjScratch s;
+    s.candv = (double *)base;
+    s.candrow = s.candv + 2 * P;
+    s.rowc = s.candrow + (size_t)2 * P * nb;
+    s.candi = (int *)(s.rowc + 2 * nb);
+    return s;
+}
+
+constexpr int GJ_THREADS = 256;
+constexpr int GJ_CTR_STRIDE = 32;     // one 128-byte line per walker
+
+__global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, int nb, int c0, int nbe, int P,
+                                                                double *work, int *piv, double *Lt, double *R,
+                                                                double *lu_logabs, int *lu_sign, int *status,
+                                                                unsigned *gj_ctr, unsigned char *scratch,
+                                                                size_t scratch_stride, long long budget_ns)
+{
+    extern __shared__ double S[];              // [nb][Rr]: column q of the CTA's rows at S + q*Rr
+    __shared__ double wval[GJ_THREADS / 32], prow[64];
+    __shared__ int widx[GJ_THREADS / 32], win_s, wr_s;
+    const int b = blockIdx.x / P, r = blockIdx.x - b * P;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Rr = (N + P - 1) / P;
+    const int i0 = min(N, r * Rr), nr = min(Rr, N - i0);
+    double *X = work + (size_t)b * N * ld;
+    unsigned *ctr = gj_ctr + GJ_CTR_STRIDE * b;     // this walker's own barrier counter
+    unsigned nbar = 0;
+    GjScratch g = gj_scratch(scratch + (size_t)b * scratch_stride, P, nb);
+    // the CTA's column share of X for row interchanges and R
+    const int xs = (N + P - 1) / P, x0 = min(N, r * xs), x1 = min(N, x0 + xs);
+
+    for (int e = tid; e < nr * nbe; e += GJ_THREADS) {
+        const int li = e / nbe, q = e - li * nbe;
+        S[q * Rr + li] = X[(size_t)(i0 + li) * ld + c0 + q];
+    }
+    __syncthreads();
+    double la = 0.0;
+    int sg = 1, singular = 0;
+    for (int q = 0; q < nbe; ++q) {
+        const int c = c0 + q, par = q & 1;
+        // my candidate
+        double best = -1.0;
+        int bi = N;
+        for (int li = tid; li < nr; li += GJ_THREADS) {
+            const int gi = i0 + li;
+            if (gi < c) continue;
+            const double v = fabs(S[q * Rr + li]);
+            if (v > best || (v == best && gi < bi)) { best = v; bi = gi; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < GJ_THREADS / 32 ? wval[lane] : -1.0;
+            bi = lane < GJ_THREADS / 32 ? widx[lane] : N;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) {
+                g.candv[par * P + r] = best;
+                g.candi[par * P + r] = bi;
+                win_s = bi;
+            }
+        }
+        __syncthreads();
+        const int mine = win_s;
+        if (mine < N)
+            for (int t = tid; t < nbe; t += GJ_THREADS) g.candrow[((size_t)par * P + r) * nb + t] = S[t * Rr + (mine - i0)];
+        if (c >= i0 && c < i0 + nr)
+            for (int t = tid; t < nbe; t += GJ_THREADS) g.rowc[par * nb + t] = S[t * Rr + (c - i0)];
+        if (!group_barrier(ctr, (++nbar) * P, status, budget_ns)) return;
+        // the winner: largest candidate, lowest row on ties, in a fixed order
+        if (warp == 0) {
+            double bv = -1.0;
+            int bidx = N, brk = 0;
+            for (int k = lane; k < P; k += 32) {
+                const double v = __ldcg(g.candv + par * P + k);
+                const int i = __ldcg(g.candi + par * P + k);
+                if (v > bv || (v == bv && i < bidx)) { bv = v; bidx = i; brk = k; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+                const int ok_ = __shfl_xor_sync(0xffffffffu, brk, o);
+                if (ov > bv || (ov == bv && oi < bidx)) { bv = ov; bidx = oi; brk = ok_; }
+            }
+            if (lane == 0) {
+                win_s = bidx < N ? bidx : c;
+                wr_s = bidx < N ? brk : -1;
+            }
+        }
+        __syncthreads();
+        const int p = win_s, rp = wr_s;
+        const double pv = rp >= 0 ? __ldcg(g.candrow + ((size_t)par * P + rp) * nb + q) : 0.0;
+        if (r == 0 && tid == 0) piv[(size_t)b * N + c] = p;
+        if (p != c) sg = -sg;
+        if (pv == 0.0) {
+            singular = 1;
+            continue;
+        }
+        if (r == 0 && tid == 0) la += log(fabs(pv));     // one thread: fp64 log is costly here
+        if (pv < 0.0) sg = -sg;
+        if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : __ldcg(g.candrow + ((size_t)par * P + rp) * nb + tid) / pv;
+        // the owner of row p takes row c's old panel values; rows c and p of X
+        // outside the panel are interchanged in column shares
+        if (p != c) {
+            if (p >= i0 && p < i0 + nr)
+                for (int t = tid; t < nbe; t += GJ_THREADS) S[t * Rr + (p - i0)] = __ldcg(g.rowc + par * nb + t);
+            for (int x = x0 + tid; x < x1; x += GJ_THREADS) {
+                if (x >= c0 && x < c0 + nbe) continue;
+                const double s = X[(size_t)c * ld + x];
+                X[(size_t)c * ld + x] = X[(size_t)p * ld + x];
+                X[(size_t)p * ld + x] = s;
+            }
+        }
+        __syncthreads();
+        for (int li = tid; li < nr; li += GJ_THREADS) {
+            const int gi = i0 + li;
+            if (gi == c) {
+                for (int t = 0; t < nbe; ++t) S[t * Rr + li] = prow[t];
+            } else {
+                const double f = S[q * Rr + li];
+                S[q * Rr + li] = 0.0;
+                for (int t = 0; t < nbe; ++t) S[t * Rr + li] -= f * prow[t];
+            }
+        }
+        __syncthreads();
+    }
+    // every CTA's interchanges of X are done before the pivot rows are read
+    if (!group_barrier(ctr, (++nbar) * P, status, budget_ns)) return;
+    double *Ltb = Lt + (size_t)b * nb * ld;
+    double *Rb = R + (size_t)b * nb * ld;
+    for (int e = tid; e < nr * nbe; e += GJ_THREADS) {
+        const int li = e / nbe, q = e - li * nbe, gi = i0 + li;
+        const double v = S[q * Rr + li];
+        X[(size_t)gi * ld + c0 + q] = v;
+        Ltb[(size_t)q * ld + gi] = v - (gi == c0 + q ? 1.0 : 0.0);
+    }
+    for (int q = 0; q < nbe; ++q)
+        for (int x = x0 + tid; x < x1; x += GJ_THREADS)
+            Rb[(size_t)q * ld + x] = (x >= c0 && x < c0 + nbe) ? 0.0 : X[(size_t)(c0 + q) * ld + x];
+    if (r == 0 && tid == 0) {
+        if (singular) {
+            atomicOr(status, ST_SINGULAR);
+            lu_logabs[b] = -INFINITY;
+            lu_sign[b] = 0;
+        } else if (lu_sign[b] != 0) {
+            lu_logabs[b] += la;
+            lu_sign[b] *= sg;
+        }
+    }
+}
+
+size_t gj_mc_scratch_bytes(int P, int nb) { return (gj_scratch_bytes(P, nb) + 255) / 256 * 256; }
+
+cudaError_t launch_gj_panel_mc(Ctx &c, int c0, int nbe)
+{
+    const int P = c.gj_ctas, N = c.N;
+    const int Rr = (N + P - 1) / P;
+    const size_t smem = (size_t)c.nb * Rr * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(gj_panel_mc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // its own counters: a serving pool recomputes admitted walkers on one
+    // stream while its sweep runs on another
+    e = cudaMemsetAsync(c.gj_ctr, 0, (size_t)c.batch * GJ_CTR_STRIDE * sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return e;
+    int n = N, ld = c.ld, nb = c.nb, cc0 = c0, nn = nbe, PP = P;
+    size_t stride = gj_mc_scratch_bytes(P, c.nb);
+    long long budget = c.opt_budget_ns;
+    void *args[] = {&n, &ld, &nb, &cc0, &nn, &PP, &c.work, &c.piv, &c.Lt, &c.R, &c.lu_logabs, &c.lu_sign,
+                    &c.status, &c.gj_ctr, &c.gj_scr, &stride, &budget};
+    return cudaLaunchCooperativeKernel((const void *)gj_panel_mc_kernel, dim3(c.batch * P), dim3(GJ_THREADS), args,
+                                       smem, c.stream);
+}
+
 // ---------------------------------------------------------------- per-call flush
 // qmcdu_flush of fp64 walkers (K <= 32): the two N x N x k contractions of
 // Eq. 4 emulated on the tensor cores by flush_oz, one walker at a time per

@@ -100,6 +100,10 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
     AL(c->lu_logabs, B * sizeof(double));
     AL(c->lu_sign, B * sizeof(int));
     AL(c->drift, B * 4 * sizeof(double));
+    if (c->gj_ctas > 0) {
+        AL(c->gj_scr, B * gj_mc_scratch_bytes(c->gj_ctas, c->nb));
+        AL(c->gj_ctr, B * 32 * sizeof(unsigned));
+    }
     AL(c->sw_acc, B * N);
     AL(c->sw_ratio, B * N * sizeof(double));
     AL(c->sw_ties, B * sizeof(long long));
@@ -140,7 +144,7 @@ static void release(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
-                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz};
+                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz, c->gj_scr, c->gj_ctr};
     for (void *p : more)
         if (p) cudaFree(p);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -336,7 +340,7 @@ int qmcdu_create(int N, int K, int precision, int batch, void *stream, qmcdu_t *
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         c->num_sms = 148;
     c->nsplit = (N + 255) / 256;
-    c->nb = choose_panel_width(N);
+    configure_recompute(*c);
     size_t total = 0;
     cudaError_t e = alloc_state(c, true, &total);
     // the zeroing is complete when create returns: any stream may use the handle
@@ -938,7 +942,7 @@ int qmcdu_footprint(int N, int K, int precision, int batch, unsigned long long *
     Ctx c;
     c.N = N; c.K = K; c.prec = precision; c.batch = batch; c.ld = padded_ld(N);
     c.nsplit = (N + 255) / 256;
-    c.nb = choose_panel_width(N);
+    configure_recompute(c);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
@@ -959,6 +963,11 @@ static void range_view(const Ctx &c, int w0, int n, Ctx &v)
     v.N = c.N; v.K = c.K; v.prec = c.prec; v.batch = n; v.ld = c.ld;
     v.stream = c.stream; v.device = c.device; v.num_sms = c.num_sms;
     v.nb = c.nb; v.nsplit = c.nsplit; v.status = c.status;
+    v.gj_ctas = c.gj_ctas;
+    v.gj_scr = c.gj_scr ? c.gj_scr + w * gj_mc_scratch_bytes(c.gj_ctas, c.nb) : nullptr;
+    v.gj_ctr = c.gj_ctr ? c.gj_ctr + w * 32 : nullptr;
+    v.opt_budget_ns = c.opt_budget_ns; v.nb1 = c.nb1;
+    v.opt_group_ctas = c.opt_group_ctas; v.opt_max_ctas = c.opt_max_ctas;
     v.A = c.A + w * wN;
     v.Ainv = (char *)c.Ainv + w * wN * elem_size(c.prec);
     v.work = c.work + w * wN;

@@ -73,7 +73,11 @@ struct Ctx {
     std::vector<int> h_elec;
     bool pending = false;
     int nsplit = 1;
-    int nb = 16;
+    int nb = 16;                     // recompute: Lt / R rows per walker, the multi-CTA panel width
+    int nb1 = 16;                    // recompute: the one-CTA panel width (<= nb)
+    int gj_ctas = 0;                 // > 0: each walker's recompute panels over this many CTAs
+    unsigned char *gj_scr = nullptr; // their pivot-candidate buffers (batch x gj_mc_scratch_bytes)
+    unsigned *gj_ctr = nullptr;      // their barrier counters (batch x 32 words)
     std::string err;
     // profiling (qmcdu_profile_*)
     bool prof = false;
@@ -193,6 +197,11 @@ cudaError_t launch_flush(Ctx &c, int kthresh);
 // ---- recompute (kernels_recompute.cu) ----
 cudaError_t launch_recompute(Ctx &c, int have_old_inverse);
 cudaError_t launch_init_matrix(Ctx &c, int w0, int n, const unsigned long long *seeds);
+// Recompute panels over several CTAs per walker (kernels_sweep.cu).
+cudaError_t launch_gj_panel_mc(Ctx &c, int c0, int nbe);
+size_t gj_mc_scratch_bytes(int P, int nb);
+// Recompute shape of a handle: the panel width and, for a few walkers, the CTAs per walker.
+void configure_recompute(Ctx &c);
 cudaError_t launch_gj_update(Ctx &c, int nbe);
 int choose_panel_width(int N);
 
