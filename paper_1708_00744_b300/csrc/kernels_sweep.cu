@@ -3,7 +3,8 @@
 //
 // Each walker is served by a group of Gf CTAs. The first Gr of them (the ratio
 // CTAs) each own a chunk of rows of the N-vectors and advance the proposals in
-// lock step, one group barrier per proposal; all Gf CTAs (ratio CTAs and
+// lock step, exchanging tagged partial dot products (polled in global memory,
+// no counter barrier) once per proposal; all Gf CTAs (ratio CTAs and
 // helpers) apply the flush of Eq. 4, each to its own block of columns of
 // A^{-1}. Groups never wait on one another.
 //
@@ -65,7 +66,7 @@ struct SweepParams {
     int *idx, *kglob;
     const double *gauss;    // [batch][N][ld] proposal Gaussians of this sweep
     const double *unif;     // [batch][N] Metropolis uniforms of this sweep
-    double *partial;        // [ngroups][2][Gr][2K+1]
+    double *partial;        // [ngroups][2][Gr][2K+1] tagged (hi, lo) words
     unsigned *sync;         // [ngroups][SYNC_STRIDE]: ratio barrier, flush barrier, flush command,
                             // each on its own 128-byte line
     int *status;
@@ -220,6 +221,48 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b)
     const float bb = __fsub_rn(s, a.x);
     const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
     return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
+}
+
+// ---- tagged partials: a (hi, lo) pair travels as one 64-bit word, the two
+// lowest bits of lo replaced by the proposal's tag (1 + p mod 3, p the
+// group's count of proposals in this launch; 0 after the clearing memset that
+// precedes every launch). One single-copy-atomic 64-bit store publishes the
+// value and its readiness together, so the readers poll the data itself: no
+// CTA barrier, release fence or counter round trip per proposal. A proposal
+// reads the slots of its 2k + 1 dot products in one of two buffers (by the
+// parity of j); k grows by at most one per proposal, so besides its own slots
+// every proposal tags the next four (zero values) in its buffer: then every
+// slot that a proposal reads was last written two proposals before it (or,
+// across a walker boundary, one or two proposals before, behind the flush
+// barriers), and three tags tell the current value from every stale one.
+// The two bits cost under 4 ulp of lo (about 2^-45 of the value).
+__device__ __forceinline__ void st_tagged(double *dst, float2 v, unsigned tag)
+{
+    const unsigned lo = (__float_as_uint(v.y) & ~3u) | tag;
+    const unsigned long long w = ((unsigned long long)lo << 32) | __float_as_uint(v.x);
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(dst), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_tagged(const double *src)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(src));
+    return w;
+}
+__device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32) & 3u; }
+__device__ __forceinline__ float2 untag(unsigned long long w)
+{
+    return make_float2(__uint_as_float((unsigned)w), __uint_as_float((unsigned)(w >> 32) & ~3u));
+}
+
+// Lanes of this warp that take part in a loop iteration over t < n, where t
+// runs lane by lane (t = base + lane, base a multiple of 32). The shuffles
+// after a loop name these lanes explicitly: lanes that left a data-dependent
+// loop (the polls of tagged partials) at different times need not have
+// reconverged, so __activemask() could miss some of them.
+__device__ __forceinline__ unsigned lanes_below(int t, int n)
+{
+    const int rem = n - (t - (int)(threadIdx.x & 31));
+    return rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : (1u << rem) - 1u);
 }
 
 template <typename T>
@@ -1608,7 +1651,6 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     unsigned tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // phases of the tensor-core flush's mbarriers
     const int N = p.N, K = p.K, ld = p.ld, Gf = p.Gf, Gr = p.Gr;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
-    unsigned *ratio_ctr = p.sync + SYNC_STRIDE * grp + 0;
     unsigned *flush_ctr = p.sync + SYNC_STRIDE * grp + 32;
     unsigned *cmd = p.sync + SYNC_STRIDE * grp + 64;
     unsigned n_ratio = 0, n_flush = 0, n_event = 0, bar_phase = 0;
@@ -1715,7 +1757,6 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             const T *vsb = vs + b * chunk, *asb = as + b * chunk;
             const double *vdb = vd + b * chunk;
             __syncthreads();
-            if (FM == FM_OZ && threadIdx.x == 0) vx_s[b ^ 1] = 0;   // staged below (after a barrier)
             // ---- the next proposal's inputs (row j + 1 of A and its Gaussians,
             // column j + 1 of A^{-1}, u): loaded now, so that their latency
             // overlaps the dot products, and staged after the arrival below
@@ -1736,6 +1777,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             unsigned *clflag = (unsigned *)(clp + 2 * nj);
             // (partials as double-fp32 pairs)
             double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
+            const unsigned tag = 1u + n_ratio % 3u;
             if (RES) {
                 // G consecutive lanes per job (a power of two up to 8 that the
                 // CTA's threads allow), lane g taking elements g, g + G, ...,
@@ -1756,9 +1798,12 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     }
                     if (t < L) acc0 += src[t] * with[t];
                     double s = (double)acc0 + (double)acc1;
-                    const unsigned act = __activemask();
+                    const unsigned act = lanes_below(t0, njk * G);
                     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(act, s, o, G);
-                    if (g == 0) reinterpret_cast<float2 *>(part)[job] = df_split(s);
+                    if (g == 0) {
+                        if (CL) reinterpret_cast<float2 *>(part)[job] = df_split(s);
+                        else st_tagged(part + job, df_split(s), tag);
+                    }
                 }
             } else {
                 // queue rows in global memory: four jobs per warp at a time, so that
@@ -1783,18 +1828,21 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const T v = warp_allsum(acc[q]);
-                        if (lane == 0 && j0 + q < nj_k) reinterpret_cast<float2 *>(part)[j0 + q] = df_split((double)v);
+                        if (lane == 0 && j0 + q < nj_k) {
+                            if (CL) reinterpret_cast<float2 *>(part)[j0 + q] = df_split((double)v);
+                            else st_tagged(part + j0 + q, df_split((double)v), tag);
+                        }
                     }
                 }
             }
+            if (!CL && threadIdx.x < 4 && 2 * k + 1 + (int)threadIdx.x < nj)
+                st_tagged(part + 2 * k + 1 + threadIdx.x, make_float2(0.f, 0.f), tag);
             tick(0);
-            // ---- arrive, stage the next proposal (its column speculatively), wait
-            const unsigned extra = (p.stall && n_ratio == 0) ? 1u : 0u;
+            // ---- (cluster mode: arrive), stage the next proposal (its column
+            // speculatively), wait
             if (CL) {
                 __syncthreads();                       // every partial written
                 if (threadIdx.x == 0) cl_st_release(clflag, n_ratio + 1);
-            } else {
-                group_arrive(ratio_ctr);
             }
             if (pf) {
                 if (threadIdx.x < L) {
@@ -1809,17 +1857,18 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 stage(j + 1, b ^ 1, true, true);
             }
             tick(1);
-            if (CL) {
-                if (!cl_wait_flags(clflag, ++n_ratio, Gr, p.status, p.budget_ns)) return;
-            } else if (!group_wait_for(ratio_ctr, (++n_ratio) * Gr + extra, p.status, p.budget_ns)) {
-                return;
-            }
+            if (CL && !cl_wait_flags(clflag, n_ratio + 1, Gr, p.status, p.budget_ns)) return;
             tick(2);
             // ---- every ratio CTA sums the partials in the same order: G
             // consecutive lanes per job (a power of two up to 8 that the CTA's
             // threads allow), lane g of the group summing the partials of CTAs
-            // g, g + G, ..., then a fixed shuffle tree over the group
+            // g, g + G, ..., then a fixed shuffle tree over the group. Outside
+            // cluster mode the loads poll the tagged words until every one
+            // carries this proposal's tag (the stall option asks for a tag that
+            // never comes, to exercise the timeout).
             const double *pb = p.partial + ((size_t)grp * 2 + b) * Gr * nj;
+            const unsigned want = (p.stall && n_ratio == 0) ? 4u : tag;
+            int late = 0;
             {
                 const int njk = 2 * k + 1;
                 int G = 1;
@@ -1829,7 +1878,6 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     // the partials as double-fp32 pairs, summed with two-sums
                     float2 s = make_float2(0.f, 0.f);
                     int q = g;
-                    const float2 *pb2 = reinterpret_cast<const float2 *>(pb);
                     if (CL) {
                         // sibling q's partials in its shared memory, same order
                         const double *mine = clp + b * nj + job;
@@ -1842,18 +1890,39 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         }
                         for (; q < Gr; q += G) s = df_add(s, cl_ld_f2(cl_map(mine, q)));
                     } else {
-                        for (; q + 7 * G < Gr; q += 8 * G) {
-                            float2 x[8];
+                        const double *pbj = pb + job;
+                        unsigned long long deadline = 0;
+                        const size_t stp = (size_t)G * nj;
+                        for (; q < Gr; q += 8 * G) {
+                            const int cnt = min(8, (Gr - q + G - 1) / G);
+                            const double *pq = pbj + (size_t)q * nj;
+                            unsigned long long x[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) x[e] = __ldcg(pb2 + (size_t)(q + e * G) * nj + job);
+                            for (int e = 0; e < 8; ++e)
+                                if (e < cnt) x[e] = ld_tagged(pq + e * stp);
+                            for (unsigned spins = 1;; ++spins) {
+                                unsigned stale = 0;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) s = df_add(s, x[e]);
+                                for (int e = 0; e < 8; ++e)
+                                    if (e < cnt && tag_of(x[e]) != want) stale |= 1u << e;
+                                if (!stale || late) break;
+                                if ((spins & 15u) == 0) {
+                                    const unsigned long long now = globaltimer();
+                                    if (!deadline) deadline = now + (unsigned long long)p.budget_ns;
+                                    else if (now > deadline || (*(volatile const int *)p.status & ST_TIMEOUT)) late = 1;
+                                }
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    if ((stale >> e) & 1u) x[e] = ld_tagged(pq + e * stp);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                if (e < cnt) s = df_add(s, untag(x[e]));
                         }
-                        for (; q < Gr; q += G) s = df_add(s, __ldcg(pb2 + (size_t)q * nj + job));
                     }
-                    // groups are whole (njk * G is a multiple of G), so the active
-                    // lanes of the warp hold complete groups
-                    const unsigned act = __activemask();
+                    // groups are whole (njk * G is a multiple of G), so the lanes
+                    // of the iteration hold complete groups
+                    const unsigned act = lanes_below(t, njk * G);
                     for (int o = G / 2; o > 0; o >>= 1) {
                         float2 t2;
                         t2.x = __shfl_down_sync(act, s.x, o, G);
@@ -1863,7 +1932,11 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     if (g == 0) red[job] = (double)s.x + (double)s.y;
                 }
             }
-            __syncthreads();
+            ++n_ratio;
+            if (__syncthreads_or(late)) {
+                if (threadIdx.x == 0) atomicOr(p.status, ST_TIMEOUT);
+                return;
+            }
             // ---- the ratio and the Metropolis decision in warp 0 (fp64 work on
             // one warp only: the fp64 pipe retires two lanes per clock), then a
             // broadcast through shared memory
@@ -1989,6 +2062,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 if (FM == FM_OZ && threadIdx.x == 0) atomicMax(oz_vex(p, grp) + k, vx_s[b]);
                 ++k;
             }
+            // (vx_s[b] is staged again in the next proposal, after its first barrier)
+            if (FM == FM_OZ && threadIdx.x == 0) vx_s[b] = 0;
             tick(4);
             const bool last = (j == N - 1);
             if (k < K && !last) continue;
@@ -2283,6 +2358,12 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.off_cl = offs[10];
     e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
     if (e != cudaSuccess) return e;
+    if (!CL) {
+        // tag 0 in every partial slot: no word left by an earlier launch can
+        // carry the tag that a proposal of this one waits for
+        e = cudaMemsetAsync(c.sw_partial, 0, (size_t)ngroups * 2 * Gr * (2 * K + 1) * sizeof(double), c.stream);
+        if (e != cudaSuccess) return e;
+    }
     if (CL) {
         cfg.gridDim = dim3(ngroups * Gf);
         cfg.numAttrs = 2;
