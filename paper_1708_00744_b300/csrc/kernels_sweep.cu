@@ -1003,18 +1003,20 @@ __device__ __forceinline__ void mag56(double x, int emax, uint32_t &qhi, uint32_
     neg = (uint32_t)(b >> 63);
 }
 // slice j (0 = most significant byte) of two magnitudes as a packed pair of
-// fp16: the bytes are placed under the exponent of 1024 (1024 + b is exact in
-// fp16 for b < 1024) and 1024 is subtracted from both halves at once
+// fp16: the bytes are placed under the exponent of +-1024 (the pair's signs
+// already in `base` = 0x6400 per half with the sign bits set; 1024 + b is
+// exact in fp16 for b < 1024), and +-1024 is subtracted from both halves at
+// once, which leaves +-b
 __device__ __forceinline__ uint32_t slice_pair(uint32_t qh0, uint32_t ql0, uint32_t qh1, uint32_t ql1,
-                                               int j, uint32_t sgn)
+                                               int j, uint32_t base)
 {
     const bool hi = j < 3;
     const uint32_t a = hi ? qh0 : ql0, b = hi ? qh1 : ql1;
     const uint32_t idx = hi ? (uint32_t)(2 - j) : (uint32_t)(6 - j);      // byte index in the word
-    const uint32_t w = (__byte_perm(a, b, idx | ((4u + idx) << 8)) & 0x00FF00FFu) | 0x64006400u;
+    const uint32_t w = (__byte_perm(a, b, idx | ((4u + idx) << 8)) & 0x00FF00FFu) | base;
     __half2 h = *reinterpret_cast<const __half2 *>(&w);
-    h = __hsub2(h, __half2half2(__ushort_as_half((unsigned short)0x6400u)));
-    return *reinterpret_cast<const uint32_t *>(&h) ^ sgn;
+    h = __hsub2(h, *reinterpret_cast<const __half2 *>(&base));
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 // eight values with one exponent: plane j of the slices as eight packed fp16
 __device__ __forceinline__ void slice8(const double (&x)[8], int emax, uint4 (&out)[NS])
@@ -1024,7 +1026,7 @@ __device__ __forceinline__ void slice8(const double (&x)[8], int emax, uint4 (&o
     for (int e = 0; e < 8; ++e) mag56(x[e], emax, qh[e], ql[e], ng[e]);
     uint32_t sg[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sg[q] = (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
+    for (int q = 0; q < 4; ++q) sg[q] = 0x64006400u | (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
         uint32_t w[4];
@@ -1168,14 +1170,16 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
             // A pipeline without CTA barriers. Thread t copies, with 16-byte
             // asynchronous copies NSLOT - 1 blocks ahead, exactly the raw data it
             // cuts (rows 8 (t & 1) .. + 7 of column t >> 1 of A^{-1}, and of V
-            // row t >> 1 for t < 2 kp), so its own wait_group suffices; each warp
+            // row (t - 64) >> 1 for 64 <= t < 64 + 2 kp: warps 2 and 3, which
+            // share no scheduler with warp 0, whose thread 0 also issues the
+            // MMAs), so its own wait_group suffices; each warp
             // announces its slices of stage s on bars[6 + s] (8 arrivals), thread
             // 0 issues the stage's MMAs and commits them to bars[s], which every
             // thread waits on before it cuts into stage s again. A wait that
             // runs out of budget marks the thread bad; it keeps walking the loop
             // without work and the CTA leaves together after it.
-            const int ca = tid >> 1, kk = (tid & 1) * 8;
-            const bool hasv = tid < 2 * kp;
+            const int ca = tid >> 1, kk = (tid & 1) * 8, cv = (tid - 64) >> 1;
+            const bool hasv = tid >= 64 && tid < 64 + 2 * kp;
             auto issue = [&](int kb) {
                 if (kb < nkb) {
                     const int i = r0 + kb * AK;
@@ -1188,12 +1192,12 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                                      ::"r"(su32(dst + (size_t)ca * AK + kk + 2 * q)), "l"(ina ? srca + 2 * q : srca),
                                        "r"(ina ? 16 : 0) : "memory");
                     if (hasv) {
-                        const bool inv = i < ld && ca < k;
-                        const double *srcv = inv ? Vb + (size_t)ca * ld + i + kk : Vb;
+                        const bool inv = i < ld && cv < k;
+                        const double *srcv = inv ? Vb + (size_t)cv * ld + i + kk : Vb;
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                         ::"r"(su32(dst + (size_t)(AM + ca) * AK + kk + 2 * q)),
+                                         ::"r"(su32(dst + (size_t)(AM + cv) * AK + kk + 2 * q)),
                                            "l"(inv ? srcv + 2 * q : srcv), "r"(inv ? 16 : 0) : "memory");
                     }
                 }
@@ -1233,17 +1237,17 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                     }
                     if (hasv) {
                         double x[8];
-                        const bool in = ca < k && i < ld;
+                        const bool in = cv < k && i < ld;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + ca) * AK + kk + 2 * q)
+                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + cv) * AK + kk + 2 * q)
                                                  : make_double2(0.0, 0.0);
                             x[2 * q] = u.x;
                             x[2 * q + 1] = u.y;
                         }
                         uint4 out[NS];
-                        slice8(x, erow[ca], out);
-                        const uint32_t o = coff(ca, kk, AK) >> 1;
+                        slice8(x, erow[cv], out);
+                        const uint32_t o = coff(cv, kk, AK) >> 1;
 #pragma unroll
                         for (int j = 0; j < NS; ++j)
                             *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = out[j];
