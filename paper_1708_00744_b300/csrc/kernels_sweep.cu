@@ -363,6 +363,14 @@ __device__ void flush_columns_small(const SweepParams<T> &p, int w, int k, int c
     else if (k == 2) flush_columns_small_k<T, 2>(p, w, c_begin, c_end);
     else flush_columns_small_k<T, 3>(p, w, c_begin, c_end);
 }
+// The same, out of line: the emulated-fp64 sweep calls it only for a queue
+// shorter than SMALL_K (end of a sweep), and inlined there its registers would
+// press on the proposal chain's, which already fills 255
+template <typename T>
+__device__ __noinline__ void flush_columns_small_ool(const SweepParams<T> &p, int w, int k, int c_begin, int c_end)
+{
+    flush_columns_small(p, w, k, c_begin, c_end);
+}
 
 // Flush of walker w on a wide column block [c_begin, c_end) (fp64, K <= 64): a
 // register-tiled GEMM in two phases per tile of BT = 64 columns, so that the
@@ -1618,8 +1626,9 @@ __device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, i
     return true;
 }
 
+// (out of line for the same reason as flush_columns_small_ool)
 template <typename T>
-__device__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int rank,
+__device__ __noinline__ bool flush_oz(const SweepParams<T> &p, int w, int k, int grp, int rank,
                          unsigned char *smem, uint32_t tmem, unsigned *tph, unsigned *flush_ctr,
                          unsigned &n_flush)
 {
@@ -1677,7 +1686,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     if (k >= SMALL_K) {
                         if (!flush_oz(p, w, k, grp, rank, smem, tmem, tph, flush_ctr, n_flush)) return;
                     } else if (k > 0) {
-                        flush_columns_small(p, w, k, fc0, fc1);
+                        flush_columns_small_ool(p, w, k, fc0, fc1);
                     }
                 } else if (FM == FM_TC) {
                     if (k > 0 && !flush_tc(p, w, k, fc0, fc1, smem, tmem, tph)) return;
@@ -2092,7 +2101,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 if (k >= SMALL_K) {
                     if (!flush_oz(p, w, k, grp, rank, smem, tmem, tph, flush_ctr, n_flush)) return;
                 } else if (k > 0) {
-                    flush_columns_small(p, w, k, fc0, fc1);
+                    flush_columns_small_ool(p, w, k, fc0, fc1);
                     if (rank == 0 && threadIdx.x < 64) oz_vex(p, grp)[threadIdx.x] = 0;
                 }
             } else if (FM == FM_TC) {
