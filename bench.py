@@ -52,8 +52,8 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 # from one ncu capture; keyed by the sha256 of kernels_sweep.cu at capture time
 # and the workload (a stale key gives null).
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush:
-#   102.8 MB read + 83.6 MB written (the working set stays in L2).
-NCU_TRAFFIC = {"dadaf0fb68490082:single": 102.774784e6 + 83.583488e6}
+#   101.1 MB read + 88.1 MB written (the working set stays in L2).
+NCU_TRAFFIC = {"a458043c9ab1b176:single": 101.069056e6 + 88.081152e6}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],
