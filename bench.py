@@ -52,7 +52,9 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 # from one ncu capture; keyed by the sha256 of kernels_sweep.cu at capture time
 # and the workload (a stale key gives null).
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush:
-#   101.1 MB read + 88.1 MB written (the working set stays in L2).
+#   101.1 MB read + 88.1 MB written (the working set stays in L2). Taken on the
+#   revision before the partial buffers were indexed by the proposal count, so
+#   the current source reports null until the counters are taken again.
 NCU_TRAFFIC = {"a458043c9ab1b176:single": 101.069056e6 + 88.081152e6}
 
 WORKLOADS = {

@@ -228,14 +228,14 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b)
 // group's count of proposals in this launch; 0 after the clearing memset that
 // precedes every launch). One single-copy-atomic 64-bit store publishes the
 // value and its readiness together, so the readers poll the data itself: no
-// CTA barrier, release fence or counter round trip per proposal. A proposal
-// reads the slots of its 2k + 1 dot products in one of two buffers (by the
-// parity of j); k grows by at most one per proposal, so besides its own slots
-// every proposal tags the next four (zero values) in its buffer: then every
-// slot that a proposal reads was last written two proposals before it (or,
-// across a walker boundary, one or two proposals before, behind the flush
-// barriers), and three tags tell the current value from every stale one.
-// The two bits cost under 4 ulp of lo (about 2^-45 of the value).
+// CTA barrier, release fence or counter round trip per proposal. Proposal p
+// reads the slots of its 2k + 1 dot products in buffer p & 1 (by the launch's
+// proposal count, not the walker's electron index: walkers of odd N follow
+// one another in a launch); k grows by at most one per proposal, so besides
+// its own slots every proposal tags the next four (zero values) in its
+// buffer: then every slot that proposal p reads was last written by p - 2,
+// and three tags tell the current value from every stale one. The two bits
+// cost under 4 ulp of lo (about 2^-45 of the value).
 __device__ __forceinline__ void st_tagged(double *dst, float2 v, unsigned tag)
 {
     const unsigned lo = (__float_as_uint(v.y) & ~3u) | tag;
@@ -1789,8 +1789,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             double *clp = (double *)(smem + p.off_cl);
             unsigned *clflag = (unsigned *)(clp + 2 * nj);
             // (partials as double-fp32 pairs)
-            double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + b) * Gr + rank) * nj;
-            const unsigned tag = 1u + n_ratio % 3u;
+            const unsigned pbuf = n_ratio & 1u, tag = 1u + n_ratio % 3u;
+            double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + pbuf) * Gr + rank) * nj;
             if (RES) {
                 // G consecutive lanes per job (a power of two up to 8 that the
                 // CTA's threads allow), lane g taking elements g, g + G, ...,
@@ -1879,7 +1879,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             // cluster mode the loads poll the tagged words until every one
             // carries this proposal's tag (the stall option asks for a tag that
             // never comes, to exercise the timeout).
-            const double *pb = p.partial + ((size_t)grp * 2 + b) * Gr * nj;
+            const double *pb = p.partial + ((size_t)grp * 2 + pbuf) * Gr * nj;
             const unsigned want = (p.stall && n_ratio == 0) ? 4u : tag;
             int late = 0;
             {
