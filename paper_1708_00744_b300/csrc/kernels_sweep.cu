@@ -1772,7 +1772,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             __syncthreads();
             // ---- the next proposal's inputs (row j + 1 of A and its Gaussians,
             // column j + 1 of A^{-1}, u): loaded now, so that their latency
-            // overlaps the dot products, and staged after the arrival below
+            // overlaps the dot products, and staged after them
             const bool pf = L <= STHREADS && j + 1 < N;
             double pa = 0.0, pg = 0.0, pu = 0.0;
             T pc = 0;
@@ -1788,7 +1788,8 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             // (cluster mode: into this CTA's shared memory, for the siblings to read)
             double *clp = (double *)(smem + p.off_cl);
             unsigned *clflag = (unsigned *)(clp + 2 * nj);
-            // (partials as double-fp32 pairs)
+            // (partials as double-fp32 pairs; outside cluster mode as tagged
+            // words in buffer pbuf of the group's two)
             const unsigned pbuf = n_ratio & 1u, tag = 1u + n_ratio % 3u;
             double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + pbuf) * Gr + rank) * nj;
             if (RES) {
