@@ -70,10 +70,14 @@ def test_persistent_equals_host_driven(precision):
         assert rel_norm_err(a["Ainv"][w], b["Ainv"][w]) < tol
 
 
-def test_batch_larger_than_sm_count():
-    """One CTA per walker, several walkers per CTA group when needed."""
+@pytest.mark.parametrize("N", [40, 41])
+def test_batch_larger_than_sm_count(N):
+    """One CTA per walker, several walkers per CTA group when needed; with odd
+    N a walker's last proposal and the next walker's first land on the same
+    partial-sum buffer parity of the electron index, which the exchange must
+    not depend on."""
     need_gpu()
-    N, K, batch, base, sigma = 40, 8, 400, 5, 0.4
+    K, batch, base, sigma = 8, 400, 5, 0.4
     out = sweep_once(N, K, batch, base, sigma)
     assert out["shape"]["flush_ctas"] == 1 and out["shape"]["ratio_ctas"] == 1
     A, G, U = walker_inputs(base, batch, N, 1)
