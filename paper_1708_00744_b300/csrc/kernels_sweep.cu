@@ -67,8 +67,9 @@ struct SweepParams {
     const double *gauss;    // [batch][N][ld] proposal Gaussians of this sweep
     const double *unif;     // [batch][N] Metropolis uniforms of this sweep
     double *partial;        // [ngroups][2][Gr][2K+1] tagged (hi, lo) words
-    unsigned *sync;         // [ngroups][SYNC_STRIDE]: ratio barrier, flush barrier, flush command,
-                            // each on its own 128-byte line
+    unsigned *sync;         // [ngroups][SYNC_STRIDE]: a spare line (the proposals exchange tagged
+                            // partials instead of a barrier), the flush barrier and the flush
+                            // command, each on its own 128-byte line
     int *status;
     double sigma;
     const signed char *override_;
