@@ -222,9 +222,11 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
  *   [3] recomputes       [4] recompute time (ms)   [5] stream syncs inside
  *   sweeps  [6] ratio launches  [7] accept launches
  *   [8..15] persistent sweeps, walker 0's lead CTA, time (ms) in: partial
- *   dot products, staging the next proposal, the group barrier, reduction and
- *   decision, accept, the flush's first barrier, the flush arithmetic, the
- *   flush's second barrier (host-driven sweeps time [2] instead)
+ *   dot products, staging the next proposal, the cluster-mode exchange wait
+ *   (near zero otherwise), waiting for and summing the other CTAs' partials
+ *   plus the decision, accept, the flush's first barrier, the flush
+ *   arithmetic, the flush's second barrier (host-driven sweeps time [2]
+ *   instead)
  *   [16] persistent sweep kernel launches  [17] their total time (ms)
  *   [18..20] the emulated-fp64 flush's phases (walker 0's lead CTA, barrier
  *   waits included), time (ms): T' = V'A^{-1} over row chunks; the reduction
@@ -242,8 +244,9 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *   QMCDU_OPT_FLUSH_CTAS   [auto] CTAs per walker that apply the flush
  *   QMCDU_OPT_WAIT_BUDGET_NS [2e9] time budget of every device spin-wait;
  *       on expiry the call fails with ERR_TIMEOUT at the next sync
- *   QMCDU_OPT_TEST_STALL   [0] test hook: the next persistent sweep waits for
- *       one arrival that never comes, so that its wait runs out of budget
+ *   QMCDU_OPT_TEST_STALL   [0] test hook: the next persistent sweep's first
+ *       proposal waits for partial sums that never come, so that its wait runs
+ *       out of budget
  *   QMCDU_OPT_MAX_CTAS     [whole GPU] cap on the persistent sweep's grid, so
  *       that several handles' sweeps can run side by side (qmcdu_group_*)
  *   QMCDU_OPT_GROUP_CTAS   [from the batch] fixed CTAs per walker group (at
