@@ -51,3 +51,21 @@ def test_version_and_argument_errors_without_gpu(lib):
 
 def test_library_is_built_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in qbuild.ARCH
+
+
+def header_enums():
+    text = open(os.path.join(ROOT, "include", "qmcdu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(QMCDU_\w+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    enums = header_enums()
+    opts = {k[len("QMCDU_OPT_"):].lower(): v for k, v in enums.items() if k.startswith("QMCDU_OPT_")}
+    assert opts == qmcdu.OPTIONS
+    assert {"QMCDU_FP64": qmcdu.PRECISIONS["fp64"], "QMCDU_FP32": qmcdu.PRECISIONS["fp32"],
+            "QMCDU_FP32_BF16X3": qmcdu.PRECISIONS["bf16x3"]} == {
+        k: enums[k] for k in ("QMCDU_FP64", "QMCDU_FP32", "QMCDU_FP32_BF16X3")}
+    status = {v: k[len("QMCDU_"):] for k, v in enums.items()
+              if k == "QMCDU_OK" or k.startswith("QMCDU_ERR_")}
+    assert status == qmcdu.STATUS
