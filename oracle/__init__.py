@@ -40,10 +40,11 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP for
+    the loops over independent output elements)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -65,10 +66,19 @@ def _load():
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]
         lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                      ip, dp, u8p, u8p, dp, dp, dp, dp, ip]
-        for f in (lib.oracle_slogdet, lib.oracle_inverse, lib.oracle_sweeps, lib.oracle_moves):
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        for f in (lib.oracle_slogdet, lib.oracle_inverse, lib.oracle_sweeps, lib.oracle_moves,
+                  lib.oracle_set_threads):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (n <= 0: every core OpenMP
+    sees). Results are identical for every count: each output element is
+    computed by one thread in the single-thread order. Returns the count."""
+    return _load().oracle_set_threads(int(n))
 
 
 def _p(a, ct):

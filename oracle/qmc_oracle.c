@@ -28,10 +28,19 @@
  * the squared determinant ratio, Sec. I). A per-move override (-1 decide, 0
  * reject, 1 accept) replays decisions; |min(1, r^2) - u| < 1e-10 counts as a
  * near tie.
+ *
+ * Threads: loops whose iterations write disjoint output elements (the rows of
+ * an elimination step, the columns of an inverse, the rows of a rank-k update,
+ * the entries of a look-ahead border) may run on several OpenMP threads. Every
+ * element is still computed by the same sequence of operations as on one
+ * thread, so results do not depend on the thread count.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_ERR_ARG 1
@@ -43,6 +52,22 @@
 #define METHOD_DELAYED 2
 
 static const double NEAR_TIE = 1e-10;
+
+/* Below this many multiply-adds a loop stays on one thread. */
+#define PAR_WORK 65536L
+
+/* Threads for the parallel loops (n <= 0: the OpenMP default). Returns the
+ * count in effect, 1 without OpenMP. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Dense LU with partial pivoting (textbook Doolittle, row interchanges).      */
@@ -72,6 +97,7 @@ static int lu_factor(int n, double *a, int *perm, int *nswaps)
         }
         double piv = a[(size_t)c * n + c];
         if (piv == 0.0) { singular = 1; continue; }
+        #pragma omp parallel for schedule(static) if ((long)(n - c) * (n - c) > PAR_WORK)
         for (int i = c + 1; i < n; ++i) {
             double l = a[(size_t)i * n + c] / piv;
             a[(size_t)i * n + c] = l;
@@ -119,20 +145,36 @@ int oracle_inverse(int n, const double *a, double *inv)
     memcpy(lu, a, sizeof(double) * (size_t)n * n);
     int nswaps;
     if (lu_factor(n, lu, perm, &nswaps)) { free(lu); free(perm); free(x); return OR_ERR_SINGULAR; }
-    for (int col = 0; col < n; ++col) {
-        for (int i = 0; i < n; ++i) x[i] = (i == col) ? 1.0 : 0.0;
-        for (int c = 0; c < n; ++c) {          /* apply the row interchanges */
-            int p = perm[c];
-            if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
+    int oom = 0;
+    #pragma omp parallel if ((long)n * n > PAR_WORK)
+    {
+        double *xt = x;                      /* thread 0 reuses x, the others their own */
+#ifdef _OPENMP
+        if (omp_get_thread_num() != 0) xt = malloc(sizeof(double) * (size_t)n);
+#endif
+        if (!xt) {
+            #pragma omp atomic write
+            oom = 1;
         }
-        for (int i = 0; i < n; ++i)             /* L y = P e_col */
-            for (int j = 0; j < i; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
-        for (int i = n - 1; i >= 0; --i) {      /* U x = y */
-            for (int j = i + 1; j < n; ++j) x[i] -= lu[(size_t)i * n + j] * x[j];
-            x[i] /= lu[(size_t)i * n + i];
+        #pragma omp for schedule(static)
+        for (int col = 0; col < n; ++col) {
+            if (!xt) continue;
+            for (int i = 0; i < n; ++i) xt[i] = (i == col) ? 1.0 : 0.0;
+            for (int c = 0; c < n; ++c) {          /* apply the row interchanges */
+                int p = perm[c];
+                if (p != c) { double t = xt[c]; xt[c] = xt[p]; xt[p] = t; }
+            }
+            for (int i = 0; i < n; ++i)             /* L y = P e_col */
+                for (int j = 0; j < i; ++j) xt[i] -= lu[(size_t)i * n + j] * xt[j];
+            for (int i = n - 1; i >= 0; --i) {      /* U x = y */
+                for (int j = i + 1; j < n; ++j) xt[i] -= lu[(size_t)i * n + j] * xt[j];
+                xt[i] /= lu[(size_t)i * n + i];
+            }
+            for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = xt[i];
         }
-        for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = x[i];
+        if (xt != x) free(xt);
     }
+    if (oom) { free(lu); free(perm); free(x); return OR_ERR_OOM; }
     free(lu); free(perm); free(x);
     return OR_OK;
 }
@@ -237,11 +279,13 @@ static double walker_propose(walker *w, int j, const double *col)
          * new border and take the explicit determinant of the (k+1) block. */
         int k = w->k, st = w->K + 1;
         const double *urow_j = w->Minv + (size_t)j * n;     /* e_j' Minv */
+        #pragma omp parallel for schedule(static) if ((long)n * k > PAR_WORK)
         for (int b = 0; b < k; ++b) {                         /* new row k */
             double t = 0.0;
             for (int i = 0; i < n; ++i) t += urow_j[i] * w->U[(size_t)i * w->K + b];
             w->S[k * st + b] = t;
         }
+        #pragma omp parallel for schedule(static) if ((long)n * k > PAR_WORK)
         for (int a = 0; a < k; ++a) {                         /* new column k */
             const double *row = w->Minv + (size_t)w->elec[a] * n;
             double t = 0.0;
@@ -276,6 +320,7 @@ static int walker_flush(walker *w)
         for (int b = 0; b < k; ++b) S[a * k + b] = w->S[a * st + b];
     int status = oracle_inverse(k, S, Sinv);
     if (status == OR_OK) {
+        #pragma omp parallel for schedule(static) if ((long)n * n * k > PAR_WORK)
         for (int i = 0; i < n; ++i)
             for (int b = 0; b < k; ++b) {
                 double t = 0.0;
@@ -284,12 +329,14 @@ static int walker_flush(walker *w)
             }
         for (int a = 0; a < k; ++a)
             memcpy(VM + (size_t)a * n, w->Minv + (size_t)w->elec[a] * n, sizeof(double) * n);
+        #pragma omp parallel for schedule(static) if ((long)n * k * k > PAR_WORK)
         for (int i = 0; i < n; ++i)
             for (int b = 0; b < k; ++b) {
                 double t = 0.0;
                 for (int a = 0; a < k; ++a) t += MU[(size_t)i * k + a] * Sinv[a * k + b];
                 X[(size_t)i * k + b] = t;
             }
+        #pragma omp parallel for schedule(static) if ((long)n * n * k > PAR_WORK)
         for (int i = 0; i < n; ++i)
             for (int l = 0; l < n; ++l) {
                 double t = 0.0;
@@ -312,12 +359,14 @@ static int walker_accept(walker *w)
     if (w->method == METHOD_SM) {
         /* Eq. 2: Minv <- Minv - (Minv u)(1 + e_j' Minv u)^{-1}(e_j' Minv). */
         double *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
+        #pragma omp parallel for schedule(static) if ((long)n * n > PAR_WORK)
         for (int i = 0; i < n; ++i) {
             double t = 0.0;
             for (int l = 0; l < n; ++l) t += w->Minv[(size_t)i * n + l] * w->u[l];
             x[i] = t;
         }
         memcpy(y, w->Minv + (size_t)j * n, sizeof(double) * n);
+        #pragma omp parallel for schedule(static) if ((long)n * n > PAR_WORK)
         for (int i = 0; i < n; ++i)
             for (int l = 0; l < n; ++l) w->Minv[(size_t)i * n + l] -= x[i] * y[l] / r;
         free(x); free(y);

@@ -321,3 +321,25 @@ def test_golden_fixture_reproduces():
         assert ["".join("1" if x else "0" for x in row) for row in out["accepted"]] == c["accepted"]
         assert np.max(np.abs(out["ratios"] - np.array(c["ratios"]))) == 0.0
         assert out["logabs"] == c["final_logabs"]
+
+
+@pytest.mark.parametrize("method,K", [(oracle.SM, 1), (oracle.DELAYED, 16)])
+def test_results_do_not_depend_on_thread_count(method, K):
+    """The parallel loops write disjoint elements, each in the one-thread
+    order: every output is bit-identical for 1 and several threads."""
+    n, ns = 300, 2
+    A, G, U = _sweep_inputs(77, n, ns)
+    prev = oracle.set_threads(1)
+    try:
+        one = oracle.sweeps(method, A, G, U, 0.3, K=K)
+        oracle.set_threads(4)
+        many = oracle.sweeps(method, A, G, U, 0.3, K=K)
+        inv1 = oracle.inverse(A)
+        oracle.set_threads(1)
+        inv0 = oracle.inverse(A)
+    finally:
+        oracle.set_threads(prev)
+    for key in ("ratios", "accepted", "A", "Ainv"):
+        assert np.array_equal(one[key], many[key]), key
+    assert one["logabs"] == many["logabs"] and one["sign"] == many["sign"]
+    assert np.array_equal(inv0, inv1)
