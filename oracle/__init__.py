@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
 leg of the benchmark are the only callers. The product path never imports it.
 
-Three readings of the paper, all in its column convention (one column of the
+Readings of the paper, all in its column convention (one column of the
 Slater matrix per electron, Sec. I), each loaded from qmc_oracle.c:
   BRUTE   ratio = det(M_new) / det(M) by two LU determinants (direct calculation)
   SM      ratio by the matrix determinant lemma (Eq. 1), inverse by the
@@ -11,6 +11,9 @@ Slater matrix per electron, Sec. I), each loaded from qmc_oracle.c:
   DELAYED ratios by look-ahead determinants of I_k + V'M^{-1}U (Eq. 3), queued
           accepted moves applied en bloc by Sherman-Morrison-Woodbury (Eq. 4)
           when k reaches K or the sweep ends (Sec. II)
+  DELAYED_SLOT  the same with Sec. II's fixed slots: a rejected proposal also
+          takes a queue slot, as an unchanged column (a zero change), so the
+          queue is flushed every K proposals
 plus LU log|det| and LU inverse. Inputs and outputs use the row convention of
 the library (row j of A = electron j); inverses come back in the column-major
 layout of A^{-1} (row c of the returned array is column c of A^{-1}).
@@ -31,7 +34,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qmc_oracle.c")
 _LIB = os.path.join(_HERE, "libqmc_oracle.so")
 
-BRUTE, SM, DELAYED = 0, 1, 2
+BRUTE, SM, DELAYED, DELAYED_SLOT = 0, 1, 2, 3
 OK, ERR_ARG, ERR_SINGULAR, ERR_OOM = 0, 1, 3, 4
 
 
@@ -67,11 +70,19 @@ def _load():
         lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                      ip, dp, u8p, u8p, dp, dp, dp, dp, ip]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_last_update_seconds.argtypes = []
+        lib.oracle_last_update_seconds.restype = ctypes.c_double
         for f in (lib.oracle_slogdet, lib.oracle_inverse, lib.oracle_sweeps, lib.oracle_moves,
                   lib.oracle_set_threads):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def last_update_seconds() -> float:
+    """Wall seconds of the last sweeps() call after its setup (the LU
+    determinant and inverse of the starting matrix): the update work alone."""
+    return _load().oracle_last_update_seconds()
 
 
 def set_threads(n: int = 0) -> int:

@@ -15,7 +15,7 @@
  * and out; an inverse is returned as Minv stored row-major, which is exactly
  * A^{-1} stored column-major.
  *
- * Three implementations of one sweep, each a different reading of the paper:
+ * Implementations of one sweep, each a different reading of the paper:
  *   O1 brute force: ratio det(M_new)/det(M) from two LU determinants.
  *   O2 Sherman-Morrison: ratio by the matrix determinant lemma (Eq. 1), inverse
  *      by the rank-1 Sherman-Morrison formula (Eq. 2).
@@ -23,6 +23,10 @@
  *      I_k + V' M^{-1} U (Eq. 3) divided by the previous one -- and the queued
  *      accepted moves applied en bloc by Sherman-Morrison-Woodbury (Eq. 4) when k
  *      reaches K or the sweep ends (Sec. II). Rejected moves change nothing.
+ *   O3' delayed, fixed slots: Sec. II's other treatment of a rejected move --
+ *      it takes a queue slot like an accepted one, with its column left
+ *      unchanged (a zero change) -- so that the queue holds every proposal
+ *      and is flushed every K proposals and at the end of the sweep.
  *
  * Metropolis rule: accept iff u < min(1, r^2) (the acceptance probability is
  * the squared determinant ratio, Sec. I). A per-move override (-1 decide, 0
@@ -38,6 +42,7 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -50,8 +55,24 @@
 #define METHOD_BRUTE 0
 #define METHOD_SM 1
 #define METHOD_DELAYED 2
+#define METHOD_DELAYED_SLOT 3
+#define IS_DELAYED(m) ((m) == METHOD_DELAYED || (m) == METHOD_DELAYED_SLOT)
 
 static const double NEAR_TIE = 1e-10;
+
+/* Wall time of the last oracle_sweeps call after its setup (the LU
+ * determinant and inverse of the starting matrix): the update work alone,
+ * for the benchmark's CPU baseline. */
+static double last_update_seconds = 0.0;
+
+double oracle_last_update_seconds(void) { return last_update_seconds; }
+
+static double wall_seconds(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 /* Below this many multiply-adds a loop stays on one thread. */
 #define PAR_WORK 65536L
@@ -306,7 +327,7 @@ static double walker_propose(walker *w, int j, const double *col)
  * Minv <- Minv - (Minv U) (I_k + V' Minv U)^{-1} (V' Minv). */
 static int walker_flush(walker *w)
 {
-    if (w->method != METHOD_DELAYED || w->k == 0) return OR_OK;
+    if (!IS_DELAYED(w->method) || w->k == 0) return OR_OK;
     int n = w->n, k = w->k, st = w->K + 1, KK = w->K;
     double *S = malloc(sizeof(double) * (size_t)k * k);
     double *Sinv = malloc(sizeof(double) * (size_t)k * k);
@@ -370,7 +391,7 @@ static int walker_accept(walker *w)
         for (int i = 0; i < n; ++i)
             for (int l = 0; l < n; ++l) w->Minv[(size_t)i * n + l] -= x[i] * y[l] / r;
         free(x); free(y);
-    } else if (w->method == METHOD_DELAYED) {
+    } else if (IS_DELAYED(w->method)) {
         int k = w->k;
         for (int i = 0; i < n; ++i) w->U[(size_t)i * w->K + k] = w->u[i];
         w->elec[k] = j;
@@ -385,7 +406,24 @@ static int walker_accept(walker *w)
         int st = oracle_inverse(n, w->M, w->Minv);
         if (st) return st;
     }
-    if (w->method == METHOD_DELAYED && w->k == w->K) return walker_flush(w);
+    if (IS_DELAYED(w->method) && w->k == w->K) return walker_flush(w);
+    return OR_OK;
+}
+
+/* Fixed slots (Sec. II): the rejected proposal still takes slot k, with the
+ * unchanged column of electron j, i.e. a zero change. The new column of
+ * I + V' Minv U is then e_k (row elec[a] of Minv times a zero column), its new
+ * row the one filled at the proposal, so the block determinant is unchanged;
+ * A, the running log|det| and sign stay as they are. */
+static int walker_reject_slot(walker *w)
+{
+    int n = w->n, k = w->k, st = w->K + 1;
+    for (int i = 0; i < n; ++i) w->U[(size_t)i * w->K + k] = 0.0;
+    for (int a = 0; a < k; ++a) w->S[a * st + k] = 0.0;
+    w->S[k * st + k] = 1.0;
+    w->elec[k] = w->prop_j;
+    w->k = k + 1;
+    if (w->k == w->K) return walker_flush(w);
     return OR_OK;
 }
 
@@ -436,10 +474,13 @@ int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
                   double *A_out, double *Ainv_out, double *logabs, int *sign,
                   long long *near_ties, long long max_moves)
 {
-    if (n < 1 || nsweeps < 0 || (method == METHOD_DELAYED && K < 1)) return OR_ERR_ARG;
+    if (n < 1 || nsweeps < 0 || method < METHOD_BRUTE || method > METHOD_DELAYED_SLOT ||
+        (IS_DELAYED(method) && K < 1))
+        return OR_ERR_ARG;
     walker w;
     int st = walker_init(&w, n, K, method, A0);
     if (st) return st;
+    const double t_start = wall_seconds();
     double *col = malloc(sizeof(double) * n);
     *near_ties = 0;
     long long done = 0;
@@ -456,9 +497,11 @@ int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
             int acc = decide(r, U[at], ov, near_ties);
             accepted[at] = (unsigned char)acc;
             if (acc) st = walker_accept(&w);
+            else if (method == METHOD_DELAYED_SLOT) st = walker_reject_slot(&w);
         }
         if (st == OR_OK) st = walker_flush(&w);
     }
+    last_update_seconds = wall_seconds() - t_start;
     if (st == OR_OK) walker_export(&w, A_out, Ainv_out, logabs, sign);
     free(col);
     walker_free(&w);
@@ -477,17 +520,20 @@ int oracle_moves(int method, int n, int K, int nmoves, const double *A0,
                  double *ratios, double *A_out, double *Ainv_out,
                  double *logabs, int *sign)
 {
-    if (n < 1 || nmoves < 0 || (method == METHOD_DELAYED && K < 1)) return OR_ERR_ARG;
+    if (n < 1 || nmoves < 0 || method < METHOD_BRUTE || method > METHOD_DELAYED_SLOT ||
+        (IS_DELAYED(method) && K < 1))
+        return OR_ERR_ARG;
     walker w;
     int st = walker_init(&w, n, K, method, A0);
     if (st) return st;
     for (int m = 0; m < nmoves && st == OR_OK; ++m) {
         int j = elec[m];
         if (j < 0 || j >= n) { st = OR_ERR_ARG; break; }
-        if (method == METHOD_DELAYED && in_queue(&w, j)) st = walker_flush(&w);
+        if (IS_DELAYED(method) && in_queue(&w, j)) st = walker_flush(&w);
         if (st) break;
         ratios[m] = walker_propose(&w, j, vrows + (size_t)m * n);
         if (decisions[m]) st = walker_accept(&w);
+        else if (method == METHOD_DELAYED_SLOT) st = walker_reject_slot(&w);
         if (st == OR_OK && flush_after && flush_after[m]) st = walker_flush(&w);
     }
     if (st == OR_OK) st = walker_flush(&w);

@@ -343,3 +343,38 @@ def test_results_do_not_depend_on_thread_count(method, K):
         assert np.array_equal(one[key], many[key]), key
     assert one["logabs"] == many["logabs"] and one["sign"] == many["sign"]
     assert np.array_equal(inv0, inv1)
+
+
+@pytest.mark.parametrize("sigma", [0.3, 1.5])
+def test_fixed_slot_reading_equivalent_to_one_move_at_a_time(sigma):
+    """Sec. II's fixed slots (a rejected proposal takes a queue slot as an
+    unchanged column): the same trajectory as Sherman-Morrison for every K,
+    with many rejections (sigma 1.5) and with few."""
+    n = 40
+    a, g, u = _sweep_inputs(12, n, 3)
+    ref = oracle.sweeps(oracle.SM, a, g, u, sigma)
+    assert ref["near_ties"] == 0
+    assert 0.2 < ref["accepted"].mean() < 0.98
+    for K in (1, 2, 3, 7, 16, 40):
+        d = oracle.sweeps(oracle.DELAYED_SLOT, a, g, u, sigma, K=K)
+        assert np.array_equal(d["accepted"], ref["accepted"]), K
+        assert np.max(np.abs(d["ratios"] - ref["ratios"]) / np.maximum(1.0, np.abs(ref["ratios"]))) < 1e-10
+        assert np.linalg.norm(d["Ainv"] - ref["Ainv"]) < 1e-10 * np.linalg.norm(ref["Ainv"])
+        assert abs(d["logabs"] - ref["logabs"]) < 1e-10 * max(1.0, abs(ref["logabs"]))
+        assert d["sign"] == ref["sign"] and np.array_equal(d["A"], ref["A"])
+
+
+def test_fixed_slot_rejections_change_nothing():
+    """Every proposal rejected: the queue fills with zero changes, the flushes
+    subtract exact zeros, and the inverse, A and log|det| stay bit for bit."""
+    n, K = 30, 4
+    a, g, u = _sweep_inputs(5, n, 2)
+    ov = np.zeros((2, n), dtype=np.int8)
+    d = oracle.sweeps(oracle.DELAYED_SLOT, a, g, u, 0.2, K=K, override=ov)
+    s, l = oracle.slogdet(a)
+    assert not d["accepted"].any()
+    assert np.array_equal(d["A"], a)
+    # the walker's inverse is the LU inverse of the paper's matrix M = A'
+    # (one column per electron), exported as it is
+    assert np.array_equal(d["Ainv"], oracle.inverse(np.ascontiguousarray(a.T)))
+    assert d["logabs"] == l and d["sign"] == s
