@@ -65,10 +65,14 @@ def _load():
         lib.oracle_slogdet.argtypes = [ctypes.c_int, dp, dp, ip]
         lib.oracle_inverse.argtypes = [ctypes.c_int, dp, dp]
         lib.oracle_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_double, dp, dp, dp, i8p, dp, u8p, dp, dp, dp, ip,
+                                      ctypes.c_double, dp, dp, dp, i8p, dp, dp, u8p, dp, dp, dp, ip,
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]
         lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
-                                     ip, dp, u8p, u8p, dp, dp, dp, dp, ip]
+                                     ip, dp, u8p, u8p, dp, dp, dp, dp, dp, ip]
+        lib.oracle_md_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int, ip, dp, i8p,
+                                         dp, u8p, dp, dp, dp, ip]
+        lib.oracle_md_sweeps.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_last_update_seconds.argtypes = []
         lib.oracle_last_update_seconds.restype = ctypes.c_double
@@ -86,8 +90,8 @@ def last_update_seconds() -> float:
 
 
 def set_threads(n: int = 0) -> int:
-    """Threads of the oracle's parallel loops (n <= 0: every core OpenMP
-    sees). Results are identical for every count: each output element is
+    """Threads of the oracle's parallel loops (n <= 0: every processor of
+    the host). Results are identical for every count: each output element is
     computed by one thread in the single-thread order. Returns the count."""
     return _load().oracle_set_threads(int(n))
 
@@ -127,12 +131,20 @@ def inverse_colmajor(a):
     return np.ascontiguousarray(inverse(a).T)
 
 
+ALT_INIT = 16      # added to a method: start from the inverse by the LU of A (not of A')
+
+
 def sweeps(method, A0, G, U, sigma, K=1, override=None, max_moves=-1):
     """Metropolis sweeps from A0 with Gaussians G[s, j, :] and uniforms U[s, j].
 
     max_moves >= 0 stops after that many proposals (a bounded sample).
+    method + ALT_INIT starts the walk from the inverse computed by the LU of
+    A (then transposed) instead of the LU of the paper's M = A'.
     Returns dict(ratios, accepted, A, Ainv (column-major layout), logabs, sign,
-    near_ties)."""
+    near_ties, terms). terms[s, j] = 1 + sum_i |(A^{-1})_ij (v - a_j)_i|, the
+    size of the terms of proposal j's Eq. 1 dot product (with the inverse of
+    the last flush for the delayed readings): it bounds that dot product's
+    rounding error."""
     A0 = _f64(A0)
     n = A0.shape[0]
     G = _f64(G).reshape(-1, n, n)
@@ -140,6 +152,7 @@ def sweeps(method, A0, G, U, sigma, K=1, override=None, max_moves=-1):
     U = _f64(U).reshape(ns, n)
     ov = None if override is None else np.ascontiguousarray(override, dtype=np.int8).reshape(ns, n)
     ratios = np.zeros((ns, n))
+    terms = np.zeros((ns, n))
     acc = np.zeros((ns, n), dtype=np.uint8)
     A = np.zeros((n, n))
     Ainv = np.zeros((n, n))
@@ -147,17 +160,19 @@ def sweeps(method, A0, G, U, sigma, K=1, override=None, max_moves=-1):
     st = _load().oracle_sweeps(method, n, K, ns, float(sigma), _p(A0, ctypes.c_double),
                                _p(G, ctypes.c_double), _p(U, ctypes.c_double),
                                _p(ov, ctypes.c_int8), _p(ratios, ctypes.c_double),
+                               _p(terms, ctypes.c_double),
                                _p(acc, ctypes.c_uint8), _p(A, ctypes.c_double),
                                _p(Ainv, ctypes.c_double), ctypes.byref(la), ctypes.byref(sg),
                                ctypes.byref(nt), int(max_moves))
     if st != OK:
         raise OracleError("oracle_sweeps status %d" % st)
     return dict(ratios=ratios, accepted=acc.astype(bool), A=A, Ainv=Ainv,
-                logabs=la.value, sign=sg.value, near_ties=nt.value)
+                logabs=la.value, sign=sg.value, near_ties=nt.value, terms=terms)
 
 
 def moves(method, A0, elec, vrows, decisions, K=1, flush_after=None):
-    """Explicit moves with given decisions. Returns dict(ratios, A, Ainv, logabs, sign)."""
+    """Explicit moves with given decisions. Returns dict(ratios, A, Ainv, logabs, sign,
+    terms) (terms as in sweeps())."""
     A0 = _f64(A0)
     n = A0.shape[0]
     elec = np.ascontiguousarray(elec, dtype=np.int32)
@@ -166,6 +181,7 @@ def moves(method, A0, elec, vrows, decisions, K=1, flush_after=None):
     dec = np.ascontiguousarray(decisions, dtype=np.uint8).reshape(m)
     fa = None if flush_after is None else np.ascontiguousarray(flush_after, dtype=np.uint8)
     ratios = np.zeros(m)
+    terms = np.zeros(m)
     A = np.zeros((n, n))
     Ainv = np.zeros((n, n))
     la, sg = ctypes.c_double(), ctypes.c_int()
@@ -173,8 +189,50 @@ def moves(method, A0, elec, vrows, decisions, K=1, flush_after=None):
                               elec.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                               _p(vrows, ctypes.c_double), _p(dec, ctypes.c_uint8),
                               _p(fa, ctypes.c_uint8), _p(ratios, ctypes.c_double),
+                              _p(terms, ctypes.c_double),
                               _p(A, ctypes.c_double), _p(Ainv, ctypes.c_double),
                               ctypes.byref(la), ctypes.byref(sg))
     if st != OK:
         raise OracleError("oracle_moves status %d" % st)
-    return dict(ratios=ratios, A=A, Ainv=Ainv, logabs=la.value, sign=sg.value)
+    return dict(ratios=ratios, A=A, Ainv=Ainv, logabs=la.value, sign=sg.value, terms=terms)
+
+
+MD_BRUTE, MD_TABLE = 0, 1
+
+
+def md_sweeps(method, A0, B0, G, H, U, sigma, exc, coef, override=None):
+    """Metropolis sweeps of a multideterminant walker, Psi = sum_I coef_I
+    det(A_I): A_I is A (electron rows, occupied orbital columns) with occupied
+    columns o_p replaced by columns a_p of B (the virtual orbitals at the
+    electrons), exc[I] = (o1, a1, o2, a2) with -1 for unused pairs.
+    Proposals v = a_j + sigma G[s, j], w = b_j + sigma H[s, j]; accept iff
+    u < min(1, R^2), R = Psi(new) / Psi(old).
+      MD_BRUTE  R from every det(A_I) by LU (the definition)
+      MD_TABLE  Clark et al.'s table T = A^{-1} B with the reference ratio of
+                Eq. 1 and Sherman-Morrison updates of A^{-1} and T
+    Returns dict(ratios, accepted, A, B, logabs, sign) (log|Psi|, sign Psi)."""
+    A0, B0 = _f64(A0), _f64(B0)
+    n, nv = A0.shape[0], B0.shape[1]
+    G = _f64(G).reshape(-1, n, n)
+    ns = G.shape[0]
+    H = _f64(H).reshape(ns, n, nv)
+    U = _f64(U).reshape(ns, n)
+    exc = np.ascontiguousarray(exc, dtype=np.int32).reshape(-1, 4)
+    coef = _f64(coef).reshape(-1)
+    ov = None if override is None else np.ascontiguousarray(override, dtype=np.int8).reshape(ns, n)
+    ratios = np.zeros((ns, n))
+    acc = np.zeros((ns, n), dtype=np.uint8)
+    A = np.zeros((n, n))
+    B = np.zeros((n, nv))
+    la, sg = ctypes.c_double(), ctypes.c_int()
+    st = _load().oracle_md_sweeps(method, n, nv, ns, float(sigma), _p(A0, ctypes.c_double),
+                                  _p(B0, ctypes.c_double), _p(G, ctypes.c_double), _p(H, ctypes.c_double),
+                                  _p(U, ctypes.c_double), exc.shape[0],
+                                  exc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  _p(coef, ctypes.c_double), _p(ov, ctypes.c_int8),
+                                  _p(ratios, ctypes.c_double), _p(acc, ctypes.c_uint8),
+                                  _p(A, ctypes.c_double), _p(B, ctypes.c_double),
+                                  ctypes.byref(la), ctypes.byref(sg))
+    if st != OK:
+        raise OracleError("oracle_md_sweeps status %d" % st)
+    return dict(ratios=ratios, accepted=acc.astype(bool), A=A, B=B, logabs=la.value, sign=sg.value)

@@ -77,12 +77,12 @@ static double wall_seconds(void)
 /* Below this many multiply-adds a loop stays on one thread. */
 #define PAR_WORK 65536L
 
-/* Threads for the parallel loops (n <= 0: the OpenMP default). Returns the
+/* Threads for the parallel loops (n <= 0: every processor). Returns the
  * count in effect, 1 without OpenMP. */
 int oracle_set_threads(int n)
 {
 #ifdef _OPENMP
-    if (n > 0) omp_set_num_threads(n);
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
     return omp_get_max_threads();
 #else
     (void)n;
@@ -221,6 +221,8 @@ typedef struct {
     double *u;         /* change u = prop_col - M[:, j]                        */
     double prop_logabs, prop_sign; /* look-ahead: det of the (k+1) block      */
     double ratio;
+    double terms;   /* 1 + sum_i |row j of the inverse in use| |u_i|: the size of */
+                    /* Eq. 1's terms, which bounds the rounding of its dot product */
 } walker;
 
 static void walker_free(walker *w)
@@ -229,7 +231,18 @@ static void walker_free(walker *w)
     free(w->prop_col); free(w->u);
 }
 
+/* init_alt = 1: the starting inverse from the LU of the caller's matrix A
+ * (rows = electrons), transposed, instead of the LU of M = A' -- another fp64
+ * computation of the same inverse, whose difference from the usual one shows
+ * how much the starting inverse alone moves a walk. */
+static int walker_init_alt(walker *w, int n, int K, int method, const double *A_rows, int init_alt);
+
 static int walker_init(walker *w, int n, int K, int method, const double *A_rows)
+{
+    return walker_init_alt(w, n, K, method, A_rows, 0);
+}
+
+static int walker_init_alt(walker *w, int n, int K, int method, const double *A_rows, int init_alt)
 {
     memset(w, 0, sizeof(*w));
     w->n = n; w->K = K > 0 ? K : 1; w->method = method;
@@ -250,8 +263,19 @@ static int walker_init(walker *w, int n, int K, int method, const double *A_rows
     int st = oracle_slogdet(n, w->M, &w->logabs, &sg);
     if (st) { walker_free(w); return st; }
     w->sign = sg;
-    st = oracle_inverse(n, w->M, w->Minv);
-    if (st) { walker_free(w); return st; }
+    if (init_alt) {
+        st = oracle_inverse(n, A_rows, w->Minv);     /* A^{-1}, row-major */
+        if (st) { walker_free(w); return st; }
+        for (int i = 0; i < n; ++i)                   /* Minv = (A^{-1})' */
+            for (int k = i + 1; k < n; ++k) {
+                double t = w->Minv[(size_t)i * n + k];
+                w->Minv[(size_t)i * n + k] = w->Minv[(size_t)k * n + i];
+                w->Minv[(size_t)k * n + i] = t;
+            }
+    } else {
+        st = oracle_inverse(n, w->M, w->Minv);
+        if (st) { walker_free(w); return st; }
+    }
     w->k = 0;
     w->blk_logabs = 0.0; w->blk_sign = 1.0;
     return OR_OK;
@@ -287,11 +311,19 @@ static double walker_propose(walker *w, int j, const double *col)
         oracle_slogdet(n, w->M, &la_old, &s_old);
         free(Mn);
         w->ratio = (s_new == 0) ? 0.0 : (double)(s_new * s_old) * exp(la_new - la_old);
+        double ta = 1.0;
+        for (int i = 0; i < n; ++i) ta += fabs(w->Minv[(size_t)j * n + i] * w->u[i]);
+        w->terms = ta;
     } else if (w->method == METHOD_SM) {
         /* Eq. 1: det(M + u e_j')/det(M) = 1 + e_j' Minv u. */
         double t = 1.0;
-        for (int i = 0; i < n; ++i) t += w->Minv[(size_t)j * n + i] * w->u[i];
+        double ta = 1.0;
+        for (int i = 0; i < n; ++i) {
+            t += w->Minv[(size_t)j * n + i] * w->u[i];
+            ta += fabs(w->Minv[(size_t)j * n + i] * w->u[i]);
+        }
         w->ratio = t;
+        w->terms = ta;
     } else {
         /* Eq. 3 look-ahead. The queue gives U (changes) and V (unit columns
          * e_elec[m]); the proposal appends u and e_j. Entry (a, b) of
@@ -314,7 +346,12 @@ static double walker_propose(walker *w, int j, const double *col)
             w->S[a * st + k] = t;
         }
         double t = 1.0;
-        for (int i = 0; i < n; ++i) t += urow_j[i] * w->u[i];
+        double ta = 1.0;
+        for (int i = 0; i < n; ++i) {
+            t += urow_j[i] * w->u[i];
+            ta += fabs(urow_j[i] * w->u[i]);
+        }
+        w->terms = ta;
         w->S[k * st + k] = t;
         small_slogdet(w->S, st, k + 1, &w->prop_logabs, &w->prop_sign);
         if (w->prop_sign == 0.0) w->ratio = 0.0;
@@ -462,7 +499,11 @@ static int decide(double r, double u, int override, long long *near_ties)
  *   G        nsweeps x n x n Gaussians, U nsweeps x n uniforms
  *   override nsweeps x n (-1 decide, 0 reject, 1 accept) or NULL
  * Outputs: ratios, accepted (nsweeps x n), final A rows, final inverse in the
- * column-major layout of A^{-1}, running log|det| and sign, near-tie count.
+ * column-major layout of A^{-1}, running log|det| and sign, near-tie count;
+ * terms (nsweeps x n, may be NULL): 1 + sum_i |(row j of the inverse) u_i| of
+ * each proposal (for the delayed readings with the inverse of the last flush).
+ * method + 16: the same reading started from the alternative inverse (see
+ * walker_init_alt).
  * The delayed method flushes when k reaches K and at the end of every sweep.
  * max_moves >= 0 stops after that many proposals (a bounded sample; the queue
  * is flushed); -1 runs every sweep in full.
@@ -470,15 +511,17 @@ static int decide(double r, double u, int override, long long *near_ties)
 int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
                   const double *A0, const double *G, const double *U,
                   const signed char *override,
-                  double *ratios, unsigned char *accepted,
+                  double *ratios, double *terms, unsigned char *accepted,
                   double *A_out, double *Ainv_out, double *logabs, int *sign,
                   long long *near_ties, long long max_moves)
 {
+    const int init_alt = (method & 16) != 0;
+    method &= 15;
     if (n < 1 || nsweeps < 0 || method < METHOD_BRUTE || method > METHOD_DELAYED_SLOT ||
         (IS_DELAYED(method) && K < 1))
         return OR_ERR_ARG;
     walker w;
-    int st = walker_init(&w, n, K, method, A0);
+    int st = walker_init_alt(&w, n, K, method, A0, init_alt);
     if (st) return st;
     const double t_start = wall_seconds();
     double *col = malloc(sizeof(double) * n);
@@ -493,6 +536,7 @@ int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
             double r = walker_propose(&w, j, col);
             size_t at = (size_t)s * n + j;
             ratios[at] = r;
+            if (terms) terms[at] = w.terms;
             int ov = override ? override[at] : -1;
             int acc = decide(r, U[at], ov, near_ties);
             accepted[at] = (unsigned char)acc;
@@ -517,14 +561,16 @@ int oracle_sweeps(int method, int n, int K, int nsweeps, double sigma,
 int oracle_moves(int method, int n, int K, int nmoves, const double *A0,
                  const int *elec, const double *vrows,
                  const unsigned char *decisions, const unsigned char *flush_after,
-                 double *ratios, double *A_out, double *Ainv_out,
+                 double *ratios, double *terms, double *A_out, double *Ainv_out,
                  double *logabs, int *sign)
 {
+    const int init_alt = (method & 16) != 0;
+    method &= 15;
     if (n < 1 || nmoves < 0 || method < METHOD_BRUTE || method > METHOD_DELAYED_SLOT ||
         (IS_DELAYED(method) && K < 1))
         return OR_ERR_ARG;
     walker w;
-    int st = walker_init(&w, n, K, method, A0);
+    int st = walker_init_alt(&w, n, K, method, A0, init_alt);
     if (st) return st;
     for (int m = 0; m < nmoves && st == OR_OK; ++m) {
         int j = elec[m];
@@ -532,6 +578,7 @@ int oracle_moves(int method, int n, int K, int nmoves, const double *A0,
         if (IS_DELAYED(method) && in_queue(&w, j)) st = walker_flush(&w);
         if (st) break;
         ratios[m] = walker_propose(&w, j, vrows + (size_t)m * n);
+        if (terms) terms[m] = w.terms;
         if (decisions[m]) st = walker_accept(&w);
         else if (method == METHOD_DELAYED_SLOT) st = walker_reject_slot(&w);
         if (st == OR_OK && flush_after && flush_after[m]) st = walker_flush(&w);
@@ -539,5 +586,222 @@ int oracle_moves(int method, int n, int K, int nmoves, const double *A0,
     if (st == OR_OK) st = walker_flush(&w);
     if (st == OR_OK) walker_export(&w, A_out, Ainv_out, logabs, sign);
     walker_free(&w);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multideterminant wavefunctions (the expansion Sec. II says the delayed     */
+/* scheme combines with: Clark et al.'s table method).                        */
+/*                                                                            */
+/* Row convention throughout this part: A[e][o] = phi_o(r_e) (electron rows,  */
+/* occupied orbital columns), B[e][a] = psi_a(r_e) (nv virtual orbitals).     */
+/* Determinant I replaces occupied columns o_p by virtual columns a_p,        */
+/* p = 1, 2 (exc[4 I + 2(p-1)] = o_p, exc[4 I + 2(p-1) + 1] = a_p, -1 when   */
+/* unused: I with no pair is the reference); Psi = sum_I coef_I det(A_I).    */
+/* ------------------------------------------------------------------------ */
+
+/* log|Psi| and sign(Psi) from every det(A_I) by LU (the definition). */
+static int md_psi_direct(int n, int nv, const double *A, const double *B, int ndet, const int *exc,
+                         const double *coef, double *logabs, double *sign)
+{
+    double *AI = malloc(sizeof(double) * (size_t)n * n);
+    double *la = malloc(sizeof(double) * (size_t)(ndet > 0 ? ndet : 1));
+    int *sg = malloc(sizeof(int) * (size_t)(ndet > 0 ? ndet : 1));
+    if (!AI || !la || !sg) { free(AI); free(la); free(sg); return OR_ERR_OOM; }
+    double lmax = -INFINITY;
+    for (int I = 0; I < ndet; ++I) {
+        memcpy(AI, A, sizeof(double) * (size_t)n * n);
+        for (int p = 0; p < 2; ++p) {
+            int o = exc[4 * I + 2 * p], a = exc[4 * I + 2 * p + 1];
+            if (o < 0 || a < 0) continue;
+            for (int e = 0; e < n; ++e) AI[(size_t)e * n + o] = B[(size_t)e * nv + a];
+        }
+        if (oracle_slogdet(n, AI, &la[I], &sg[I]) != OR_OK) { la[I] = -INFINITY; sg[I] = 0; }
+        if (sg[I] != 0 && la[I] > lmax) lmax = la[I];
+    }
+    double s = 0.0;
+    for (int I = 0; I < ndet; ++I)
+        if (sg[I] != 0) s += coef[I] * sg[I] * exp(la[I] - lmax);
+    free(AI); free(la); free(sg);
+    if (!(s != 0.0) || !isfinite(lmax)) { *logabs = -INFINITY; *sign = 0.0; return OR_ERR_SINGULAR; }
+    *logabs = lmax + log(fabs(s));
+    *sign = s < 0 ? -1.0 : 1.0;
+    return OR_OK;
+}
+
+/* r Psi(new) / det(A_new) after a move with reference ratio r: each
+ * determinant's table block T_I (rows o_p, columns a_p) changes by the rank-1
+ * term x_I d_I' / r, and the matrix determinant lemma gives
+ * r det(T_I + x_I d_I' / r) = r det(T_I) + d_I' adj(T_I) x_I (reference: r;
+ * one pair: r T_oa + x_o d_a; two pairs: the 2 x 2 adjugate), with no
+ * division by r. */
+static double md_table_num(int nv, const double *T, const double *x, const double *d, double r,
+                           int ndet, const int *exc, const double *coef)
+{
+    double s = 0.0;
+    for (int I = 0; I < ndet; ++I) {
+        int o1 = exc[4 * I], a1 = exc[4 * I + 1], o2 = exc[4 * I + 2], a2 = exc[4 * I + 3];
+        double t;
+        if (o1 < 0 || a1 < 0) {
+            t = r;
+        } else if (o2 < 0 || a2 < 0) {
+            t = r * T[(size_t)o1 * nv + a1] + x[o1] * d[a1];
+        } else {
+            double t11 = T[(size_t)o1 * nv + a1], t12 = T[(size_t)o1 * nv + a2];
+            double t21 = T[(size_t)o2 * nv + a1], t22 = T[(size_t)o2 * nv + a2];
+            t = r * (t11 * t22 - t12 * t21) + d[a1] * (t22 * x[o1] - t12 * x[o2]) +
+                d[a2] * (t11 * x[o2] - t21 * x[o1]);
+        }
+        s += coef[I] * t;
+    }
+    return s;
+}
+
+/* sum_I coef_I det(T_I) with T_I the rows o_p, columns a_p of the table (the
+ * reference: 1): Psi / det(A) by the table method (Cramer's rule). */
+static double md_table_sum(int nv, const double *T, int ndet, const int *exc, const double *coef)
+{
+    double s = 0.0;
+    for (int I = 0; I < ndet; ++I) {
+        int o1 = exc[4 * I], a1 = exc[4 * I + 1], o2 = exc[4 * I + 2], a2 = exc[4 * I + 3];
+        double d;
+        if (o1 < 0 || a1 < 0) d = 1.0;
+        else if (o2 < 0 || a2 < 0) d = T[(size_t)o1 * nv + a1];
+        else d = T[(size_t)o1 * nv + a1] * T[(size_t)o2 * nv + a2] - T[(size_t)o1 * nv + a2] * T[(size_t)o2 * nv + a1];
+        s += coef[I] * d;
+    }
+    return s;
+}
+
+#define MD_BRUTE 0
+#define MD_TABLE 1
+
+/*
+ * Metropolis sweeps of a multideterminant walker. Electron j = 0..n-1 in
+ * order; the proposed rows are v = a_j + sigma g (occupied orbitals) and
+ * w = b_j + sigma h (virtual orbitals), g = G[s][j][:], h = H[s][j][:]; the
+ * move is accepted iff u < min(1, R^2) with R = Psi(new) / Psi(old).
+ *   MD_BRUTE  R from Psi by md_psi_direct before and after (the definition)
+ *   MD_TABLE  R = r S' / S with r the reference ratio (Eq. 1), S = sum_I
+ *             coef_I det(T_I) over the table T = A^{-1} B (orbitals x
+ *             virtuals) and T' = T + x d' / r, d = w - b_j - T'u, x = A^{-1} e_j
+ *             (the table after the move, Sherman-Morrison), r S' formed
+ *             without dividing by r (md_table_num); on accept A^{-1} by
+ *             Eq. 2, T <- T' and S <- S'. The table is relative to the
+ *             reference determinant: accepting a move that makes it singular
+ *             (r = 0) returns OR_ERR_SINGULAR.
+ * exc: ndet x 4 ints as above; coef: ndet. Outputs: ratios R (nsweeps x n),
+ * accepted, final A and B rows, log|Psi| and its sign.
+ */
+int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
+                     const double *A0, const double *B0, const double *G, const double *H,
+                     const double *U, int ndet, const int *exc, const double *coef,
+                     const signed char *override, double *ratios, unsigned char *accepted,
+                     double *A_out, double *B_out, double *logabs, int *sign)
+{
+    if (n < 1 || nv < 1 || nsweeps < 0 || ndet < 1 || (method != MD_BRUTE && method != MD_TABLE))
+        return OR_ERR_ARG;
+    for (int I = 0; I < ndet; ++I)
+        for (int p = 0; p < 2; ++p) {
+            int o = exc[4 * I + 2 * p], a = exc[4 * I + 2 * p + 1];
+            if ((o >= 0) != (a >= 0) || o >= n || a >= nv) return OR_ERR_ARG;
+        }
+    size_t nn = (size_t)n * n, nb = (size_t)n * nv;
+    double *A = malloc(sizeof(double) * nn), *B = malloc(sizeof(double) * nb);
+    double *An = malloc(sizeof(double) * nn), *Bn = malloc(sizeof(double) * nb);
+    double *Ainv = malloc(sizeof(double) * nn), *T = malloc(sizeof(double) * nb);
+    double *Tn = malloc(sizeof(double) * nb), *u = malloc(sizeof(double) * n);
+    double *x = malloc(sizeof(double) * n), *dl = malloc(sizeof(double) * nv), *y = malloc(sizeof(double) * n);
+    int st = OR_OK;
+    if (!A || !B || !An || !Bn || !Ainv || !T || !Tn || !u || !x || !dl || !y) { st = OR_ERR_OOM; goto done; }
+    memcpy(A, A0, sizeof(double) * nn);
+    memcpy(B, B0, sizeof(double) * nb);
+    double lpsi, spsi;
+    st = md_psi_direct(n, nv, A, B, ndet, exc, coef, &lpsi, &spsi);
+    if (st) goto done;
+    double S = 1.0;
+    if (method == MD_TABLE) {
+        st = oracle_inverse(n, A, Ainv);     /* Ainv[o][e]: (A^{-1})_{oe} */
+        if (st) goto done;
+        for (int o = 0; o < n; ++o)          /* T = A^{-1} B */
+            for (int a = 0; a < nv; ++a) {
+                double t = 0.0;
+                for (int e = 0; e < n; ++e) t += Ainv[(size_t)o * n + e] * B[(size_t)e * nv + a];
+                T[(size_t)o * nv + a] = t;
+            }
+        S = md_table_sum(nv, T, ndet, exc, coef);
+    }
+    for (int s = 0; s < nsweeps && st == OR_OK; ++s) {
+        for (int j = 0; j < n && st == OR_OK; ++j) {
+            const double *g = G + ((size_t)s * n + j) * n, *h = H + ((size_t)s * n + j) * nv;
+            double R, lnew = 0.0, snew = 0.0, Sn = 0.0, r = 0.0;
+            if (method == MD_BRUTE) {
+                memcpy(An, A, sizeof(double) * nn);
+                memcpy(Bn, B, sizeof(double) * nb);
+                for (int o = 0; o < n; ++o) An[(size_t)j * n + o] = A[(size_t)j * n + o] + sigma * g[o];
+                for (int a = 0; a < nv; ++a) Bn[(size_t)j * nv + a] = B[(size_t)j * nv + a] + sigma * h[a];
+                if (md_psi_direct(n, nv, An, Bn, ndet, exc, coef, &lnew, &snew) != OR_OK) R = 0.0;
+                else R = snew * spsi * exp(lnew - lpsi);
+            } else {
+                for (int o = 0; o < n; ++o) {
+                    double v = A[(size_t)j * n + o] + sigma * g[o];
+                    u[o] = v - A[(size_t)j * n + o];
+                    x[o] = Ainv[(size_t)o * n + j];
+                }
+                r = 1.0;                                     /* Eq. 1 */
+                for (int o = 0; o < n; ++o) r += u[o] * x[o];
+                for (int a = 0; a < nv; ++a) {               /* w - b_j - T'u */
+                    double wb = (B[(size_t)j * nv + a] + sigma * h[a]) - B[(size_t)j * nv + a];
+                    double t = 0.0;
+                    for (int o = 0; o < n; ++o) t += u[o] * T[(size_t)o * nv + a];
+                    dl[a] = wb - t;
+                }
+                const double num = md_table_num(nv, T, x, dl, r, ndet, exc, coef);
+                R = num / S;
+                if (r != 0.0) Sn = num / r;
+            }
+            size_t at = (size_t)s * n + j;
+            ratios[at] = R;
+            int ov = override ? override[at] : -1;
+            double p = R * R;
+            if (p > 1.0) p = 1.0;
+            int acc = ov == 0 ? 0 : (ov == 1 ? 1 : (U[at] < p));
+            if (acc && (!(R != 0.0) || !isfinite(R))) { st = OR_ERR_SINGULAR; break; }
+            accepted[at] = (unsigned char)acc;
+            if (!acc) continue;
+            if (method == MD_BRUTE) {
+                memcpy(A, An, sizeof(double) * nn);
+                memcpy(B, Bn, sizeof(double) * nb);
+                lpsi = lnew; spsi = snew;
+            } else {
+                if (!(r != 0.0)) { st = OR_ERR_SINGULAR; break; }
+                for (int o = 0; o < n; ++o)          /* T <- T + x d' / r */
+                    for (int a = 0; a < nv; ++a)
+                        Tn[(size_t)o * nv + a] = T[(size_t)o * nv + a] + x[o] * dl[a] / r;
+                /* Eq. 2 on A^{-1} (row form): A^{-1} -= x (u' A^{-1}) / r */
+                for (int e = 0; e < n; ++e) {
+                    double t = 0.0;
+                    for (int o = 0; o < n; ++o) t += u[o] * Ainv[(size_t)o * n + e];
+                    y[e] = t;
+                }
+                for (int o = 0; o < n; ++o)
+                    for (int e = 0; e < n; ++e) Ainv[(size_t)o * n + e] -= x[o] * y[e] / r;
+                memcpy(T, Tn, sizeof(double) * nb);
+                for (int o = 0; o < n; ++o) A[(size_t)j * n + o] = A[(size_t)j * n + o] + sigma * g[o];
+                for (int a = 0; a < nv; ++a) B[(size_t)j * nv + a] = B[(size_t)j * nv + a] + sigma * h[a];
+                lpsi += log(fabs(R));
+                if (R < 0) spsi = -spsi;
+                S = Sn;
+            }
+        }
+    }
+    if (st == OR_OK) {
+        if (A_out) memcpy(A_out, A, sizeof(double) * nn);
+        if (B_out) memcpy(B_out, B, sizeof(double) * nb);
+        *logabs = lpsi;
+        *sign = (int)spsi;
+    }
+done:
+    free(A); free(B); free(An); free(Bn); free(Ainv); free(T); free(Tn); free(u); free(x); free(dl); free(y);
     return st;
 }

@@ -378,3 +378,105 @@ def test_fixed_slot_rejections_change_nothing():
     # (one column per electron), exported as it is
     assert np.array_equal(d["Ainv"], oracle.inverse(np.ascontiguousarray(a.T)))
     assert d["logabs"] == l and d["sign"] == s
+
+
+@pytest.mark.parametrize("method", [oracle.BRUTE, oracle.SM, oracle.DELAYED])
+def test_ratio_terms_closed_form_and_bound(method):
+    """terms = 1 + sum_i |(A^{-1})_ij u_i|: for A = I it is 1 + |u_j| (the
+    only nonzero term of Eq. 1), and it bounds |r| (triangle inequality)."""
+    n = 9
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((n, n))
+    out = oracle.moves(method, np.eye(n), np.arange(n), v, np.zeros(n, np.uint8), K=4)
+    u = v[np.arange(n), np.arange(n)] - 1.0
+    assert np.allclose(out["terms"], 1.0 + np.abs(u), rtol=1e-15, atol=0)
+    a, g, uu = _sweep_inputs(8, 24, 1)
+    s = oracle.sweeps(method, a, g, uu, 0.5, K=4)
+    assert np.all(s["terms"] >= np.abs(s["ratios"]) * (1 - 1e-14))
+
+
+# ---------------------------------------------------------------- multideterminant walkers
+def _md_exact_psi(A, B, exc, coef):
+    """Psi = sum_I c_I det(A_I) in exact rational arithmetic (Leibniz)."""
+    tot = Fraction(0)
+    for (o1, a1, o2, a2), c in zip(exc, coef):
+        M = [[Fraction(int(x)) for x in row] for row in A]
+        for o, a in ((o1, a1), (o2, a2)):
+            if o >= 0:
+                for e in range(len(M)):
+                    M[e][o] = Fraction(int(B[e][a]))
+        tot += Fraction(c) * leibniz_det(M)
+    return tot
+
+
+def _md_case(seed, n=4, nv=3):
+    rng = np.random.default_rng(seed)
+    A = random_int_matrix(rng, n)
+    B = rng.integers(-3, 4, size=(n, nv)).astype(np.float64)
+    exc = [(-1, -1, -1, -1), (0, 1, -1, -1), (2, 0, -1, -1), (1, 2, 3, 0), (0, 0, 2, 1)]
+    coef = [1.0, 0.5, -0.25, 0.125, 0.75]
+    G = rng.integers(-2, 3, size=(1, n, n)).astype(np.float64)
+    H = rng.integers(-2, 3, size=(1, n, nv)).astype(np.float64)
+    return A, B, exc, coef, G, H
+
+
+@pytest.mark.parametrize("method", [oracle.MD_BRUTE, oracle.MD_TABLE])
+def test_multideterminant_ratios_match_exact_rational(method):
+    """Integer orbitals and integer moves (sigma = 1): every ratio of
+    Psi = sum_I c_I det(A_I) against exact Leibniz determinants over the
+    rationals, along the walk of given decisions."""
+    for seed in (1, 2, 3):
+        A, B, exc, coef, G, H = _md_case(seed)
+        n = A.shape[0]
+        dec = np.array([1, 0, 1, 1], dtype=np.int8)[None]
+        # a move onto a singular reference determinant is not taken (the table
+        # is relative to it); its ratio is still checked
+        cA = A.copy()
+        for j in range(n):
+            nA = cA.copy()
+            nA[j] += G[0, j]
+            if leibniz_det(nA.astype(int).tolist()) == 0:
+                dec[0, j] = 0
+            if dec[0, j]:
+                cA = nA
+        U = np.full((1, n), 0.5)
+        out = oracle.md_sweeps(method, A, B, G, H, U, 1.0, exc, coef, override=dec)
+        cur_A, cur_B = A.copy(), B.copy()
+        psi = _md_exact_psi(cur_A, cur_B, exc, coef)
+        for j in range(n):
+            nA, nB = cur_A.copy(), cur_B.copy()
+            nA[j] += G[0, j]
+            nB[j] += H[0, j]
+            npsi = _md_exact_psi(nA, nB, exc, coef)
+            exact = float(npsi / psi) if psi != 0 else 0.0
+            assert abs(out["ratios"][0, j] - exact) <= 1e-11 * max(1.0, abs(exact)), (seed, j)
+            if dec[0, j]:
+                cur_A, cur_B, psi = nA, nB, npsi
+        assert np.array_equal(out["A"], cur_A) and np.array_equal(out["B"], cur_B)
+
+
+def test_multideterminant_readings_agree_and_reduce_to_one_determinant():
+    """The table method (Sherman-Morrison on A^{-1} and the table) follows the
+    definition's trajectory, and an expansion of the reference alone is the
+    one-determinant walk."""
+    n, nv, ns = 24, 6, 2
+    rng = np.random.default_rng(9)
+    a, g, u = _sweep_inputs(31, n, ns)
+    B = rng.standard_normal((n, nv))
+    H = rng.standard_normal((ns, n, nv))
+    exc = [(-1, -1, -1, -1)] + [(int(o), int(v), -1, -1) for o, v in zip(rng.integers(0, n, 6),
+                                                                          rng.integers(0, nv, 6))]
+    exc += [(0, 1, 5, 2), (3, 4, 7, 0)]
+    coef = rng.standard_normal(len(exc)) * 0.3
+    coef[0] = 1.0
+    brute = oracle.md_sweeps(oracle.MD_BRUTE, a, B, g, H, u, 0.3, exc, coef)
+    table = oracle.md_sweeps(oracle.MD_TABLE, a, B, g, H, u, 0.3, exc, coef)
+    assert 0.2 < brute["accepted"].mean() < 0.99
+    assert np.array_equal(brute["accepted"], table["accepted"])
+    assert np.max(np.abs(brute["ratios"] - table["ratios"]) / np.maximum(1, np.abs(brute["ratios"]))) < 1e-10
+    assert abs(brute["logabs"] - table["logabs"]) < 1e-10 * max(1, abs(brute["logabs"]))
+    assert brute["sign"] == table["sign"]
+    one = oracle.md_sweeps(oracle.MD_TABLE, a, B, g, H, u, 0.3, exc[:1], [1.0])
+    sm = oracle.sweeps(oracle.SM, a, g, u, 0.3)
+    assert np.array_equal(one["accepted"], sm["accepted"])
+    assert np.max(np.abs(one["ratios"] - sm["ratios"]) / np.maximum(1, np.abs(sm["ratios"]))) < 1e-12
