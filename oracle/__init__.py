@@ -69,7 +69,7 @@ def _load():
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong]
         lib.oracle_moves.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                      ip, dp, u8p, u8p, dp, dp, dp, dp, dp, ip]
-        lib.oracle_md_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        lib.oracle_md_sweeps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int, ip, dp, i8p,
                                          dp, u8p, dp, dp, dp, ip]
         lib.oracle_md_sweeps.restype = ctypes.c_int
@@ -197,10 +197,10 @@ def moves(method, A0, elec, vrows, decisions, K=1, flush_after=None):
     return dict(ratios=ratios, A=A, Ainv=Ainv, logabs=la.value, sign=sg.value, terms=terms)
 
 
-MD_BRUTE, MD_TABLE = 0, 1
+MD_BRUTE, MD_TABLE, MD_TABLE_DELAYED = 0, 1, 2
 
 
-def md_sweeps(method, A0, B0, G, H, U, sigma, exc, coef, override=None):
+def md_sweeps(method, A0, B0, G, H, U, sigma, exc, coef, override=None, K=1):
     """Metropolis sweeps of a multideterminant walker, Psi = sum_I coef_I
     det(A_I): A_I is A (electron rows, occupied orbital columns) with occupied
     columns o_p replaced by columns a_p of B (the virtual orbitals at the
@@ -210,6 +210,10 @@ def md_sweeps(method, A0, B0, G, H, U, sigma, exc, coef, override=None):
       MD_BRUTE  R from every det(A_I) by LU (the definition)
       MD_TABLE  Clark et al.'s table T = A^{-1} B with the reference ratio of
                 Eq. 1 and Sherman-Morrison updates of A^{-1} and T
+      MD_TABLE_DELAYED  the same table with the reference inverse under the
+                delayed update (Eq. 3-4, queue length K): the current column
+                A^{-1} e_j by the Woodbury form, Eq. 4 when K moves wait or
+                a queued electron moves again
     Returns dict(ratios, accepted, A, B, logabs, sign) (log|Psi|, sign Psi)."""
     A0, B0 = _f64(A0), _f64(B0)
     n, nv = A0.shape[0], B0.shape[1]
@@ -225,7 +229,7 @@ def md_sweeps(method, A0, B0, G, H, U, sigma, exc, coef, override=None):
     A = np.zeros((n, n))
     B = np.zeros((n, nv))
     la, sg = ctypes.c_double(), ctypes.c_int()
-    st = _load().oracle_md_sweeps(method, n, nv, ns, float(sigma), _p(A0, ctypes.c_double),
+    st = _load().oracle_md_sweeps(method, int(K), n, nv, ns, float(sigma), _p(A0, ctypes.c_double),
                                   _p(B0, ctypes.c_double), _p(G, ctypes.c_double), _p(H, ctypes.c_double),
                                   _p(U, ctypes.c_double), exc.shape[0],
                                   exc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),

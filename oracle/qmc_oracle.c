@@ -635,6 +635,51 @@ static int md_psi_direct(int n, int nv, const double *A, const double *B, int nd
  * r det(T_I + x_I d_I' / r) = r det(T_I) + d_I' adj(T_I) x_I (reference: r;
  * one pair: r T_oa + x_o d_a; two pairs: the 2 x 2 adjugate), with no
  * division by r. */
+/* Eq. 4 for the multideterminant walker's delayed reading: Ainv (rows =
+ * orbitals, columns = electrons, Ainv[o][e] = (A^{-1})_{oe}) <- Ainv -
+ * P Kinv (U Ainv), P = the columns idx_m of Ainv, U = the kq queued changes
+ * as rows. */
+static void md_flush(int n, double *Ainv, int kq, const int *qidx, const double *Uq, const double *Ki,
+                     double *Pq, double *Yq)
+{
+    if (kq == 0) return;
+    for (int o = 0; o < n; ++o)
+        for (int m = 0; m < kq; ++m) Pq[(size_t)o * kq + m] = Ainv[(size_t)o * n + qidx[m]];
+    for (int m = 0; m < kq; ++m)                 /* Y = U Ainv */
+        for (int e = 0; e < n; ++e) {
+            double t = 0.0;
+            for (int o = 0; o < n; ++o) t += Uq[(size_t)m * n + o] * Ainv[(size_t)o * n + e];
+            Yq[(size_t)m * n + e] = t;
+        }
+    for (int o = 0; o < n; ++o) {                /* Ainv -= (P Kinv) Y */
+        double pk[256];
+        for (int l = 0; l < kq; ++l) {
+            double t = 0.0;
+            for (int m = 0; m < kq; ++m) t += Pq[(size_t)o * kq + m] * Ki[(size_t)m * kq + l];
+            pk[l] = t;
+        }
+        for (int e = 0; e < n; ++e) {
+            double t = 0.0;
+            for (int l = 0; l < kq; ++l) t += pk[l] * Yq[(size_t)l * n + e];
+            Ainv[(size_t)o * n + e] -= t;
+        }
+    }
+}
+
+/* Kinv = (I + U P)^{-1} of the kq queued moves (P = the columns idx_m of the
+ * last flush's Ainv): the k x k matrix of Eq. 3. */
+static int md_queue_inverse(int n, const double *Ainv, int kq, const int *qidx, const double *Uq, double *Km,
+                            double *Ki)
+{
+    for (int m = 0; m < kq; ++m)
+        for (int l = 0; l < kq; ++l) {
+            double t = m == l ? 1.0 : 0.0;
+            for (int o = 0; o < n; ++o) t += Uq[(size_t)m * n + o] * Ainv[(size_t)o * n + qidx[l]];
+            Km[(size_t)m * kq + l] = t;
+        }
+    return oracle_inverse(kq, Km, Ki);
+}
+
 static double md_table_num(int nv, const double *T, const double *x, const double *d, double r,
                            int ndet, const int *exc, const double *coef)
 {
@@ -675,6 +720,7 @@ static double md_table_sum(int nv, const double *T, int ndet, const int *exc, co
 
 #define MD_BRUTE 0
 #define MD_TABLE 1
+#define MD_TABLE_DELAYED 2
 
 /*
  * Metropolis sweeps of a multideterminant walker. Electron j = 0..n-1 in
@@ -690,17 +736,29 @@ static double md_table_sum(int nv, const double *T, int ndet, const int *exc, co
  *             Eq. 2, T <- T' and S <- S'. The table is relative to the
  *             reference determinant: accepting a move that makes it singular
  *             (r = 0) returns OR_ERR_SINGULAR.
+ *   MD_TABLE_DELAYED  the table method with the reference determinant's
+ *             inverse under the delayed update (Sec. II): A^{-1} stays that
+ *             of the last flush, the accepted changes u_m of electrons idx_m
+ *             wait in a queue of at most K, the current column
+ *             x = A_c^{-1} e_j is the Woodbury form of Eq. 3-4 applied to one
+ *             column, x = a_j - P (I + U P)^{-1} U a_j (a_j = A^{-1} e_j,
+ *             P = A^{-1}[:, idx], U the queued changes as rows), r = 1 + u'x,
+ *             and Eq. 4 flushes the queue when it holds K moves or before an
+ *             electron already in it moves again (and at the end).
  * exc: ndet x 4 ints as above; coef: ndet. Outputs: ratios R (nsweeps x n),
  * accepted, final A and B rows, log|Psi| and its sign.
  */
-int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
+int oracle_md_sweeps(int method, int K, int n, int nv, int nsweeps, double sigma,
                      const double *A0, const double *B0, const double *G, const double *H,
                      const double *U, int ndet, const int *exc, const double *coef,
                      const signed char *override, double *ratios, unsigned char *accepted,
                      double *A_out, double *B_out, double *logabs, int *sign)
 {
-    if (n < 1 || nv < 1 || nsweeps < 0 || ndet < 1 || (method != MD_BRUTE && method != MD_TABLE))
+    if (n < 1 || nv < 1 || nsweeps < 0 || ndet < 1 ||
+        (method != MD_BRUTE && method != MD_TABLE && method != MD_TABLE_DELAYED) ||
+        (method == MD_TABLE_DELAYED && (K < 1 || K > n || K > 256)))
         return OR_ERR_ARG;
+    if (method != MD_TABLE_DELAYED) K = 1;
     for (int I = 0; I < ndet; ++I)
         for (int p = 0; p < 2; ++p) {
             int o = exc[4 * I + 2 * p], a = exc[4 * I + 2 * p + 1];
@@ -712,15 +770,24 @@ int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
     double *Ainv = malloc(sizeof(double) * nn), *T = malloc(sizeof(double) * nb);
     double *Tn = malloc(sizeof(double) * nb), *u = malloc(sizeof(double) * n);
     double *x = malloc(sizeof(double) * n), *dl = malloc(sizeof(double) * nv), *y = malloc(sizeof(double) * n);
+    /* the delayed reading's queue: electrons, changes (rows), the k x k
+     * matrix I + U P and its inverse, scratch for Eq. 4 */
+    int *qidx = malloc(sizeof(int) * K);
+    double *Uq = malloc(sizeof(double) * (size_t)K * n), *Pq = malloc(sizeof(double) * (size_t)n * K);
+    double *Km = malloc(sizeof(double) * (size_t)K * K), *Ki = malloc(sizeof(double) * (size_t)K * K);
+    double *cq = malloc(sizeof(double) * K), *tq = malloc(sizeof(double) * K);
+    double *Yq = malloc(sizeof(double) * (size_t)K * n);
+    int kq = 0;
     int st = OR_OK;
-    if (!A || !B || !An || !Bn || !Ainv || !T || !Tn || !u || !x || !dl || !y) { st = OR_ERR_OOM; goto done; }
+    if (!A || !B || !An || !Bn || !Ainv || !T || !Tn || !u || !x || !dl || !y || !qidx || !Uq || !Pq || !Km ||
+        !Ki || !cq || !tq || !Yq) { st = OR_ERR_OOM; goto done; }
     memcpy(A, A0, sizeof(double) * nn);
     memcpy(B, B0, sizeof(double) * nb);
     double lpsi, spsi;
     st = md_psi_direct(n, nv, A, B, ndet, exc, coef, &lpsi, &spsi);
     if (st) goto done;
     double S = 1.0;
-    if (method == MD_TABLE) {
+    if (method != MD_BRUTE) {
         st = oracle_inverse(n, A, Ainv);     /* Ainv[o][e]: (A^{-1})_{oe} */
         if (st) goto done;
         for (int o = 0; o < n; ++o)          /* T = A^{-1} B */
@@ -743,10 +810,36 @@ int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
                 if (md_psi_direct(n, nv, An, Bn, ndet, exc, coef, &lnew, &snew) != OR_OK) R = 0.0;
                 else R = snew * spsi * exp(lnew - lpsi);
             } else {
+                if (method == MD_TABLE_DELAYED) {
+                    int queued = 0;
+                    for (int m = 0; m < kq; ++m) queued |= qidx[m] == j;
+                    if (queued) {
+                        md_flush(n, Ainv, kq, qidx, Uq, Ki, Pq, Yq);
+                        kq = 0;
+                    }
+                }
                 for (int o = 0; o < n; ++o) {
                     double v = A[(size_t)j * n + o] + sigma * g[o];
                     u[o] = v - A[(size_t)j * n + o];
                     x[o] = Ainv[(size_t)o * n + j];
+                }
+                if (method == MD_TABLE_DELAYED && kq > 0) {
+                    /* x = a_j - P Kinv (U a_j): column j of the current inverse */
+                    for (int m = 0; m < kq; ++m) {
+                        double t = 0.0;
+                        for (int o = 0; o < n; ++o) t += Uq[(size_t)m * n + o] * x[o];
+                        cq[m] = t;
+                    }
+                    for (int m = 0; m < kq; ++m) {
+                        double t = 0.0;
+                        for (int l = 0; l < kq; ++l) t += Ki[(size_t)m * kq + l] * cq[l];
+                        tq[m] = t;
+                    }
+                    for (int o = 0; o < n; ++o) {
+                        double t = 0.0;
+                        for (int m = 0; m < kq; ++m) t += Ainv[(size_t)o * n + qidx[m]] * tq[m];
+                        x[o] -= t;
+                    }
                 }
                 r = 1.0;                                     /* Eq. 1 */
                 for (int o = 0; o < n; ++o) r += u[o] * x[o];
@@ -778,14 +871,27 @@ int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
                 for (int o = 0; o < n; ++o)          /* T <- T + x d' / r */
                     for (int a = 0; a < nv; ++a)
                         Tn[(size_t)o * nv + a] = T[(size_t)o * nv + a] + x[o] * dl[a] / r;
-                /* Eq. 2 on A^{-1} (row form): A^{-1} -= x (u' A^{-1}) / r */
-                for (int e = 0; e < n; ++e) {
-                    double t = 0.0;
-                    for (int o = 0; o < n; ++o) t += u[o] * Ainv[(size_t)o * n + e];
-                    y[e] = t;
+                if (method == MD_TABLE) {
+                    /* Eq. 2 on A^{-1} (row form): A^{-1} -= x (u' A^{-1}) / r */
+                    for (int e = 0; e < n; ++e) {
+                        double t = 0.0;
+                        for (int o = 0; o < n; ++o) t += u[o] * Ainv[(size_t)o * n + e];
+                        y[e] = t;
+                    }
+                    for (int o = 0; o < n; ++o)
+                        for (int e = 0; e < n; ++e) Ainv[(size_t)o * n + e] -= x[o] * y[e] / r;
+                } else {
+                    /* queue the change; Eq. 4 once K moves wait */
+                    qidx[kq] = j;
+                    memcpy(Uq + (size_t)kq * n, u, sizeof(double) * n);
+                    ++kq;
+                    st = md_queue_inverse(n, Ainv, kq, qidx, Uq, Km, Ki);
+                    if (st) break;
+                    if (kq == K) {
+                        md_flush(n, Ainv, kq, qidx, Uq, Ki, Pq, Yq);
+                        kq = 0;
+                    }
                 }
-                for (int o = 0; o < n; ++o)
-                    for (int e = 0; e < n; ++e) Ainv[(size_t)o * n + e] -= x[o] * y[e] / r;
                 memcpy(T, Tn, sizeof(double) * nb);
                 for (int o = 0; o < n; ++o) A[(size_t)j * n + o] = A[(size_t)j * n + o] + sigma * g[o];
                 for (int a = 0; a < nv; ++a) B[(size_t)j * nv + a] = B[(size_t)j * nv + a] + sigma * h[a];
@@ -803,5 +909,6 @@ int oracle_md_sweeps(int method, int n, int nv, int nsweeps, double sigma,
     }
 done:
     free(A); free(B); free(An); free(Bn); free(Ainv); free(T); free(Tn); free(u); free(x); free(dl); free(y);
+    free(qidx); free(Uq); free(Pq); free(Km); free(Ki); free(cq); free(tq); free(Yq);
     return st;
 }

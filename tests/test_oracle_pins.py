@@ -420,11 +420,14 @@ def _md_case(seed, n=4, nv=3):
     return A, B, exc, coef, G, H
 
 
-@pytest.mark.parametrize("method", [oracle.MD_BRUTE, oracle.MD_TABLE])
-def test_multideterminant_ratios_match_exact_rational(method):
+@pytest.mark.parametrize("method,K", [(oracle.MD_BRUTE, 1), (oracle.MD_TABLE, 1), (oracle.MD_TABLE_DELAYED, 2),
+                                      (oracle.MD_TABLE_DELAYED, 4)])
+def test_multideterminant_ratios_match_exact_rational(method, K):
     """Integer orbitals and integer moves (sigma = 1): every ratio of
     Psi = sum_I c_I det(A_I) against exact Leibniz determinants over the
-    rationals, along the walk of given decisions."""
+    rationals, along the walk of given decisions (the delayed reading with
+    queued moves, so that the Woodbury column of the current inverse is
+    used)."""
     for seed in (1, 2, 3):
         A, B, exc, coef, G, H = _md_case(seed)
         n = A.shape[0]
@@ -440,7 +443,7 @@ def test_multideterminant_ratios_match_exact_rational(method):
             if dec[0, j]:
                 cA = nA
         U = np.full((1, n), 0.5)
-        out = oracle.md_sweeps(method, A, B, G, H, U, 1.0, exc, coef, override=dec)
+        out = oracle.md_sweeps(method, A, B, G, H, U, 1.0, exc, coef, override=dec, K=K)
         cur_A, cur_B = A.copy(), B.copy()
         psi = _md_exact_psi(cur_A, cur_B, exc, coef)
         for j in range(n):
@@ -476,6 +479,11 @@ def test_multideterminant_readings_agree_and_reduce_to_one_determinant():
     assert np.max(np.abs(brute["ratios"] - table["ratios"]) / np.maximum(1, np.abs(brute["ratios"]))) < 1e-10
     assert abs(brute["logabs"] - table["logabs"]) < 1e-10 * max(1, abs(brute["logabs"]))
     assert brute["sign"] == table["sign"]
+    for K in (1, 5, n):
+        dl = oracle.md_sweeps(oracle.MD_TABLE_DELAYED, a, B, g, H, u, 0.3, exc, coef,
+                              override=brute["accepted"].astype(np.int8), K=K)
+        assert np.max(np.abs(brute["ratios"] - dl["ratios"]) / np.maximum(1, np.abs(brute["ratios"]))) < 1e-10, K
+        assert abs(brute["logabs"] - dl["logabs"]) < 1e-10 * max(1, abs(brute["logabs"]))
     one = oracle.md_sweeps(oracle.MD_TABLE, a, B, g, H, u, 0.3, exc[:1], [1.0])
     sm = oracle.sweeps(oracle.SM, a, g, u, 0.3)
     assert np.array_equal(one["accepted"], sm["accepted"])
