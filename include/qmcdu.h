@@ -12,6 +12,11 @@
  *     (Eq. 3) through N x k panels and a k x k inverse, and the queued moves
  *     are applied en bloc by Sherman-Morrison-Woodbury (Eq. 4) when k reaches
  *     K or the sweep ends (Sec. II). Rejected moves change nothing.
+ *   - Every formula is taken in the paper's change form: a move of electron j
+ *     to the new row v is the rank-1 change e_j u' with u = v - a_j, its
+ *     ratio is 1 + u . A^{-1}[:, j] (Eq. 1), and the queue holds the changes of
+ *     the accepted moves (Eq. 3-4). The change is small next to the row, so
+ *     the error of the running inverse enters the ratio only through u.
  *   - The determinant is checked against direct calculation after a sweep
  *     (Sec. III): qmcdu_recompute.
  *
@@ -40,6 +45,7 @@ extern "C" {
 
 typedef struct qmcdu_ctx *qmcdu_t;
 typedef struct qmcdu_group_ctx *qmcdu_group_t;
+typedef struct qmcdu_md_ctx *qmcdu_md_t;
 
 /* Working precision of A^{-1}, the panels and the flush. */
 enum {
@@ -48,7 +54,11 @@ enum {
                            /* log-det and the recompute fp64                      */
     QMCDU_FP32_BF16X3 = 2  /* as FP32, flush on tensor cores with split-bf16 x3   */
                            /* (tcgen05) wherever a flush block is >= 128       */
-                           /* columns and K <= 64; fp32 SIMT flush otherwise   */
+                           /* columns and K <= 64; fp32 SIMT flush otherwise.  */
+                           /* Small moves (DMC-like, sigma ~ 0.1) only: at     */
+                           /* sigma = 1 its ratio errors reach 0.02-0.16 and   */
+                           /* most decisions fall within them of a tie, which  */
+                           /* no tolerance of the method accepts; use FP32     */
 };
 
 enum {
@@ -137,6 +147,18 @@ int qmcdu_recompute(qmcdu_t h, double *drift_out);
 int qmcdu_logdet(qmcdu_t h, double *logabs, int *sign);
 
 /*
+ * A walker of two determinants, one per spin (the paper sizes its solid-state
+ * walkers by both spins, Sec. III): walker b's up determinant in handle h1
+ * and its down determinant in handle h2 (same batch, same device). Writes
+ * log|det A_up det A_down| = log|det A_up| + log|det A_down| (host or device,
+ * [batch] fp64) and the product of the signs (host or device, [batch] int),
+ * formed on the device on h1's stream after h2's work so far. Synchronises
+ * both handles. ERR_ARG for a null or repeated handle, or handles that differ
+ * in batch or device.
+ */
+int qmcdu_logdet_product(qmcdu_t h1, qmcdu_t h2, double *logabs, int *sign);
+
+/*
  * One Metropolis sweep per walker, entirely on the device: electrons
  * j = 0..N-1 in order; proposal v = a_j + sigma * g (a_j the current row j,
  * g ~ N(0,1)^N); accept iff u < min(1, r^2) (Sec. I); queued moves flushed at
@@ -214,6 +236,22 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
                         unsigned *out, void *stream);
 
 /*
+ * The random draws of one sweep (the a_j + sigma g proposals and the
+ * Metropolis uniforms of Sec. I), exactly as qmcdu_sweep / qmcdu_step draw
+ * them on the device for walkers 0..nwalkers-1 of base seed `base_seed`
+ * (walker w's key base_seed + w) and sweep number `sweep`:
+ *   gauss_out  device [nwalkers][N][N] fp64: row j = the Gaussians g of
+ *              electron j's proposal (Philox4x32-10, Box-Muller pairs)
+ *   unif_out   device [nwalkers][N] fp64: u of electron j
+ * Lets a caller replay a sweep elsewhere (a checkpoint, a reference
+ * implementation) from the very proposals the device used. Allocates nothing;
+ * asynchronous on `stream`. ERR_ARG for N outside 1..QMCDU_MAX_N, a negative
+ * count or sweep, null pointers (text at qmcdu_last_error(NULL)).
+ */
+int qmcdu_proposal_draws(int N, int nwalkers, unsigned long long base_seed, int sweep,
+                         double *gauss_out, double *unif_out, void *stream);
+
+/*
  * Profiling. While enabled, the library records CUDA events on the handle's
  * stream around every flush (Eq. 4) and every recompute, and counts its
  * kernel launches. qmcdu_profile_enable(h, 1) resets the counters; 0 stops.
@@ -235,6 +273,13 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
 int qmcdu_profile_enable(qmcdu_t h, int enable);
 int qmcdu_profile_read(qmcdu_t h, double *out, int n);
 
+/* While profiling is enabled: the device time (ms, CUDA events on the
+ * handle's stream) of each persistent sweep launch since the last enable, in
+ * launch order, into ms_out (host, up to max_n values); *n_out receives the
+ * count written. One launch sweeps every walker of the handle once, so these
+ * are per-sweep latencies. Synchronises. */
+int qmcdu_profile_sweep_times(qmcdu_t h, double *ms_out, int max_n, int *n_out);
+
 /*
  * Options of a handle (value semantics in brackets; 0 restores the default):
  *   QMCDU_OPT_SWEEP_PERSISTENT  [1] qmcdu_sweep runs as one persistent
@@ -253,13 +298,16 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       most the grid cap). Every walker then gets the same arithmetic, in the
  *       same order, whatever the number of walkers in the launch: its results
  *       are bit-identical alone and in a batch (qmcdu_sweep_walkers, serving)
- *   QMCDU_OPT_FP64_FLUSH   [0: auto] the persistent sweep's flush (Eq. 4) for
- *       fp64 walkers: 1 = fp64 arithmetic units only; 2 (and auto) = the
- *       contraction emulated on the tensor cores (operands cut into seven
- *       8-bit slices, exact fp32 accumulation of slice products, exact integer
- *       recombination; near 2^-53 relative to |row| |column|, the error of
- *       fp64 arithmetic) where it applies: 4 <= K <= 32 and walker groups of
- *       two or more CTAs
+ *   QMCDU_OPT_FP64_FLUSH   [0: auto] the flush (Eq. 4) of fp64 walkers: 1 =
+ *       fp64 arithmetic units only; 2 (and auto) = the contraction emulated on
+ *       the tensor cores (operands cut into seven 8-bit slices relative to
+ *       shared exponents after a power-of-two rescaling of every contraction
+ *       index, exact fp32 accumulation of slice products, exact integer
+ *       recombination; the error of fp64 arithmetic, also on matrices whose
+ *       rows and columns span many binades) where it applies: 4 <= K <= 32
+ *       and walker groups of two or more CTAs; also the recompute's rank-32
+ *       updates (on the equilibrated matrix: the recompute scales A's rows
+ *       and columns by powers of two first) where the handle owns the GPU
  *   QMCDU_OPT_CLUSTER      [0: off] persistent sweeps of fp64 walkers (at
  *       most 4 walkers, N >= 1024, no fixed group shape, ratio or flush CTA
  *       counts left automatic): 2 = the 16 ratio CTAs of a walker form one
@@ -268,6 +316,14 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n);
  *       16 ratio CTAs); results agree with the global-memory exchange to
  *       rounding (other sums of the same terms). Slower than the default at
  *       N = 2048 (fp64 work on 16 CTAs instead of 64); 0 and 1 = off
+ *   QMCDU_OPT_FIXED_SLOT   [0: off] 1 = Sec. II's fixed slots in the
+ *       persistent sweep: a rejected proposal also takes a queue slot, as
+ *       an unchanged row (a zero change, which leaves the ratios of later
+ *       proposals and the determinant as they are), so that every walker's
+ *       queue is flushed every K proposals whatever its acceptance. The
+ *       results are those of the default policy (rejected moves take no slot)
+ *       up to rounding. qmcdu_sweep with QMCDU_OPT_SWEEP_PERSISTENT = 0
+ *       returns ERR_STATE while it is set.
  * Returns ERR_ARG for an unknown option or a negative value.
  */
 enum {
@@ -279,7 +335,8 @@ enum {
     QMCDU_OPT_MAX_CTAS = 6,
     QMCDU_OPT_GROUP_CTAS = 7,
     QMCDU_OPT_FP64_FLUSH = 8,
-    QMCDU_OPT_CLUSTER = 9
+    QMCDU_OPT_CLUSTER = 9,
+    QMCDU_OPT_FIXED_SLOT = 10
 };
 int qmcdu_set_option(qmcdu_t h, int option, long long value);
 
@@ -338,32 +395,77 @@ int qmcdu_sweep_walkers(qmcdu_t h, int count, const int *walkers, const unsigned
  * callers for whom cudaMalloc is not an option: code that must not
  * synchronise the device (cudaMalloc can), or code running where another
  * allocator (a framework's caching allocator, a pool reserved up front) owns
- * the device's memory. It computes exactly what qmcdu_ratio computes for one
- * walker, from a delay queue the caller holds, and allocates nothing: its
+ * the device's memory. It computes what qmcdu_ratio computes for one walker
+ * (the change form of Eq. 1-3), from a delay queue the caller holds, and
+ * allocates nothing: its
  * scratch (the CTAs' partial sums and their arrival counter, 131,584 bytes) is
  * a fixed array in the library's device memory, which every GPU that loads
  * the library holds until the process exits.
  *   N          1..8192 electrons;  k  0..min(N, 256) queued moves
  *   ainv_col   device [N]     column j of A^{-1} as of the last flush (j is
  *                             the moving electron, not among the queued ones)
- *   v          device [N]     proposed new row j of A
+ *   u          device [N]     the move's change of row j: u = v - a_j (proposed
+ *                             row minus the current row)
  *   P          device [k][N]  row m: column idx_m of A^{-1} as of the last flush
- *   V          device [k][N]  row m: the new row of queued move m
- *   Kinv       device [k][k]  (V P')^{-1}, row-major (P, V, Kinv may be NULL if k = 0)
- *   ratio_out  device [1]     r = v.a - (P v)' Kinv (V a)
+ *   V          device [k][N]  row m: the change u_m of queued move m
+ *   Kinv       device [k][k]  (I + V P')^{-1}, row-major (P, V, Kinv may be NULL
+ *                             if k = 0)
+ *   ratio_out  device [1]     r = 1 + (u.a - (P u)' Kinv (V a)), a = ainv_col
  *   stream     cudaStream_t (NULL: the legacy default stream)
  * Asynchronous on `stream`. Every call on a device shares the one scratch
  * array, which keeps the last call's contents; each call clears what must
  * start at zero. Calls whose executions overlap on the GPU (concurrent
  * streams, or several host threads) race on the scratch and give wrong
  * results: serialise them. The first call on a device looks up the scratch's
- * device address (once per device, with that device current); make that first
- * call before any stream capture. Errors: ERR_ARG for sizes beyond the limits
+ * device address (once per device, with that device current); under CUDA's
+ * lazy module loading that look-up also loads this library's device code,
+ * which places the scratch array in device memory and may synchronise the
+ * device. Make that first call during the caller's own set-up, before any
+ * stream capture; later calls neither allocate nor synchronise. Errors: ERR_ARG for sizes beyond the limits
  * above or null pointers, ERR_CUDA; the text is at qmcdu_last_error(NULL).
  * No cudaMalloc, cudaFree or allocating library routine is called.
  */
-int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v, const double *P,
+int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *u, const double *P,
                         const double *V, const double *Kinv, double *ratio_out, void *stream);
+
+/*
+ * Multideterminant walkers: the delayed update combined with the table method
+ * of Clark et al. for Psi = sum_I c_I det(A_I) (the extension Sec. II names).
+ * det(A_I) replaces up to two occupied orbital columns o_p of A by virtual
+ * orbital columns a_p; B (N x nv) holds the nv virtual orbitals at the
+ * electrons. The context keeps the table T = A^{-1} B of the CURRENT matrix
+ * (queued moves included) by a rank-1 update per accepted move, from the
+ * current inverse column the delay queue yields, while A^{-1} itself is
+ * updated only at the handle's flushes (Eq. 4). A move's ratio is
+ * R = Psi_new / Psi = sum_I c_I (r det T_I + d_I' adj(T_I) z_I) / S, with r
+ * the reference ratio (Eq. 1/3), z = A_c^{-1} e_j, d = (w - b_j) - T'u and
+ * S = sum_I c_I det(T_I) (no division by r). The table is relative to the
+ * reference determinant: accepting a move with r = 0 is ERR_SINGULAR.
+ * Per-call, on fp64 handles; one context per handle, which it uses through
+ * qmcdu_ratio / qmcdu_accept (call those only through the context while it
+ * exists).
+ *   qmcdu_md_create   exc host [ndet][4] ints (o1, a1, o2, a2; -1 = unused
+ *                     pair, all -1 = the reference), coef host [ndet]
+ *   qmcdu_md_set_virtuals  B host or device [batch][N][nv] fp64: flushes the
+ *                     queue, builds T from the current A^{-1} and S, log|Psi|
+ *                     (recall after a recompute or qmcdu_set_matrix)
+ *   qmcdu_md_ratio    as qmcdu_ratio, plus w device [batch][nv] (the proposed
+ *                     virtual orbital values); ratio_out device [batch]: R;
+ *                     ref_ratio_out device [batch] or NULL: r
+ *   qmcdu_md_accept   as qmcdu_accept, then the table update
+ *   qmcdu_md_logpsi   running log|Psi| and sign (host or device); synchronises
+ * Errors: ERR_ARG (null pointers, excitations outside the orbitals, a
+ * non-fp64 handle), ERR_STATE (ratio before set_virtuals, accept without a
+ * pending ratio), and those of the handle's calls; text at qmcdu_md_last_error.
+ */
+int qmcdu_md_create(qmcdu_t h, int nv, int ndet, const int *exc, const double *coef, qmcdu_md_t *out);
+int qmcdu_md_destroy(qmcdu_md_t m);
+int qmcdu_md_set_virtuals(qmcdu_md_t m, const double *B);
+int qmcdu_md_ratio(qmcdu_md_t m, const int *elec, const double *v, const double *w, double *ratio_out,
+                   double *ref_ratio_out);
+int qmcdu_md_accept(qmcdu_md_t m, const unsigned char *mask);
+int qmcdu_md_logpsi(qmcdu_md_t m, double *logabs, int *sign);
+const char *qmcdu_md_last_error(qmcdu_md_t m);
 
 /*
  * The tensor-core contraction of the fp32 flush (Eq. 4), exposed for direct use

@@ -97,3 +97,14 @@ def lookup(table_path, N, batch, precision, bucket):
         return None
     with open(table_path) as f:
         return json.load(f).get(table_key(N, batch, precision, bucket))
+
+
+def default_K(N, precision="fp64"):
+    """The K the tuner settles on without timing (host only): min(32, N). At
+    fp64 the emulated tensor-core flush takes queues of at most 32 (its 16
+    accumulator blocks of K columns fill tensor memory) and K = 32 was the
+    fastest measured point at every N from 512 to 4096, at both acceptances
+    and in fp32 too (the K sweep of the benchmark). Used where a K must be
+    known before any GPU work, e.g. by a CPU run that reports the same
+    configuration as the device run."""
+    return max(1, min(32, int(N)))

@@ -2,10 +2,10 @@
 // on SIMT cores, and the tile GEMM it shares with the recompute.
 //
 // Row-convention form of Eq. 4: with P = A^{-1}[:, idx] (N x k), V the queued
-// rows (N x k), Kinv = (V'P)^{-1} and E the selector of idx,
-//   A^{-1} <- A^{-1} - (P Kinv) (V' A^{-1} - E').
+// changes u_m = v_m - a_idx_m (N x k) and Kinv = (I + V'P)^{-1},
+//   A^{-1} <- A^{-1} - (P Kinv) (V' A^{-1}).
 // Three launches per flush, each a batched tile GEMM:
-//   T = V' A^{-1} - E'     (k x N, inner dimension N)
+//   T = V' A^{-1}          (k x N, inner dimension N)
 //   W = P Kinv             (N x k, inner dimension k)
 //   A^{-1} -= W T          (N x N, inner dimension k)
 // 4 N^2 k flops per flush of k moves (the same 4 N^2 per accepted move as
@@ -27,8 +27,6 @@ struct GemmArgs {
     int kthresh;        // walkers with k_b < kthresh are skipped (when kdyn)
     double alpha;
     int accumulate;     // C = alpha AB + (accumulate ? C : 0)
-    const int *fix_idx; // C(m, n) -= [n == fix_idx[b*fix_stride + m]]
-    int fix_stride;
 };
 
 constexpr int GTHREADS = 256;
@@ -100,7 +98,6 @@ __global__ void __launch_bounds__(GTHREADS) gemm_tile_kernel(GemmArgs<TA, TB, TC
     for (int a = 0; a < TM; ++a) {
         const int gm = m0 + ty + 16 * a;
         if (gm >= M) continue;
-        const int fix = g.fix_idx ? g.fix_idx[(size_t)b * g.fix_stride + gm] : -1;
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
             const int gn = n0 + tx + 16 * c;
@@ -108,7 +105,6 @@ __global__ void __launch_bounds__(GTHREADS) gemm_tile_kernel(GemmArgs<TA, TB, TC
             TC *dst = Cb + gm * g.sCm + gn * g.sCn;
             Acc v = (Acc)g.alpha * acc[a][c];
             if (g.accumulate) v += (Acc)*dst;
-            if (gn == fix) v -= (Acc)1;
             *dst = (TC)v;
         }
     }
@@ -153,7 +149,7 @@ static cudaError_t launch_flush_t(Ctx &c, int kthresh)
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
     }
-    // T = V' A^{-1} - E':  T(m, n) = sum_i V[m][i] A^{-1}[i][n] - [n == idx_m]
+    // T = V' A^{-1}:  T(m, n) = sum_i V[m][i] A^{-1}[i][n]
     {
         GemmArgs<T, T, T> g{};
         g.A = (const T *)c.V; g.sAb = wK; g.sAm = ld; g.sAl = 1;
@@ -162,7 +158,6 @@ static cudaError_t launch_flush_t(Ctx &c, int kthresh)
         g.M = K; g.Nn = N; g.Kd = N;
         g.kdyn = c.kcount; g.dyn = 1; g.kthresh = kthresh;
         g.alpha = 1.0; g.accumulate = 0;
-        g.fix_idx = c.idx; g.fix_stride = K;
         dim3 grid((N + 31) / 32, (K + 31) / 32, c.batch);
         gemm_tile_kernel<T, T, T, T, 32, 32, true, false><<<grid, GTHREADS, 0, c.stream>>>(g);
     }
@@ -192,9 +187,9 @@ static cudaError_t launch_flush_tc(Ctx &c, int kthresh)
     float *Ainv = (float *)c.Ainv;
     float *Tt = (float *)c.Tbuf;     // T' stored [c][m] (N x K, row length K)
     float *Wb = (float *)c.Wbuf;
-    // T'(c, m) = A^{-1}[:, c] . V[m] - [idx_m == c]
+    // T'(c, m) = A^{-1}[:, c] . V[m]
     cudaError_t e = launch_gemm_bf16x3(N, K, N, Ainv, ld, wN, (const float *)c.V, ld, wK, 0, Tt, K,
-                                       wK, 1.f, 0.f, c.batch, c.kcount, 1, kthresh, c.idx, K,
+                                       wK, 1.f, 0.f, c.batch, c.kcount, 1, kthresh,
                                        c.status, c.opt_budget_ns, c.stream);
     if (e != cudaSuccess) return e;
     {
@@ -213,7 +208,7 @@ static cudaError_t launch_flush_tc(Ctx &c, int kthresh)
     }
     // A^{-1}[:, c] -= sum_m T'(c, m) W[m]   (B operand W read as K x N)
     e = launch_gemm_bf16x3(N, N, K, Tt, K, wK, Wb, ld, wK, 1, Ainv, ld, wN, -1.f, 1.f, c.batch,
-                           c.kcount, 0, kthresh, nullptr, 0, c.status, c.opt_budget_ns, c.stream);
+                           c.kcount, 0, kthresh, c.status, c.opt_budget_ns, c.stream);
     if (e != cudaSuccess) return e;
     flush_reset_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.kcount, kthresh);
     return cudaGetLastError();

@@ -3,8 +3,14 @@
 // ratio_stage_kernel, ratio_dots_kernel, ratio_finish_kernel : determinant
 //                 ratio of one proposal per walker (Eq. 1 at k = 0, Eq. 3
 //                 through the queued panels otherwise). GEMV class: reads
-//                 A^{-1}[:, j], v, the k queued rows of P and V (streamed by
-//                 bulk copies) and the k x k Kinv.
+//                 A^{-1}[:, j], the change u = v - a_j, the k queued rows of
+//                 P and V (streamed by bulk copies) and the k x k Kinv.
+//
+// The change form of the paper (Eq. 1-4): a move of electron j to the new row
+// v changes A by e_j u' with u = v - a_j, and the ratio is 1 + u . A^{-1}[:, j]
+// (Eq. 1). The queue holds the changes of the accepted moves (V row m = u_m),
+// the columns P = A^{-1}[:, idx] of the inverse at the last flush and
+// Kinv = (I + V'P)^{-1}, the inverse of the k x k matrix of Eq. 3.
 // accept_kernel : Metropolis decision (or a given mask), append to the delay
 //                 queue with the bordered k x k inverse update, new row of A,
 //                 running log|det A|.
@@ -88,15 +94,16 @@ struct Vec16<float> {
 
 // The ratio of one proposal per walker (Eq. 1 at k = 0, Eq. 3 through the
 // queued panels otherwise) in three launches:
-//   ratio_stage_kernel   v and A^{-1}[:, j] into slot k of V and P (the slot a
-//                        subsequent accept fills; the rows the dots read)
+//   ratio_stage_kernel   u and A^{-1}[:, j] into slot k of V and P (the slot a
+//                        subsequent accept fills; the rows the dots read),
+//                        v (fp64) into the stash the accept copies into A
 //   ratio_dots_kernel    the 2k+1 full-row dot products of every walker,
-//                          d = v . A^{-1}[:, j],  b_m = P[m] . v,  c_m = V[m] . A^{-1}[:, j]:
+//                          d = u . A^{-1}[:, j],  b_m = P[m] . u,  c_m = V[m] . A^{-1}[:, j]:
 //                        grid-stride over (walker, row), one warp per row, so
 //                        that every warp streams rows from HBM the whole time
 //   ratio_finish_kernel  per walker: x = Kinv c and y = Kinv' b in one
-//                        coalesced pass over Kinv, r = d - b' Kinv c (the
-//                        Schur complement of the bordered V'P, Eq. 3)
+//                        coalesced pass over Kinv, r = 1 + (d - b' Kinv c)
+//                        (the Schur complement of the bordered I + V'P, Eq. 3)
 // Rows are padded to ld with zeros (nothing writes past N), so 16-byte vectors
 // that reach into the padding add nothing.
 
@@ -117,27 +124,28 @@ __global__ void __launch_bounds__(RTHREADS) ratio_stage_kernel(RatioParams<T> p)
     T *Vk = p.V + b * wK + (size_t)k * ld;
     const int i0 = blockIdx.x * (2 * RTHREADS);
     for (int i = i0 + threadIdx.x; i < min(N, i0 + 2 * RTHREADS); i += RTHREADS) Pk[i] = acol[i];
+    const double *arow = p.A + b * wN + (size_t)j * ld;
+    double *vst = p.vstash + (size_t)b * ld;
     if (p.generate) {
         // v = a_j + sigma g, g from Philox / Box-Muller in pairs
-        const double *arow = p.A + b * wN + (size_t)j * ld;
         const unsigned long long wseed = p.seed + (unsigned long long)b;
         const int i = i0 + 2 * threadIdx.x;
         if (i < N) {
             const double2 g = proposal_gaussian_pair(wseed, j, p.sweep, i >> 1);
-            const double v0 = arow[i] + p.sigma * g.x;
-            Vk[i] = (T)v0;
-            if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i] = v0;
+            const double v0 = __dadd_rn(arow[i], __dmul_rn(p.sigma, g.x));
+            Vk[i] = (T)__dsub_rn(v0, arow[i]);
+            vst[i] = v0;
             if (i + 1 < N) {
-                const double v1 = arow[i + 1] + p.sigma * g.y;
-                Vk[i + 1] = (T)v1;
-                if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i + 1] = v1;
+                const double v1 = __dadd_rn(arow[i + 1], __dmul_rn(p.sigma, g.y));
+                Vk[i + 1] = (T)__dsub_rn(v1, arow[i + 1]);
+                vst[i + 1] = v1;
             }
         }
     } else {
         for (int i = i0 + threadIdx.x; i < min(N, i0 + 2 * RTHREADS); i += RTHREADS) {
             const double v0 = p.v_in[(size_t)b * N + i];
-            Vk[i] = (T)v0;
-            if (!std::is_same<T, double>::value) p.vstash[(size_t)b * ld + i] = v0;
+            Vk[i] = (T)__dsub_rn(v0, arow[i]);
+            vst[i] = v0;
         }
     }
 }
@@ -384,7 +392,7 @@ __global__ void __launch_bounds__(RTHREADS) ratio_finish_kernel(RatioParams<T> p
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int pp = 0; pp < kparts; ++pp) s += __ldcg(s0 + (size_t)pp * (K + 1) + K);
-        const double r = d - s;
+        const double r = 1.0 + (d - s);
         rec[0] = d;
         rec[1] = r;
         rec[2] = (double)k;
@@ -427,8 +435,8 @@ constexpr int ACHUNK = 1024;
 // row into A.
 //
 // Bordered inverse (Sec. II, Eq. 3-4 in the row convention): with
-// B_k = V'P, the proposal borders it as [[B_k, c], [b', d]] whose Schur
-// complement is r, so with x = Kinv c and y = Kinv' b
+// B_k = I + V'P, the proposal borders it as [[B_k, c], [b', 1 + d]] whose
+// Schur complement is r, so with x = Kinv c and y = Kinv' b
 //   Kinv' = [[Kinv + x y'/r, -x/r], [-y'/r, 1/r]].
 template <typename T>
 __global__ void __launch_bounds__(ATHREADS) accept_kernel(AcceptParams<T> p)
@@ -460,16 +468,11 @@ __global__ void __launch_bounds__(ATHREADS) accept_kernel(AcceptParams<T> p)
     if (blockIdx.x == 0 && threadIdx.x == 0) p.acc[b] = (unsigned char)a;
     if (!a) return;
 
-    // New row of A (fp64).
+    // New row of A (fp64, the stash of the proposed row).
     const int i0 = blockIdx.x * ACHUNK, i1 = min(N, i0 + ACHUNK);
     double *arow = p.A + (size_t)b * N * ld + (size_t)j * ld;
-    if (std::is_same<T, double>::value) {
-        const T *vk = p.V + ((size_t)b * K + k) * ld;
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) arow[i] = (double)vk[i];
-    } else {
-        const double *vs = p.vstash + (size_t)b * ld;
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) arow[i] = vs[i];
-    }
+    const double *vs = p.vstash + (size_t)b * ld;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) arow[i] = vs[i];
     if (blockIdx.x != 0) return;
 
     if (K > 1) {
@@ -496,9 +499,10 @@ __global__ void __launch_bounds__(ATHREADS) accept_kernel(AcceptParams<T> p)
     }
 }
 
-// K = 1 (Eq. 2 in the row convention): with u = A^{-1}[:, j] (the P slot copy
-// taken by the ratio kernel) and w_c = v . A^{-1}[:, c],
-//   A^{-1}[:, c] -= u (w_c - [c == j]) / r    for every column c.
+// K = 1 (Eq. 2 in the row convention): with p = A^{-1}[:, j] (the P slot copy
+// taken by the ratio kernel) and w_c = u . A^{-1}[:, c] (u = v - a_j, the V
+// slot),
+//   A^{-1}[:, c] -= p w_c / r    for every column c.
 // One warp per column: a dot product then an axpy over the same column, a
 // single pass over A^{-1} (2 N^2 elements moved per accepted move).
 constexpr int SMTHREADS = 256;
@@ -515,15 +519,14 @@ __global__ void __launch_bounds__(SMTHREADS) sm_update_kernel(int N, int ld, T *
     const int lane = threadIdx.x & 31;
     const double *rec = rs + (size_t)b * rs_stride(K);
     const double r = rec[1];
-    const int j = (int)rec[3];
     T *col = Ainv + (size_t)b * N * ld + (size_t)c * ld;
-    const T *u = P + (size_t)b * K * ld;
-    const T *v = V + (size_t)b * K * ld;
+    const T *pcol = P + (size_t)b * K * ld;
+    const T *ucol = V + (size_t)b * K * ld;
     T w = 0;
-    for (int i = lane; i < N; i += 32) w += __ldg(v + i) * col[i];
+    for (int i = lane; i < N; i += 32) w += __ldg(ucol + i) * col[i];
     w = warp_sum(w);
-    const T f = (T)(((double)w - (c == j ? 1.0 : 0.0)) / r);
-    for (int i = lane; i < N; i += 32) col[i] -= __ldg(u + i) * f;
+    const T f = (T)((double)w / r);
+    for (int i = lane; i < N; i += 32) col[i] -= __ldg(pcol + i) * f;
 }
 
 template <typename T>
@@ -593,6 +596,25 @@ cudaError_t launch_sm_update(Ctx &c)
 }
 
 // ---------------------------------------------------------------- utilities
+// A walker of two determinants (spin up and spin down): log|det| of the
+// product is the sum, its sign the product of the signs.
+__global__ void logdet_pair_kernel(int batch, const double *l1, const int *s1, const double *l2,
+                                   const int *s2, double *lout, int *sout)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    lout[b] = l1[b] + l2[b];
+    sout[b] = s1[b] * s2[b];
+}
+
+cudaError_t launch_logdet_pair(int batch, const double *l1, const int *s1, const double *l2, const int *s2,
+                               double *lout, int *sout, cudaStream_t s)
+{
+    if (batch <= 0) return cudaSuccess;
+    logdet_pair_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, l1, s1, l2, s2, lout, sout);
+    return cudaGetLastError();
+}
+
 __global__ void philox_fill_kernel(const unsigned *c0, const unsigned *c1, const unsigned *c2,
                                    const unsigned *c3, int n, unsigned long long seed,
                                    unsigned *out)

@@ -10,12 +10,19 @@
 //     in place (S the row interchanges), and X^{-1} = (S X)^{-1} S is a column
 //     permutation of it; X^{-1} = A^{-T} stored row-major is A^{-1} stored
 //     column-major.
+// Equilibration: A' = D_r A D_c with power-of-two scales (each row's largest
+// element into [1, 2), then each column's), so that X = A'' has no rows or
+// columns many binades apart (which the emulated-fp64 rank-nb update, and
+// partial pivoting, handle poorly); A^{-1} = D_c A'^{-1} D_r and
+// log|det A| = log|det A'| - log|det D_r D_c| are exact.
 // Blocking: for a panel of nb columns, one CTA per walker eliminates the panel
 // (all N rows, panel staged in shared memory) -- or, for a few walkers, P CTAs
 // per walker split the rows (gj_panel_mc_kernel, kernels_sweep.cu) -- then every
 // other column gets the panel's transformation as one rank-nb update,
 // X += (Mp - E) X_p, with Mp the eliminated panel and X_p the panel's pivot
-// rows. 2 N^3 flops in all.
+// rows: for fp64 handles on the tensor cores, emulated in fp64 by the flush's
+// slice products (kernels_sweep.cu, oz_gj_update_kernel), otherwise a SIMT
+// tile GEMM. 2 N^3 flops in all.
 #include <math.h>
 
 #include <algorithm>
@@ -61,17 +68,80 @@ static bool use_gj_mc(const Ctx &c)
     return c.gj_ctas > 0 && c.opt_group_ctas == 0 && c.opt_max_ctas == 0;
 }
 
-// work[b][i][x] = A[b][x][i]  (X = A'); padding stays zero.
-__global__ void transpose_kernel(int N, int ld, const double *A, double *work)
+__device__ __forceinline__ int rc_bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+constexpr int EQ_NONE = -(1 << 30);
+
+// Row scales: sr[x] = 1023 - (largest biased exponent of row x) (0 for a zero
+// row), one warp per row; the column maxima start empty.
+__global__ void eq_rows_kernel(int N, int ld, const double *A, int *eqs)
+{
+    const int b = blockIdx.y;
+    const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (x >= N) return;
+    const double *row = A + ((size_t)b * N + x) * ld;
+    unsigned e = 0;
+    for (int i = lane; i < N; i += 32) e = max(e, (unsigned)rc_bexp(row[i]));
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (lane == 0) {
+        eqs[(size_t)b * 2 * N + x] = e ? 1023 - (int)e : 0;
+        eqs[(size_t)b * 2 * N + N + x] = EQ_NONE;
+    }
+}
+
+// Column maxima of the row-scaled matrix, max_x (E(A[x][i]) + sr[x]) over the
+// nonzero elements: CTA (cx, rx) takes columns [128 cx, +128) of rows
+// [64 rx, +64).
+__global__ void eq_cols_kernel(int N, int ld, const double *A, int *eqs)
+{
+    const int b = blockIdx.z;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = blockIdx.y * 64, x1 = min(N, x0 + 64);
+    const int *sr = eqs + (size_t)b * 2 * N;
+    int *cm = eqs + (size_t)b * 2 * N + N;
+    if (i >= N) return;
+    const double *Ab = A + (size_t)b * N * ld;
+    int e = EQ_NONE;
+    for (int x = x0; x < x1; ++x) {
+        const int be = rc_bexp(Ab[(size_t)x * ld + i]);
+        if (be) e = max(e, be + sr[x]);
+    }
+    if (e > EQ_NONE) atomicMax(cm + i, e);
+}
+
+// Column scales sc[i] = 1023 - (the column maximum) (0 for a zero column) and
+// the log-det correction -ln 2 (sum sr + sum sc), added to the recompute's
+// pivot sum; one CTA per walker, fixed summation order.
+__global__ void eq_logdet_kernel(int N, int *eqs, double *lu_logabs)
+{
+    const int b = blockIdx.x;
+    __shared__ long long part[256];
+    int *sc = eqs + (size_t)b * 2 * N + N;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) sc[t] = sc[t] == EQ_NONE ? 0 : 1023 - sc[t];
+    __syncthreads();
+    long long s = 0;
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) s += eqs[(size_t)b * 2 * N + t];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int q = 0; q < (int)blockDim.x; ++q) tot += part[q];
+        lu_logabs[b] -= 0.69314718055994530942 * (double)tot;
+    }
+}
+
+// work[b][i][x] = A'[b][x][i] = A[b][x][i] 2^(sr[x] + sc[i])  (X = A''); padding stays zero.
+__global__ void transpose_kernel(int N, int ld, const double *A, const int *eqs, double *work)
 {
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const int x0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
     const double *Ab = A + (size_t)b * N * ld;
     double *Wb = work + (size_t)b * N * ld;
+    const int *sr = eqs + (size_t)b * 2 * N, *sc = sr + N;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int row = i0 + r, col = x0 + threadIdx.x;   // read A[row][col]
-        if (row < N && col < N) tile[r][threadIdx.x] = Ab[(size_t)row * ld + col];
+        if (row < N && col < N) tile[r][threadIdx.x] = ldexp(ldexp(Ab[(size_t)row * ld + col], sr[row]), sc[col]);
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -228,18 +298,21 @@ __global__ void colperm_kernel(int N, int batch, const int *piv, int *colperm)
     }
 }
 
-// A^{-1} (working precision) from the eliminated matrix, with drift sums.
+// A^{-1} (working precision) from the eliminated matrix, with drift sums:
+// column r of A^{-1} is row r of X^{-1} = A'^{-T}, element x scaled back by
+// 2^(sc[x] + sr[r]) (A^{-1} = D_c A'^{-1} D_r).
 template <typename T>
-__global__ void gather_kernel(int N, int ld, const double *work, const int *colperm, T *Ainv,
+__global__ void gather_kernel(int N, int ld, const double *work, const int *colperm, const int *eqs, T *Ainv,
                               double *drift, int have_old)
 {
     const int b = blockIdx.z, r = blockIdx.y;
     const double *src = work + ((size_t)b * N + r) * ld;
     const int *cp = colperm + (size_t)b * N;
+    const int *sr = eqs + (size_t)b * 2 * N, *sc = sr + N;
     T *dst = Ainv + ((size_t)b * N + r) * ld;
     double dsq = 0.0, nsq = 0.0;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        const double v = src[cp[x]];
+        const double v = ldexp(ldexp(src[cp[x]], sc[x]), sr[r]);
         if (have_old) {
             const double o = (double)dst[x];
             dsq += (o - v) * (o - v);
@@ -300,11 +373,14 @@ cudaError_t launch_init_matrix(Ctx &c, int w0, int n, const unsigned long long *
 cudaError_t launch_recompute(Ctx &c, int have_old)
 {
     const int N = c.N, ld = c.ld;
+    lu_init_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.lu_logabs, c.lu_sign, c.drift);
+    eq_rows_kernel<<<dim3((N + 7) / 8, c.batch), 256, 0, c.stream>>>(N, ld, c.A, c.eqs);
+    eq_cols_kernel<<<dim3((N + 127) / 128, (N + 63) / 64, c.batch), 128, 0, c.stream>>>(N, ld, c.A, c.eqs);
+    eq_logdet_kernel<<<c.batch, 256, 0, c.stream>>>(N, c.eqs, c.lu_logabs);
     {
         dim3 grid((N + 31) / 32, (N + 31) / 32, c.batch);
-        transpose_kernel<<<grid, dim3(32, 8), 0, c.stream>>>(N, ld, c.A, c.work);
+        transpose_kernel<<<grid, dim3(32, 8), 0, c.stream>>>(N, ld, c.A, c.eqs, c.work);
     }
-    lu_init_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.lu_logabs, c.lu_sign, c.drift);
     const bool mc = use_gj_mc(c);
     const int pw = mc ? c.nb : c.nb1;                       // panel width of this launch
     const size_t smem = (size_t)N * c.nb1 * sizeof(double);
@@ -326,17 +402,18 @@ cudaError_t launch_recompute(Ctx &c, int have_old)
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return e;
-        e = launch_gj_update(c, nbe);
+        e = launch_gj_update_oz(c, nbe);
+        if (e == cudaErrorNotSupported) e = launch_gj_update(c, nbe);
         if (e != cudaSuccess) return e;
     }
     colperm_kernel<<<(c.batch + 127) / 128, 128, 0, c.stream>>>(N, c.batch, c.piv, c.colperm);
     {
         dim3 grid((N + 255) / 256, N, c.batch);
         if (c.prec == QMCDU_FP64)
-            gather_kernel<double><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm,
+            gather_kernel<double><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm, c.eqs,
                                                              (double *)c.Ainv, c.drift, have_old);
         else
-            gather_kernel<float><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm,
+            gather_kernel<float><<<grid, 256, 0, c.stream>>>(N, ld, c.work, c.colperm, c.eqs,
                                                             (float *)c.Ainv, c.drift, have_old);
     }
     lu_finish_kernel<<<(c.batch + 255) / 256, 256, 0, c.stream>>>(c.batch, c.logabs, c.sign,

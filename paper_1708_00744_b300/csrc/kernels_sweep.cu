@@ -8,19 +8,22 @@
 // helpers) apply the flush of Eq. 4, each to its own block of columns of
 // A^{-1}. Groups never wait on one another.
 //
-// Delay queue. Instead of the k x k inverse Kinv = (V'P)^{-1} the kernel keeps
-// its product with the panel, W = P Kinv (N x k), which is the operand the
-// flush needs. The bordered-inverse algebra of Eq. 3-4 carries over: with
-// a = A^{-1}[:, j], d = v.a, y = W'v, c = V'a,
-//   r  = d - y.c                            (ratio of the proposal, Eq. 3)
+// Delay queue, in the paper's change form (Eq. 1-4). A move of electron j to
+// the new row v changes A by the rank-1 term e_j u' with u = v - a_j; the
+// queue keeps the changes of the k accepted moves as the rows of V (Delta'),
+// the columns P = A^{-1}[:, idx] of the inverse at the last flush and, instead
+// of the k x k inverse Kinv = (I + V'P)^{-1} of Eq. 3, its product with the
+// panel, W = P Kinv (N x k), which is the operand the flush needs. With
+// a = A^{-1}[:, j], d = u.a, y = W'u, c = V'a the bordered-inverse algebra gives
+//   r  = 1 + (d - y.c)                      (ratio of the proposal, Eq. 1/3)
 //   z  = a - W c,   W <- [W - z y'/r, z/r]   (append on accept)
 // so every step is an N-parallel dot product or axpy over the row chunks, with
 // no k x k work on the critical path. When a ratio CTA's rows of W and V fit,
 // they stay in its shared memory for the whole sweep (RES) and are written to
 // global memory only for a flush.
 //
-// Flush (column c of the column-major A^{-1}, T = V'A^{-1} - E'):
-//   t_m = V[m] . A^{-1}[:, c] - [idx_m == c],   A^{-1}[:, c] -= sum_m t_m W[m].
+// Flush (column c of the column-major A^{-1}, T = V'A^{-1}, Eq. 4):
+//   t_m = V[m] . A^{-1}[:, c],   A^{-1}[:, c] -= sum_m t_m W[m].
 // Four implementations, chosen per flush: flush_columns_small (k < 4, K = 1's
 // Sherman-Morrison), flush_block (fp64 column blocks >= 64 wide: a
 // register-tiled GEMM), flush_tc (split-bf16 walkers: tcgen05 with the
@@ -66,7 +69,7 @@ struct SweepParams {
     int *idx, *kglob;
     const double *gauss;    // [batch][N][ld] proposal Gaussians of this sweep
     const double *unif;     // [batch][N] Metropolis uniforms of this sweep
-    double *partial;        // [ngroups][2][Gr][2K+1] tagged (hi, lo) words
+    double *partial;        // [ngroups][2][Gr][2K+2] tagged (hi, lo) words (slot 2K+1: row padding)
     unsigned *sync;         // [ngroups][SYNC_STRIDE]: a spare line (the proposals exchange tagged
                             // partials instead of a barrier), the flush barrier and the flush
                             // command, each on its own 128-byte line
@@ -88,6 +91,7 @@ struct SweepParams {
     size_t oz_stride;               // bytes per walker group
     int off_tcbar;                  // the tensor-core flush's mbarriers (offset in shared memory)
     int off_cl;                     // cluster mode: [2][2K+1] partial dot products, then a flag
+    int fixed_slot;                 // rejected proposals take queue slots (zero changes)
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -250,6 +254,13 @@ __device__ __forceinline__ unsigned long long ld_tagged(const double *src)
     return w;
 }
 __device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32) & 3u; }
+// 16 bytes global -> shared, asynchronous, through L2 only (no stale L1 line
+// can answer a repeated copy of a polled word)
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)), "l"(src) : "memory");
+}
 __device__ __forceinline__ float2 untag(unsigned long long w)
 {
     return make_float2(__uint_as_float((unsigned)w), __uint_as_float((unsigned)(w >> 32) & ~3u));
@@ -291,7 +302,6 @@ __device__ void flush_columns_small_k(const SweepParams<T> &p, int w, int c_begi
     T *Ab = p.Ainv + (size_t)w * wN;
     const T *Vb = p.V + (size_t)w * wK;
     const T *Wb = p.W + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ T part[SWARPS][SCB * SMALL_K];
     __shared__ T tsum[SCB * SMALL_K];
@@ -331,7 +341,6 @@ __device__ void flush_columns_small_k(const SweepParams<T> &p, int w, int c_begi
             if (c < nc && m < KK) {
 #pragma unroll
                 for (int q = 0; q < SWARPS; ++q) sum += part[q][threadIdx.x];
-                if (__ldcg(idxw + m) == cb + c) sum -= (T)1;
             }
             tsum[threadIdx.x] = sum;
         }
@@ -379,7 +388,7 @@ __device__ __noinline__ void flush_columns_small_ool(const SweepParams<T> &p, in
 //   T' = V A^{-1}[:, tile]: rows i in chunks of BI1 = 32, V^t and the tile's rows
 //        staged in shared memory (row stride BT + 1: the transposing stores hit
 //        distinct banks), each thread a 4 x 4 block of (m, c);
-//   T  = T' - E^t (selector), kept in shared memory;
+//   T  = T' kept in shared memory;
 //   A^{-1}[:, tile] -= W^t T: rows i in chunks of BI2 = 64, W staged, each thread
 //        a 4 x 4 block of (i, c) with the lanes along i, so that a half-warp's
 //        read-modify-write of a column is 64 consecutive rows.
@@ -395,7 +404,6 @@ __device__ void flush_block(const SweepParams<T> &p, int w, int k, int c_begin, 
     T *Ab = p.Ainv + (size_t)w * wN;
     const T *Vb = p.V + (size_t)w * wK;
     const T *Wb = p.W + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     T *Vs = (T *)(smem + p.off_xs);        // [BI1][SLD] : V^t chunk, Vs[ci][m]
     T *As = Vs + BI1 * SLD;                // [BI1][SLD] : A^{-1} chunk, As[ci][c]
     T *Ts = Vs;                            // [BT][BT]   : T[m][c] (after phase 1)
@@ -433,15 +441,14 @@ __device__ void flush_block(const SweepParams<T> &p, int w, int k, int c_begin, 
             }
         }
         __syncthreads();
-        // ---- T = T' - E^t into shared memory
+        // ---- T = Delta' A^{-1} into shared memory
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int m = ty * 4 + u;
-            const int im = m < k ? __ldcg(idxw + m) : -1;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int c = tx * 4 + v;
-                Ts[m * BT + c] = (m < k && c < nc) ? acc[u][v] - (im == c0 + c ? (T)1 : (T)0) : (T)0;
+                Ts[m * BT + c] = (m < k && c < nc) ? acc[u][v] : (T)0;
             }
         }
         // ---- phase 2: A^{-1}[i][c0 + c] -= sum_m W[m][i] T[m][c]   (i = tx*4+u, c = ty*4+v)
@@ -498,7 +505,6 @@ __device__ bool flush_columns(const SweepParams<T> &p, int w, int k, int c_begin
     T *Ab = p.Ainv + (size_t)w * wN;
     const T *Vb = p.V + (size_t)w * wK;
     const T *Wb = p.W + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c0 = c_begin; c0 < c_end; c0 += cb) {
         const int nc = min(cb, c_end - c0);
@@ -554,12 +560,10 @@ __device__ bool flush_columns(const SweepParams<T> &p, int w, int k, int c_begin
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int m = mb + r;
-                const int im = m < k ? __ldcg(idxw + m) : -1;
 #pragma unroll
                 for (int cc = 0; cc < MAX_CB; ++cc) {
                     const T v = warp_allsum(acc[r][cc]);
-                    if (lane == 0 && cc < nc && m < k)
-                        ts[m * cb + cc] = v - (im == c0 + cc ? (T)1 : (T)0);
+                    if (lane == 0 && cc < nc && m < k) ts[m * cb + cc] = v;
                 }
             }
         }
@@ -678,7 +682,7 @@ __device__ __forceinline__ void split8(const float *x, uint4 &hi, uint4 &lo)
 //   T'[c][m] = sum_i A^{-1}[i][c] V[m][i]   M = 128 columns, N = kp, K = N in
 //       blocks of 32; the CTA splits the next block's operands (eight elements per
 //       thread, 16-byte stores) while the MMAs of the current one run;
-//   T = T' - E^t, read back from tensor memory into the B operand of
+//   T = T', read back from tensor memory into the B operand of
 //   D[i][c] = sum_m W[m][i] T[m][c]        M = 128 rows i, N = 128 columns, K = kp;
 //       the W block of the next 128 rows is split while the MMAs run, and with
 //       the rows of A^{-1} along the tensor-memory lanes the read-modify-write
@@ -705,7 +709,6 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
     T *Ab = p.Ainv + (size_t)w * wN;
     const T *Vb = p.V + (size_t)w * wK;
     const T *Wb = p.W + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kp = (k + 15) / 16 * 16;
     const uint32_t id1 = idesc(BM, kp), id2 = idesc(BM, BM);
@@ -819,7 +822,7 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
         for (int s = 0; s < 2; ++s)
             if (pend[s] && !wait_bar(s)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- T = T' - E' into shared memory (rows c, K = m): the update's B operand
+        // ---- T = T' into shared memory (rows c, K = m): the update's B operand
         if (warp < 4) {
             const int c = warp * 32 + lane;
             for (int m0 = 0; m0 < kp; m0 += 16) {
@@ -831,9 +834,7 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int m = m0 + half * 8 + j;
-                        t[j] = m < k ? __uint_as_float(v[half * 8 + j]) -
-                                           (__ldcg(idxw + m) == c0 + c ? 1.f : 0.f)
-                                     : 0.f;
+                        t[j] = m < k ? __uint_as_float(v[half * 8 + j]) : 0.f;
                     }
                     uint4 hi, lo;
                     split8(t, hi, lo);
@@ -904,6 +905,17 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
 // (Emax: the largest biased exponent of the set):
 //   q = round(|x| 2^(1078 - Emax)) < 2^56,  q = sum_j s_j 2^(48 - 8j),
 //   x ~ sign(x) 2^(Emax - 1078) q            (56 bits of every operand).
+// An element far below the largest of its set keeps few of those bits, which
+// matters where its partner in the contraction is correspondingly large (a
+// matrix whose orbitals, or electrons, span many binades). So each
+// contraction index is first scaled by a power of two on both sides, which
+// leaves every product unchanged: row i of A^{-1} by 2^-s_i and column i of
+// V by 2^s_i, with s_i chosen to make the scaled queued changes uniform in i
+// (oz_colexp_init: a move that changes orbital i by D_i makes A^{-1}'s row i
+// carry 1/D_i); queue entry m of W and T by 2^f_m and
+// 2^-f_m, with f_m from the column exponent of A^{-1} at the queued electron
+// (a scaling of the electrons' rows). The shared exponents are those of the
+// scaled values; an element's own slicing exponent adds its index's shift.
 // A slice is an integer of magnitude <= 255, exact in fp16, and the product of
 // two slices is an integer <= 65025; a tcgen05 MMA with fp32 accumulation sums
 // such products without rounding while every partial sum stays below 2^24.
@@ -924,7 +936,7 @@ __device__ bool flush_tc(const SweepParams<T> &p, int w, int k, int c_begin, int
 //      d <= 3 (exact: 256 x 65025 < 2^24), d = 4..6 spread over two blocks
 //      each (their fp32 rounding lies below 2^-53 of the result); partials as
 //      an exact int64 and an fp32 tail.
-//   B  T = sum of the partials (integers, fixed order) - E', sliced with one
+//   B  T = sum of the partials (integers, fixed order), sliced with one
 //      exponent per column c; W = P Kinv sliced with one exponent per row i;
 //      the slices are written in the tensor cores' K-major tile layout.
 //   C  A^{-1}[i][c] -= sum_m W[m][i] T[m][c]: items of 128 rows x 64 columns,
@@ -941,13 +953,16 @@ constexpr int CM = 128, CN = 64;                // phase C item: rows, columns
 constexpr int TMEM_COLS = 512;
 
 struct Layout {
-    size_t part, partg, wsl, tsl, wex, tex, cex, vex, bytes;
+    size_t part, partg, wsl, tsl, wex, tex, cex, vex, rex, fex, vsl, bytes;
     int nrc, nca, nrb, nct;
 };
 // per walker-group scratch: partial T' [nrc][nca*AM][kp] as exact int64 sums
 // of the d <= 3 diagonals and fp32 sums of d = 4, 5; slices of W
 // [nrb][NS][CM*kp] and of T [nct][NS][CN*kp] fp16; exponents of W rows, T
-// columns, A^{-1} columns (cex) and V rows (vex)
+// columns, A^{-1} columns (cex) and V rows (vex), all of the scaled values;
+// the row shifts s_i (rex) and the queue shifts f_m (fex); the slices of V
+// [nrc*AR/AK][NS][kp*AK] fp16, one block of AK rows after another in phase
+// A's shared-memory layout
 __host__ __device__ inline Layout layout(int N, int kp)
 {
     Layout L;
@@ -964,21 +979,25 @@ __host__ __device__ inline Layout layout(int N, int kp)
     L.tex = o;  o += (size_t)L.nct * CN * sizeof(int);
     L.cex = o;  o += (size_t)L.nca * AM * sizeof(int);
     L.vex = o;  o += 64 * sizeof(int);
+    L.rex = o;  o += ((size_t)L.nca * AM + 2) * sizeof(int);
+    L.fex = o;  o += 64 * sizeof(int);
+    o = (o + 255) / 256 * 256;
+    L.vsl = o;  o += (size_t)L.nrc * (AR / AK) * NS * kp * AK * 2;
     L.bytes = (o + 255) / 256 * 256;
     return L;
 }
-// shared memory: phase A's NSLOT raw fp64 K-blocks (A^{-1} columns, then V
-// rows) and two stages of their slices; phase C reuses it for one W tile, two
+// shared memory: phase A's NSLOT raw fp64 K-blocks of A^{-1} columns, two
+// stages of their slices and NSLOT blocks of V's slices; phase C reuses it for one W tile, two
 // T tiles and two blocks of column exponents; then eight mbarriers (0, 1:
 // phase A stages free again; 2: phase C MMAs; 3: W tile; 4, 5: T tiles; 6, 7:
 // phase A stages full)
 constexpr int NBAR = 8;
 // arrivals per phase: 6, 7 are phase A's stage-full barriers (one per warp)
 __host__ __device__ inline unsigned bar_count(int q) { return q >= 6 ? 8u : 1u; }
-__host__ __device__ inline size_t raw_bytes(int kp) { return (size_t)(AM + kp) * AK * sizeof(double); }
+__host__ __device__ inline size_t raw_bytes(int) { return (size_t)AM * AK * sizeof(double); }
 __host__ __device__ inline size_t phase_a_bytes(int kp)
 {
-    return NSLOT * raw_bytes(kp) + (size_t)2 * NS * (AM + kp) * AK * 2;
+    return NSLOT * raw_bytes(kp) + (size_t)2 * NS * AM * AK * 2 + (size_t)NSLOT * NS * kp * AK * 2;
 }
 __host__ __device__ inline size_t phase_c_bytes(int kp)
 {
@@ -992,6 +1011,9 @@ __host__ __device__ inline size_t bar_offset(int kp)
 __host__ __device__ inline size_t region_bytes(int kp) { return bar_offset(kp) + NBAR * sizeof(unsigned long long); }
 
 __device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+// x != 0 as an integer test (an fp64 compare would take the fp64 pipe, which
+// retires two lanes per clock per SM)
+__device__ __forceinline__ bool nz(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull; }
 
 // 56-bit magnitude q = round(|x| 2^(1078 - emax)) of x relative to the set's
 // largest biased exponent emax (|x| < 2^(emax - 1022)), clamped to 2^56 - 1,
@@ -1027,12 +1049,13 @@ __device__ __forceinline__ uint32_t slice_pair(uint32_t qh0, uint32_t ql0, uint3
     h = __hsub2(h, *reinterpret_cast<const __half2 *>(&base));
     return *reinterpret_cast<const uint32_t *>(&h);
 }
-// eight values with one exponent: plane j of the slices as eight packed fp16
-__device__ __forceinline__ void slice8(const double (&x)[8], int emax, uint4 (&out)[NS])
+// eight values, value e relative to exponent emax[e]: plane j of the slices
+// as eight packed fp16
+__device__ __forceinline__ void slice8(const double (&x)[8], const int (&emax)[8], uint4 (&out)[NS])
 {
     uint32_t qh[8], ql[8], ng[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) mag56(x[e], emax, qh[e], ql[e], ng[e]);
+    for (int e = 0; e < 8; ++e) mag56(x[e], emax[e], qh[e], ql[e], ng[e]);
     uint32_t sg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) sg[q] = 0x64006400u | (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
@@ -1093,27 +1116,59 @@ __device__ constexpr MmaC kMmaC[NMMA_C] = {
     {2, 4, 1, 0}, {3, 0, 4, 0}, {4, 0, 3, 0}, {5, 0, 2, 0}, {6, 0, 1, 0}};
 }  // namespace ozf
 
-// Column exponents of walker w's A^{-1} (largest biased exponent per column),
-// computed by all CTAs of the group at the start of the walker's sweep; every
-// emulated flush then keeps them up to date (phase C). A flush by
-// flush_columns_small, which does not, only ends a sweep.
+// Slicing exponents of walker w's A^{-1}, computed by all CTAs of the group at
+// the start of the walker's sweep (and by the per-call flush): first the row
+// shifts s_i, then, after a group barrier, the column exponents of the
+// shifted values, max_i (E(x_ic) - s_i) over the nonzero elements. Phase A
+// slices 2^-s_i A^{-1}_ic per column and 2^s_i u_i per queued change, so that
+// the shift cancels in every product. A term keeps its precision when both
+// factors sit near their shared maxima; the shift that achieves this for the
+// terms u_i A^{-1}_ic is the one that makes the scaled changes uniform in i:
+// s_i = 1023 - max_m E(V[m][i]) over the queued changes (Vq, kq rows), which
+// the per-call flush knows when it runs. (Scaling A^{-1}'s rows to a common
+// size instead loses the small entries of a row dominated by one large one,
+// as ill-conditioned walks make them.) The persistent sweep's changes are
+// sigma g for one scalar sigma, already uniform in i: it passes Vq = nullptr
+// and s_i = 0. Every emulated flush then keeps the column exponents up to
+// date (phase C) with the same shifts. A flush by flush_columns_small, which
+// does not, only ends a sweep. Returns false after the barrier's wait ran
+// out of budget.
 template <typename T>
-__device__ void oz_colexp_init(const SweepParams<T> &p, int w, int grp, int rank)
+__device__ bool oz_colexp_init(const SweepParams<T> &p, int w, int grp, int rank, unsigned *flush_ctr,
+                               unsigned &n_flush, const double *Vq, int kq)
 {
     const int N = p.N, ld = p.ld;
     const ozf::Layout Ly = ozf::layout(N, p.kp);
-    int *cex = (int *)(p.oz + (size_t)grp * p.oz_stride + Ly.cex);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    int *cex = (int *)(scr + Ly.cex);
+    int *rex = (int *)(scr + Ly.rex);
     const double *Ab = (const double *)p.Ainv + (size_t)w * N * ld;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the queue's row exponents start from zero (the accepts raise them); the
+    // scratch is shared with the recompute's update, which lays it out for
+    // 32 queue entries
+    if (rank == 0 && threadIdx.x < 64) ((int *)(scr + Ly.vex))[threadIdx.x] = 0;
+    for (int i = rank * STHREADS + (int)threadIdx.x; i < N; i += p.Gf * STHREADS) {
+        int g = 0;
+        for (int m = 0; m < kq; ++m) {
+            const double x = __ldcg(Vq + (size_t)m * ld + i);
+            if (ozf::nz(x)) g = max(g, ozf::bexp(x));
+        }
+        rex[i] = g ? 1023 - g : 0;
+    }
+    if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) return false;
     for (int c = rank * SWARPS + warp; c < N; c += p.Gf * SWARPS) {
-        unsigned e = 0;
+        int e = 0;
         for (int i = 2 * lane; i < N; i += 64) {
             const double2 u = __ldcg(reinterpret_cast<const double2 *>(Ab + (size_t)c * ld + i));
-            e = max(e, (unsigned)max(ozf::bexp(u.x), ozf::bexp(u.y)));
+            const int2 r = __ldcg(reinterpret_cast<const int2 *>(rex + i));
+            if (ozf::nz(u.x)) e = max(e, ozf::bexp(u.x) - r.x);
+            if (ozf::nz(u.y)) e = max(e, ozf::bexp(u.y) - r.y);
         }
         e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) cex[c] = (int)e;
+        if (lane == 0) cex[c] = e;
     }
+    return true;
 }
 template <typename T>
 __device__ __forceinline__ int *oz_vex(const SweepParams<T> &p, int grp)
@@ -1121,8 +1176,49 @@ __device__ __forceinline__ int *oz_vex(const SweepParams<T> &p, int grp)
     return (int *)(p.oz + (size_t)grp * p.oz_stride + ozf::layout(p.N, p.kp).vex);
 }
 
+// V's slices for phase A, cut once per flush by all CTAs of the group: block
+// kbg of AK rows (i = kbg AK .. + AK - 1), plane j, in phase A's shared-memory
+// layout, so that every row chunk of phase A copies them instead of cutting
+// them again. Entry (m, i) is sliced with the row exponent of queue entry m
+// (vex) less the row shift s_i; rows past N and entries m >= k are zero.
+template <typename T>
+__device__ __noinline__ void oz_slice_v(const SweepParams<T> &p, int w, int k, int grp, int rank)
+{
+    using namespace tcf;
+    using namespace ozf;
+    const int N = p.N, ld = p.ld, kp = p.kp;
+    const Layout Ly = layout(N, kp);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    const int *vex = (const int *)(scr + Ly.vex);
+    const int *rex = (const int *)(scr + Ly.rex);
+    __half *vg = (__half *)(scr + Ly.vsl);
+    const double *Vb = (const double *)p.V + (size_t)w * p.K * ld;
+    const size_t bplane = (size_t)kp * AK;
+    const int units = Ly.nrc * (AR / AK) * kp * 2;    // (block, m, half block): eight values each
+    for (int u = rank * STHREADS + (int)threadIdx.x; u < units; u += p.Gf * STHREADS) {
+        const int kbg = u / (kp * 2), rem = u - kbg * kp * 2, m = rem >> 1, kk = (rem & 1) * 8;
+        const int i0 = kbg * AK + kk;
+        const int ev = m < k ? __ldcg(vex + m) : 0;
+        double x[8];
+        int em[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            const bool in = m < k && i < N;
+            x[q] = in ? __ldcg(Vb + (size_t)m * ld + i) : 0.0;
+            em[q] = ev - (i < N ? __ldcg(rex + i) : 0);
+        }
+        uint4 out[NS];
+        slice8(x, em, out);
+        const uint32_t o = coff(m, kk, AK) >> 1;
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            *reinterpret_cast<uint4 *>(vg + ((size_t)kbg * NS + j) * bplane + o) = out[j];
+    }
+}
+
 // The emulated-fp64 flush of walker w (all Gf CTAs of the group call it; it
-// takes two group barriers of its own). Returns false after a wait ran out of
+// takes three group barriers of its own). Returns false after a wait ran out of
 // budget (ST_TIMEOUT recorded).
 // Phase A of flush_oz (a function of its own: its register allocation does not
 // compete with the rest of the sweep kernel's).
@@ -1136,16 +1232,15 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
     const Layout Ly = layout(N, kp);
     unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
     int *cex = (int *)(scr + Ly.cex);
-    int *vex = (int *)(scr + Ly.vex);
+    const int *rex = (const int *)(scr + Ly.rex);
     long long *partS = (long long *)(scr + Ly.part);
     float *partG = (float *)(scr + Ly.partg);
     unsigned char *reg = smem + p.off_xs;
     unsigned long long *bars = (unsigned long long *)(reg + bar_offset(kp));
-    __shared__ int ecol[AM], erow[32], ok_s;
+    __shared__ int ecol[AM], erw[AR], ok_s;
     const size_t wN = (size_t)N * ld, wK = (size_t)K * ld;
     double *Ab = (double *)p.Ainv + (size_t)w * wN;
     const double *Vb = (const double *)p.V + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Nc = Ly.nca * AM;     // row stride of the partial T' buffers
     auto wait_bar = [&](int b) -> bool {
@@ -1155,44 +1250,52 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
         return ok_s != 0;
     };
 
+    // the queue shifts f_m for phase B, from the column exponents as they
+    // stand (phase B resets them for phase C)
+    if (rank == 0 && tid < k) {
+        int *fex = (int *)(scr + Ly.fex);
+        fex[tid] = 1023 - __ldcg(cex + __ldcg(p.idx + (size_t)w * K + tid));
+    }
+
     // ------------------------------------------------------------ phase A
     {
         // T'[c][m] partial over rows [r0, r0 + AR) of column tile c0: raw fp64
-        // K-blocks of AK rows arrive by asynchronous copies NSLOT - 1 blocks
-        // ahead; each block
-        // is cut into slices with the column exponents of A^{-1} (cex) and the
-        // row exponents of V (vex), which every row chunk shares, so that the
-        // partials add up exactly as integers
+        // K-blocks of AK rows of A^{-1} arrive by asynchronous copies two
+        // blocks ahead and are cut into slices with the column exponents of
+        // A^{-1} (cex), which every row chunk shares, so that the partials add
+        // up exactly as integers; V's slices, cut once per flush
+        // (oz_slice_v), arrive by asynchronous copies one block ahead
         const int nA = Ly.nca * Ly.nrc;
         const int nkb = AR / AK;
         const size_t aplane = (size_t)AM * AK, bplane = (size_t)kp * AK;   // fp16 elements
-        double *raw = (double *)reg;                                       // [NSLOT][(AM + kp) * AK]
+        double *raw = (double *)reg;                                       // [NSLOT][AM * AK]
         __half *sa = (__half *)(reg + NSLOT * raw_bytes(kp));              // [2][NS][AM*AK]
-        __half *sb = sa + 2 * NS * aplane;                                 // [2][NS][kp*AK]
+        __half *sv = sa + 2 * NS * aplane;                                 // [NSLOT][NS][kp*AK]
+        const __half *vg = (const __half *)(scr + Ly.vsl);                 // [nrc*AR/AK][NS][kp*AK]
+        const int vch = (int)(NS * bplane * sizeof(__half) / 16);          // 16-byte chunks per block
         const uint32_t sboA = (AK / 8) * 128;
         for (int it = rank; it < nA; it += Gf) {
             const int ct = it % Ly.nca, rc = it / Ly.nca;
             const int c0 = ct * AM, r0 = rc * AR;
             const int ncol = min(AM, N - c0);
             if (tid < AM) ecol[tid] = tid < ncol ? __ldcg(cex + c0 + tid) : 0;
-            if (tid < 32) erow[tid] = tid < k ? __ldcg(vex + tid) : 0;
+            for (int t = tid; t < AR; t += STHREADS) erw[t] = r0 + t < N ? __ldcg(rex + r0 + t) : 0;
             // A pipeline without CTA barriers. Thread t copies, with 16-byte
-            // asynchronous copies NSLOT - 1 blocks ahead, exactly the raw data it
-            // cuts (rows 8 (t & 1) .. + 7 of column t >> 1 of A^{-1}, and of V
-            // row (t - 64) >> 1 for 64 <= t < 64 + 2 kp: warps 2 and 3, which
-            // share no scheduler with warp 0, whose thread 0 also issues the
-            // MMAs), so its own wait_group suffices; each warp
-            // announces its slices of stage s on bars[6 + s] (8 arrivals), thread
-            // 0 issues the stage's MMAs and commits them to bars[s], which every
-            // thread waits on before it cuts into stage s again. A wait that
+            // asynchronous copies two blocks ahead, exactly the raw data it cuts
+            // (rows 8 (t & 1) .. + 7 of column t >> 1 of A^{-1}), and a few
+            // chunks of the V slices of the next block; its own wait_group
+            // then covers both. Each warp announces stage s on bars[6 + s] (8
+            // arrivals), thread 0 issues the stage's MMAs and commits them to
+            // bars[s], which every thread waits on before it cuts into stage s
+            // (and copies into the V slot of block kb - 2) again. A wait that
             // runs out of budget marks the thread bad; it keeps walking the loop
             // without work and the CTA leaves together after it.
-            const int ca = tid >> 1, kk = (tid & 1) * 8, cv = (tid - 64) >> 1;
-            const bool hasv = tid >= 64 && tid < 64 + 2 * kp;
-            auto issue = [&](int kb) {
+            const int ca = tid >> 1, kk = (tid & 1) * 8;
+            const int kbg0 = r0 / AK;
+            auto issue = [&](int kb, int kbv) {
                 if (kb < nkb) {
                     const int i = r0 + kb * AK;
-                    double *dst = raw + (size_t)(kb % NSLOT) * (AM + kp) * AK;
+                    double *dst = raw + (size_t)(kb % NSLOT) * AM * AK;
                     const bool ina = i < ld && ca < ncol;
                     const double *srca = Ab + (size_t)(c0 + (ina ? ca : 0)) * ld + (ina ? i + kk : 0);
 #pragma unroll
@@ -1200,32 +1303,28 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
                                      ::"r"(su32(dst + (size_t)ca * AK + kk + 2 * q)), "l"(ina ? srca + 2 * q : srca),
                                        "r"(ina ? 16 : 0) : "memory");
-                    if (hasv) {
-                        const bool inv = i < ld && cv < k;
-                        const double *srcv = inv ? Vb + (size_t)cv * ld + i + kk : Vb;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                         ::"r"(su32(dst + (size_t)(AM + cv) * AK + kk + 2 * q)),
-                                           "l"(inv ? srcv + 2 * q : srcv), "r"(inv ? 16 : 0) : "memory");
-                    }
+                }
+                if (kbv >= 0 && kbv < nkb) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(vg + (size_t)(kbg0 + kbv) * NS * bplane);
+                    uint4 *dst = reinterpret_cast<uint4 *>(sv + (size_t)(kbv % NSLOT) * NS * bplane);
+                    for (int c = tid; c < vch; c += STHREADS) cp_async16(dst + c, src + c);
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
             };
-            issue(0);
-            issue(1);
-            __syncthreads();                       // ecol, erow
+            issue(0, 0);
+            issue(1, -1);
+            __syncthreads();                       // ecol, erw
             bool bad = false;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb & 1, sl = kb % NSLOT;
-                issue(kb + 2);    // this thread's own slot, cut in iteration kb - 1
-                if (kb >= 2) {    // the MMAs of block kb - 2 have read stage s
+                if (kb >= 2) {    // the MMAs of block kb - 2 have read stage s and V slot (kb + 1) % NSLOT
                     if (!bad) bad = !mbar_wait(&bars[s], tph[s], p.status, p.budget_ns);
                     tph[s] ^= 1u;
                 }
-                asm volatile("cp.async.wait_group 2;" ::: "memory");
+                issue(kb + 2, kb + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");     // blocks kb (raw, V) complete
                 const int i = r0 + kb * AK;
-                const double *rw = raw + (size_t)sl * (AM + kp) * AK;
+                const double *rw = raw + (size_t)sl * AM * AK;
                 if (!bad) {
                     {
                         double x[8];
@@ -1237,29 +1336,15 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                             x[2 * q] = u.x;
                             x[2 * q + 1] = u.y;
                         }
+                        int em[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) em[q] = ecol[ca] + erw[kb * AK + kk + q];
                         uint4 out[NS];
-                        slice8(x, ecol[ca], out);
+                        slice8(x, em, out);
                         const uint32_t o = coff(ca, kk, AK) >> 1;
 #pragma unroll
                         for (int j = 0; j < NS; ++j)
                             *reinterpret_cast<uint4 *>(sa + (s * NS + j) * aplane + o) = out[j];
-                    }
-                    if (hasv) {
-                        double x[8];
-                        const bool in = cv < k && i < ld;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + (AM + cv) * AK + kk + 2 * q)
-                                                 : make_double2(0.0, 0.0);
-                            x[2 * q] = u.x;
-                            x[2 * q + 1] = u.y;
-                        }
-                        uint4 out[NS];
-                        slice8(x, erow[cv], out);
-                        const uint32_t o = coff(cv, kk, AK) >> 1;
-#pragma unroll
-                        for (int j = 0; j < NS; ++j)
-                            *reinterpret_cast<uint4 *>(sb + (s * NS + j) * bplane + o) = out[j];
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1274,7 +1359,7 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                         for (int q = 0; q < NMMA_A; ++q) {
                             const MmaA mm = kMmaA[q];
                             const uint64_t ad = sdesc(su32(sa + (s * NS + mm.j) * aplane), 128, sboA);
-                            const uint64_t bd = sdesc(su32(sb + (s * NS + mm.l) * bplane), 128, sboA);
+                            const uint64_t bd = sdesc(su32(sv + (sl * NS + mm.l) * bplane), 128, sboA);
                             const bool first = kb == 0 && mm.fresh;
                             mma(tmem + (uint32_t)(mm.blk * kp), ad, bd, idesc_f16(AM, mm.nl * kp), first ? 0u : 1u);
                         }
@@ -1376,13 +1461,15 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
     int *tex = (int *)(scr + Ly.tex);
     const size_t wK = (size_t)K * ld;
     const double *Wb = (const double *)p.W + (size_t)w * wK;
-    const int *idxw = p.idx + (size_t)w * K;
     const int Nc = Ly.nca * AM;     // row stride of the partial T' buffers
     const int tid = threadIdx.x;
+    __shared__ int fs[32];          // queue shifts f_m (from phase A)
+    if (tid < 32) fs[tid] = tid < k ? __ldcg((const int *)(scr + Ly.fex) + tid) : 0;
+    __syncthreads();
 
     // ------------------------------------------------------------ phase B
     {
-        // T = sum_rc T'_rc - E', eight consecutive m per thread, the kp / 8
+        // T = sum_rc T'_rc, eight consecutive m per thread, the kp / 8
         // threads of a column adjacent in the warp
         const int ng = kp / 8;
         const int totT = N * ng;
@@ -1429,17 +1516,21 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
                     if (m < k) {
                         const int e = ec + __ldcg(vex + m) - 2084;
                         t[q] = fma((double)g[q], pow2(e - 8), (double)S[q] * pow2(e));
-                        t[q] -= (__ldcg(idxw + m) == c) ? 1.0 : 0.0;
                     }
                 }
             }
+            // T's column exponent over the scaled entries T[m][c] 2^-f_m
             int em = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) em = max(em, bexp(t[q]));
+            for (int q = 0; q < 8; ++q)
+                if (nz(t[q])) em = max(em, bexp(t[q]) - fs[m0 + q]);
             for (int o = 1; o < ng; o <<= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
             if (in) {
+                int emq[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) emq[q] = em + fs[m0 + q];
                 uint4 sl[NS];
-                slice8(t, em, sl);
+                slice8(t, emq, sl);
                 const int ct = c / CN;
                 const uint32_t o = coff(c - ct * CN, m0, kp) >> 1;
 #pragma unroll
@@ -1448,24 +1539,29 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
                 if (m0 == 0) tex[c] = em;
             }
         }
-        // W: one thread per row i, all kp values of m
+        // W: one thread per row i, all kp values of m; the row exponent over
+        // the scaled entries W[m][i] 2^f_m
         for (int i = rank * STHREADS + tid; i < N; i += Gf * STHREADS) {
             double x[32];
             int em = 0;
 #pragma unroll
             for (int m = 0; m < 32; ++m) {
                 x[m] = (m < k) ? __ldcg(Wb + (size_t)m * ld + i) : 0.0;
-                em = max(em, bexp(x[m]));
+                if (nz(x[m])) em = max(em, bexp(x[m]) + fs[m]);
             }
             const int rb = i / CM;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 if (g * 8 < kp) {
                     double y[8];
+                    int emq[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) y[q] = x[g * 8 + q];
+                    for (int q = 0; q < 8; ++q) {
+                        y[q] = x[g * 8 + q];
+                        emq[q] = em - fs[g * 8 + q];
+                    }
                     uint4 sl[NS];
-                    slice8(y, em, sl);
+                    slice8(y, emq, sl);
                     const uint32_t o = coff(i - rb * CM, g * 8, kp) >> 1;
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
@@ -1494,6 +1590,7 @@ __device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, i
     __half *tsl = (__half *)(scr + Ly.tsl);
     int *wex = (int *)(scr + Ly.wex);
     int *tex = (int *)(scr + Ly.tex);
+    const int *rex = (const int *)(scr + Ly.rex);
     __shared__ int ok_s;
     unsigned char *reg = smem + p.off_xs;
     unsigned long long *bars = (unsigned long long *)(reg + bar_offset(kp));
@@ -1569,6 +1666,7 @@ __device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, i
             const int cb = (warp >> 2) * 32;
             const bool rowin = i < N;
             const int ei = rowin ? __ldcg(wex + i) : 0;
+            const int ri = rowin ? __ldcg(rex + i) : 0;     // the row's shift s_i
             double xa[16];
             auto load_x = [&](int j0) {
 #pragma unroll
@@ -1609,15 +1707,17 @@ __device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, i
                     const int c = c0 + j0 + e;
                     if (rowin && c < N) Ab[(size_t)c * ld + i] = y[e];
                 }
-                // exponents of the new columns for the next flush's phase A
-                unsigned mx[16];
+                // exponents of the new columns (scaled by the row shifts) for
+                // the next flush's phase A
+                int mx[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e)
-                    mx[e] = __reduce_max_sync(0xffffffffu, (rowin && c0 + j0 + e < N) ? (unsigned)bexp(y[e]) : 0u);
+                    mx[e] = __reduce_max_sync(0xffffffffu, (rowin && c0 + j0 + e < N && nz(y[e]))
+                                                               ? bexp(y[e]) - ri : 0);
                 if (lane == 0) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
-                        if (c0 + j0 + e < N) atomicMax(cex + c0 + j0 + e, (int)mx[e]);
+                        if (c0 + j0 + e < N) atomicMax(cex + c0 + j0 + e, mx[e]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1646,6 +1746,8 @@ __device__ __noinline__ bool flush_oz(const SweepParams<T> &p, int w, int k, int
         }
     };
 
+    oz_slice_v(p, w, k, grp, rank);
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
     if (!oz_phase_a(p, w, k, grp, rank, smem, tmem, tph)) return false;
     if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
     tick(8);
@@ -1676,7 +1778,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
         // Helper CTA: take part in every flush of every walker of the group.
         for (int t = grp; t < p.nw; t += p.ngroups) {
             const int w = p.wlist ? __ldg(p.wlist + t) : t;
-            if (FM == FM_OZ) oz_colexp_init(p, w, grp, rank);
+            if (FM == FM_OZ && !oz_colexp_init(p, w, grp, rank, flush_ctr, n_flush, nullptr, 0)) return;
             for (;;) {
                 if (!group_wait_for(cmd, 2u * (n_event + 1), p.status, p.budget_ns, 128)) return;
                 const bool last = (ld_acquire(cmd) & 1u) != 0;
@@ -1706,7 +1808,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     }
 
     // Ratio CTA: rows [i0, i0 + L) of every N-vector.
-    T *vs = (T *)(smem + p.off_vs);                    // [2][chunk] proposed row (working prec.)
+    T *vs = (T *)(smem + p.off_vs);                    // [2][chunk] change u = v - a_j (working prec.)
     T *as = (T *)(smem + p.off_as);                    // [2][chunk] column j of A^{-1}
     double *vd = (double *)(smem + p.off_vd);          // [2][chunk] proposed row (fp64)
     double *red = (double *)(smem + p.off_red);        // [2K+1] reduced dots
@@ -1719,6 +1821,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
     const int i0 = rank * chunk;
     const int L = max(0, min(chunk, N - i0));
     const int nj = 2 * K + 1;
+    const int njs = 2 * K + 2;                         // row stride of the partials in global memory
 
     for (int t = grp; t < p.nw; t += p.ngroups) {
         const int w = p.wlist ? __ldg(p.wlist + t) : t;
@@ -1730,21 +1833,25 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
         T *Ww = p.W + (size_t)w * wK;
         T *Vw = p.V + (size_t)w * wK;
         if (FM == FM_OZ) {
-            oz_colexp_init(p, w, grp, rank);
+            if (!oz_colexp_init(p, w, grp, rank, flush_ctr, n_flush, nullptr, 0)) return;
             if (threadIdx.x < 2) vx_s[threadIdx.x] = 0;
         }
 
-        // proposed row of electron jj (v = a_jj + sigma g) and column jj of A^{-1};
-        // with the emulated flush also the largest exponent of the CTA's part of v
+        // proposed row of electron jj, v = a_jj + sigma g (fp64, for the new row
+        // of A), its change u = v - a_jj (working precision, for the dot
+        // products and the queue) and column jj of A^{-1}; with the emulated
+        // flush also the largest exponent of the CTA's part of u
         auto stage = [&](int jj, int bb, bool row, bool col) {
             if (row) {
                 const double *arow = Aw + (size_t)jj * ld + i0;
                 const double *grow = Gw + (size_t)jj * ld + i0;
                 for (int t = threadIdx.x; t < L; t += STHREADS) {
-                    const double v = arow[t] + p.sigma * __ldcg(grow + t);
-                    vs[bb * chunk + t] = (T)v;
+                    const double a0 = arow[t];
+                    const double v = __dadd_rn(a0, __dmul_rn(p.sigma, __ldcg(grow + t)));
+                    const double u = __dsub_rn(v, a0);
+                    vs[bb * chunk + t] = (T)u;
                     vd[bb * chunk + t] = v;
-                    if (FM == FM_OZ) atomicMax(&vx_s[bb], ozf::bexp(v));
+                    if (FM == FM_OZ && ozf::nz(u)) atomicMax(&vx_s[bb], ozf::bexp(u));
                 }
                 if (threadIdx.x == 0) u_s[bb] = __ldcg(Uw + jj);
             }
@@ -1785,14 +1892,14 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 }
                 if (threadIdx.x == 0) pu = __ldcg(Uw + j + 1);
             }
-            // ---- partial dot products over the chunk: d, y_m = W[m].v, c_m = V[m].a
+            // ---- partial dot products over the chunk: d = u.a, y_m = W[m].u, c_m = V[m].a
             // (cluster mode: into this CTA's shared memory, for the siblings to read)
             double *clp = (double *)(smem + p.off_cl);
             unsigned *clflag = (unsigned *)(clp + 2 * nj);
             // (partials as double-fp32 pairs; outside cluster mode as tagged
             // words in buffer pbuf of the group's two)
             const unsigned pbuf = n_ratio & 1u, tag = 1u + n_ratio % 3u;
-            double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + pbuf) * Gr + rank) * nj;
+            double *part = CL ? clp + b * nj : p.partial + (((size_t)grp * 2 + pbuf) * Gr + rank) * njs;
             if (RES) {
                 // G consecutive lanes per job (a power of two up to 8 that the
                 // CTA's threads allow), lane g taking elements g, g + G, ...,
@@ -1861,11 +1968,12 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             }
             if (pf) {
                 if (threadIdx.x < L) {
-                    const double v = pa + p.sigma * pg;
-                    vs[(b ^ 1) * chunk + threadIdx.x] = (T)v;
+                    const double v = __dadd_rn(pa, __dmul_rn(p.sigma, pg));
+                    const double u = __dsub_rn(v, pa);
+                    vs[(b ^ 1) * chunk + threadIdx.x] = (T)u;
                     vd[(b ^ 1) * chunk + threadIdx.x] = v;
                     as[(b ^ 1) * chunk + threadIdx.x] = pc;
-                    if (FM == FM_OZ) atomicMax(&vx_s[b ^ 1], ozf::bexp(v));
+                    if (FM == FM_OZ && ozf::nz(u)) atomicMax(&vx_s[b ^ 1], ozf::bexp(u));
                 }
                 if (threadIdx.x == 0) u_s[b ^ 1] = pu;
             } else if (j + 1 < N) {
@@ -1881,7 +1989,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             // cluster mode the loads poll the tagged words until every one
             // carries this proposal's tag (the stall option asks for a tag that
             // never comes, to exercise the timeout).
-            const double *pb = p.partial + ((size_t)grp * 2 + pbuf) * Gr * nj;
+            const double *pb = p.partial + ((size_t)grp * 2 + pbuf) * Gr * njs;
             const unsigned want = (p.stall && n_ratio == 0) ? 4u : tag;
             int late = 0;
             {
@@ -1907,10 +2015,10 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                     } else {
                         const double *pbj = pb + job;
                         unsigned long long deadline = 0;
-                        const size_t stp = (size_t)G * nj;
+                        const size_t stp = (size_t)G * njs;
                         for (; q < Gr; q += 8 * G) {
                             const int cnt = min(8, (Gr - q + G - 1) / G);
-                            const double *pq = pbj + (size_t)q * nj;
+                            const double *pq = pbj + (size_t)q * njs;
                             unsigned long long x[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e)
@@ -1960,7 +2068,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                 for (int m = lane; m < k; m += 32) s += red[1 + m] * red[1 + k + m];
                 s = warp_allsum(s);
                 if (lane == 0) {
-                    const double r = red[0] - s;
+                    const double r = 1.0 + (red[0] - s);
                     const double u = u_s[b];
                     const double prob = fmin(1.0, r * r);
                     const int ov = p.override_ ? (int)p.override_[(size_t)w * N + j] : -1;
@@ -1974,7 +2082,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         p.acc_out[(size_t)orow * N + j] = (unsigned char)a;
                         p.ratio_out[(size_t)orow * N + j] = r;
                         if (fabs(prob - u) < 1e-10) p.ties[orow] += 1;
-                        if (a) p.idx[(size_t)w * K + k] = j;
+                        if (a || p.fixed_slot) p.idx[(size_t)w * K + k] = j;
                     }
                 }
             } else if (RES) {
@@ -2008,24 +2116,27 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
             __syncthreads();
             const int a = acc_s;
             tick(3);
-            if (a) {
-                // ---- accept: z = a - W c, W <- [W - z y'/r, z/r], V[k] = v, A[j] = v
-                const double rinv = rinv_s;
+            if (a || p.fixed_slot) {
+                // ---- accept: z = a - W c, W <- [W - z y'/r, z/r], V[k] = u, A[j] = v.
+                // A rejected proposal with fixed slots takes the slot as the zero
+                // change: y = W'0 = 0 and the Schur complement is 1, so
+                // W <- [W, z], V[k] = 0, and A keeps its row.
+                const double rinv = a ? rinv_s : 1.0;
                 T *cT = coef, *yT = coef + K, *zs = coef + 2 * K;
                 for (int m = threadIdx.x; m < k; m += STHREADS) {
                     cT[m] = (T)red[1 + k + m];
-                    yT[m] = (T)(red[1 + m] * rinv);
+                    yT[m] = a ? (T)(red[1 + m] * rinv) : (T)0;
                 }
                 double *arow_w = Aw + (size_t)j * ld;
                 if (RES) {
                     // (z is in zs already)
                     for (int t = threadIdx.x; t < L; t += STHREADS) {
-                        Vsm[k * LP + t] = vsb[t];
-                        arow_w[i0 + t] = vdb[t];
+                        Vsm[k * LP + t] = a ? vsb[t] : (T)0;
+                        if (a) arow_w[i0 + t] = vdb[t];
                     }
                     __syncthreads();
                     const T rT = (T)rinv;
-                    for (int e = threadIdx.x; e < (k + 1) * L; e += STHREADS) {
+                    for (int e = threadIdx.x + (a ? 0 : k * L); e < (k + 1) * L; e += STHREADS) {
                         const int m = e / L, t = e - m * L;
                         if (m < k) Wsm[m * LP + t] -= zs[t] * yT[m];
                         else Wsm[k * LP + t] = zs[t] * rT;
@@ -2054,7 +2165,7 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                             }
                         }
 #pragma unroll 4
-                        for (int m = 0; m < k; ++m) {
+                        for (int m = 0; m < (a ? k : 0); ++m) {
                             const T ym = yT[m];
                             T *wr = Ww + (size_t)m * ld + i0;
 #pragma unroll
@@ -2068,13 +2179,13 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                             const int t = tb + threadIdx.x + q * STHREADS;
                             if (t < L) {
                                 Ww[(size_t)k * ld + i0 + t] = z[q] * rT;
-                                Vw[(size_t)k * ld + i0 + t] = vsb[t];
-                                arow_w[i0 + t] = vdb[t];
+                                Vw[(size_t)k * ld + i0 + t] = a ? vsb[t] : (T)0;
+                                if (a) arow_w[i0 + t] = vdb[t];
                             }
                         }
                     }
                 }
-                if (FM == FM_OZ && threadIdx.x == 0) atomicMax(oz_vex(p, grp) + k, vx_s[b]);
+                if (FM == FM_OZ && threadIdx.x == 0) atomicMax(oz_vex(p, grp) + k, a ? vx_s[b] : 0);
                 ++k;
             }
             // (vx_s[b] is staged again in the next proposal, after its first barrier)
@@ -2202,6 +2313,21 @@ __global__ void sweep_draw_kernel(int N, int ld, int nw, unsigned long long seed
     }
 }
 
+// The draws of one sweep of nw walkers (keys base_seed + w) into caller
+// memory: gauss [nw][N][N], unif [nw][N] (the same kernel as the sweep's own
+// draws, rows of length N).
+cudaError_t launch_proposal_draws(int N, int nw, unsigned long long base_seed, int sweep, double *gauss,
+                                  double *unif, cudaStream_t s)
+{
+    if (N <= 0 || nw <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sweep_draw_kernel<<<sms * 8, 256, 0, s>>>(N, N, nw, base_seed, sweep, nullptr, 0, nullptr, nullptr,
+                                              nullptr, gauss, unif);
+    return cudaGetLastError();
+}
+
 // log|det A| and sign after the sweep: one CTA per walker sums log|r| over the
 // accepted proposals in a fixed order.
 __global__ void sweep_logdet_kernel(int N, const int *wlist, const unsigned char *acc,
@@ -2308,7 +2434,6 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<T, RES, FM, CL>, STHREADS, smem);
     if (e != cudaSuccess) return e;
-    if (FM == FM_OZ && per_sm > 1) return cudaErrorInvalidConfiguration;   // the TMEM allocation would wait
     const int nw = L.wlist ? L.nlist : c.batch;
     int ngroups = 0;
     cudaLaunchConfig_t cfg = {};
@@ -2347,7 +2472,7 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
         if (ngroups < 1) return cudaErrorInvalidConfiguration;
     }
     if (ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorInvalidConfiguration;
-    if ((size_t)ngroups * 2 * Gr * (2 * K + 1) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
+    if ((size_t)ngroups * 2 * Gr * (2 * K + 2) > c.sw_partial_len) return cudaErrorInvalidConfiguration;
 
     SweepParams<T> p;
     p.N = c.N; p.K = K; p.ld = c.ld; p.batch = c.batch;
@@ -2357,6 +2482,7 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     p.gauss = c.sw_gauss; p.unif = c.sw_unif;
     p.partial = c.sw_partial; p.sync = c.sw_sync; p.status = c.status;
     p.sigma = L.sigma; p.override_ = L.override;
+    p.fixed_slot = c.opt_fixed_slot;
     p.acc_out = L.acc_out; p.ratio_out = L.ratio_out; p.ties = L.ties;
     p.budget_ns = c.opt_budget_ns; p.stall = c.opt_stall;
     p.off_vs = offs[0]; p.off_as = offs[1]; p.off_vd = offs[2]; p.off_red = offs[3];
@@ -2376,7 +2502,7 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
     if (!CL) {
         // tag 0 in every partial slot: no word left by an earlier launch can
         // carry the tag that a proposal of this one waits for
-        e = cudaMemsetAsync(c.sw_partial, 0, (size_t)ngroups * 2 * Gr * (2 * K + 1) * sizeof(double), c.stream);
+        e = cudaMemsetAsync(c.sw_partial, 0, (size_t)ngroups * 2 * Gr * (2 * K + 2) * sizeof(double), c.stream);
         if (e != cudaSuccess) return e;
     }
     if (CL) {
@@ -2399,8 +2525,8 @@ static cudaError_t launch_shape(Ctx &c, const SweepLaunch &L, int Gf, int Gr, in
 
 size_t oz_group_bytes(int N, int K)
 {
-    if (K > 32) return 0;
-    return ozf::layout(N, (K + 15) / 16 * 16).bytes;
+    (void)K;   // the recompute's rank-32 updates use the scratch at every K
+    return ozf::layout(N, 32).bytes;
 }
 
 // The emulated-fp64 flush (flush_oz) for this handle and group size: fp64,
@@ -2722,17 +2848,22 @@ __global__ void __launch_bounds__(STHREADS, 1) oz_flush_kernel(SweepParams<doubl
         for (int w = grp; w < p.batch; w += p.ngroups) {
             const int k = __ldcg(kcount + w);
             if (k < kthresh || k < 1) continue;           // uniform for the group
-            oz_colexp_init(p, w, grp, rank);
+            if (!oz_colexp_init(p, w, grp, rank, flush_ctr, n_flush,
+                                (const double *)p.V + (size_t)w * p.K * p.ld, k)) break;
             if (rank == 0) {
-                // exponents of V's rows (warp m: row m)
+                // exponents of V's scaled rows, max_i (E(V[m][i]) + s_i) (warp m: row m)
                 int *vex = oz_vex(p, grp);
+                const int *rex = (const int *)(p.oz + (size_t)grp * p.oz_stride + ozf::layout(p.N, p.kp).rex);
                 const double *Vb = p.V + (size_t)w * p.K * p.ld;
                 for (int m = warp; m < 64; m += SWARPS) {
-                    unsigned e = 0;
+                    int e = 0;
                     if (m < k)
-                        for (int i = lane; i < p.N; i += 32) e = max(e, (unsigned)ozf::bexp(__ldcg(Vb + (size_t)m * p.ld + i)));
+                        for (int i = lane; i < p.N; i += 32) {
+                            const double x = __ldcg(Vb + (size_t)m * p.ld + i);
+                            if (ozf::nz(x)) e = max(e, ozf::bexp(x) + __ldcg(rex + i));
+                        }
                     e = __reduce_max_sync(0xffffffffu, e);
-                    if (lane == 0) vex[m] = (int)e;
+                    if (lane == 0) vex[m] = e;
                 }
             }
             if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
@@ -2744,6 +2875,199 @@ __global__ void __launch_bounds__(STHREADS, 1) oz_flush_kernel(SweepParams<doubl
     __syncthreads();
     if (threadIdx.x < 32)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_s), "n"(ozf::TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------- recompute update
+// The rank-nb update of the Gauss-Jordan recompute, X[c][i] += sum_m Lt[m][c]
+// R[m][i] (X = A' row-major, the panel's multipliers Lt and pivot rows R, nb
+// <= 32), as the emulated-fp64 contraction of the flush: it is phase C's
+// A^{-1}[i][c] -= sum_m W[m][i] T[m][c] with W = R and T = -Lt. The slicing
+// takes the place of phase B: queue entry m is balanced by 2^f_m on R's row
+// and 2^-f_m on Lt's row, f_m half the difference of the two rows' largest
+// exponents (found in a first pass over all CTAs of the group), then Lt's
+// columns and R's rows are cut with one exponent each.
+template <typename T>
+__device__ bool oz_slice_lr(const SweepParams<T> &p, int k, int grp, int rank, const double *Lt,
+                            const double *R, unsigned *flush_ctr, unsigned &n_flush)
+{
+    using namespace tcf;
+    using namespace ozf;
+    const int N = p.N, ld = p.ld, kp = p.kp, Gf = p.Gf;
+    const Layout Ly = layout(N, kp);
+    unsigned char *scr = p.oz + (size_t)grp * p.oz_stride;
+    int *fex = (int *)(scr + Ly.fex);                // [0, 32) Lt rows, [32, 64) R rows
+    __half *wsl = (__half *)(scr + Ly.wsl);
+    __half *tsl = (__half *)(scr + Ly.tsl);
+    int *wex = (int *)(scr + Ly.wex);
+    int *tex = (int *)(scr + Ly.tex);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // pass 1: the rows' largest exponents (fex cleared before the launch)
+    for (int m = warp; m < 2 * k; m += SWARPS) {
+        const double *row = (m < k ? Lt + (size_t)m * ld : R + (size_t)(m - k) * ld);
+        int e = 0;
+        for (int i = rank * 32 + lane; i < N; i += Gf * 32) e = max(e, bexp(__ldcg(row + i)));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0 && e > 0) atomicMax(fex + (m < k ? m : 32 + m - k), e);
+    }
+    if (!group_barrier(flush_ctr, (++n_flush) * Gf, p.status, p.budget_ns)) return false;
+    __shared__ int fs[32];
+    if (tid < 32) fs[tid] = tid < k ? (__ldcg(fex + tid) - __ldcg(fex + 32 + tid)) >> 1 : 0;
+    __syncthreads();
+    // T = -Lt: eight consecutive m per thread, the kp / 8 threads of a column
+    // adjacent in the warp (as phase B)
+    const int ng = kp / 8;
+    const int totT = N * ng;
+    for (int base = rank * STHREADS; base < totT; base += Gf * STHREADS) {
+        const int e = base + tid;
+        const bool in = e < totT;
+        const int c = in ? e / ng : 0, m0 = (e - (e / ng) * ng) * 8;
+        double t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = (in && m0 + q < k) ? -__ldcg(Lt + (size_t)(m0 + q) * ld + c) : 0.0;
+        int em = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (nz(t[q])) em = max(em, bexp(t[q]) - fs[m0 + q]);
+        for (int o = 1; o < ng; o <<= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+        if (in) {
+            int emq[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) emq[q] = em + fs[m0 + q];
+            uint4 sl[NS];
+            slice8(t, emq, sl);
+            const int ct = c / CN;
+            const uint32_t o = coff(c - ct * CN, m0, kp) >> 1;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                *reinterpret_cast<uint4 *>(tsl + ((size_t)ct * NS + j) * CN * kp + o) = sl[j];
+            if (m0 == 0) tex[c] = em;
+        }
+    }
+    // W = R: one thread per row i, all kp values of m
+    for (int i = rank * STHREADS + tid; i < N; i += Gf * STHREADS) {
+        double x[32];
+        int em = 0;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            x[m] = (m < k) ? __ldcg(R + (size_t)m * ld + i) : 0.0;
+            if (nz(x[m])) em = max(em, bexp(x[m]) + fs[m]);
+        }
+        const int rb = i / CM;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            if (g * 8 < kp) {
+                double y[8];
+                int emq[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    y[q] = x[g * 8 + q];
+                    emq[q] = em - fs[g * 8 + q];
+                }
+                uint4 sl[NS];
+                slice8(y, emq, sl);
+                const uint32_t o = coff(i - rb * CM, g * 8, kp) >> 1;
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    *reinterpret_cast<uint4 *>(wsl + ((size_t)rb * NS + j) * CM * kp + o) = sl[j];
+            }
+        }
+        wex[i] = em;
+    }
+    return true;
+}
+
+// One update of every walker's X (walker groups as in oz_flush_kernel); k
+// the panel's width (<= kp = 32). fex of every group is cleared before the
+// launch.
+__global__ void __launch_bounds__(STHREADS, 1) oz_gj_update_kernel(SweepParams<double> p, const double *Lt,
+                                                                   const double *R, int nb, int k)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t tmem_s;
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tcf::su32(&tmem_s)), "n"(ozf::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long *bars = (unsigned long long *)(smem + p.off_tcbar);
+        for (int q = 0; q < ozf::NBAR; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                         ::"r"(tcf::su32(&bars[q])), "r"(ozf::bar_count(q)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+        const int grp = blockIdx.x / p.Gf, rank = blockIdx.x - grp * p.Gf;
+        unsigned *flush_ctr = p.sync + SYNC_STRIDE * grp + 32;
+        unsigned n_flush = 0, tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = grp; w < p.batch; w += p.ngroups) {
+            const double *Ltw = Lt + (size_t)w * nb * p.ld, *Rw = R + (size_t)w * nb * p.ld;
+            if (w != grp) {
+                // the group's fex is cleared for each further walker (the first
+                // is cleared before the launch)
+                if (rank == 0 && threadIdx.x < 64) ((int *)(p.oz + (size_t)grp * p.oz_stride +
+                                                            ozf::layout(p.N, p.kp).fex))[threadIdx.x] = 0;
+                if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
+            }
+            if (!oz_slice_lr(p, k, grp, rank, Ltw, Rw, flush_ctr, n_flush)) break;
+            if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
+            if (!oz_phase_c(p, w, k, grp, rank, smem, tmem_s, tph)) break;
+            if (!group_barrier(flush_ctr, (++n_flush) * p.Gf, p.status, p.budget_ns)) break;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_s), "n"(ozf::TMEM_COLS) : "memory");
+}
+
+// cudaErrorNotSupported when the emulated update does not apply (the caller
+// then takes the fp64 tile GEMM).
+cudaError_t launch_gj_update_oz(Ctx &c, int nbe)
+{
+    constexpr int KP = 32;
+    // the handle owns the GPU (no group shape or grid cap: a serving pool
+    // recomputes admitted walkers on a second stream while its sweep, which
+    // shares this scratch, runs)
+    if (c.prec != QMCDU_FP64 || !c.oz || c.oz_groups < 1 || c.opt_fp64_flush == 1 || nbe < 1 || nbe > KP ||
+        c.nb > KP || c.oz_stride < ozf::layout(c.N, KP).bytes || c.opt_group_ctas != 0 || c.opt_max_ctas != 0)
+        return cudaErrorNotSupported;
+    const size_t smem = std::max((size_t)OZ_MIN_SMEM, ozf::region_bytes(KP));
+    cudaError_t e = cudaFuncSetAttribute(oz_gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_gj_update_kernel, STHREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm != 1) return cudaErrorNotSupported;     // the TMEM allocation would wait
+    const int ngroups = std::min(c.batch, c.oz_groups);
+    const int Gf = c.num_sms / ngroups;
+    if (Gf < 2 || ngroups * SYNC_STRIDE > c.sync_words) return cudaErrorNotSupported;
+    SweepParams<double> p{};
+    p.N = c.N; p.K = KP; p.ld = c.ld; p.batch = c.batch;
+    p.Gf = Gf; p.Gr = 1; p.ngroups = ngroups;
+    p.Ainv = c.work;                 // X[c][i] at c * ld + i: phase C's column c, row i
+    p.sync = c.sw_sync; p.status = c.status;
+    p.budget_ns = c.opt_budget_ns;
+    p.kp = KP; p.oz = c.oz; p.oz_stride = c.oz_stride;
+    p.off_xs = 0;
+    p.off_tcbar = (int)ozf::bar_offset(KP);
+    p.phase_ns = nullptr;
+    e = cudaMemsetAsync(c.sw_sync, 0, (size_t)ngroups * SYNC_STRIDE * sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return e;
+    const size_t fex = ozf::layout(c.N, KP).fex;
+    for (int g = 0; g < ngroups; ++g) {
+        e = cudaMemsetAsync(c.oz + (size_t)g * c.oz_stride + fex, 0, 64 * sizeof(int), c.stream);
+        if (e != cudaSuccess) return e;
+    }
+    const double *Lt = c.Lt, *R = c.R;
+    int nb = c.nb, k = nbe;
+    void *args[] = {&p, &Lt, &R, &nb, &k};
+    return cudaLaunchCooperativeKernel((const void *)oz_gj_update_kernel, dim3(ngroups * Gf), dim3(STHREADS),
+                                       args, smem, c.stream);
 }
 
 // cudaErrorNotSupported when the emulated flush does not apply (the caller

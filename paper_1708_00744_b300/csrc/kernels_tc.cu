@@ -115,8 +115,6 @@ struct Args {
     const int *kdyn;             // per-batch k (device) or null
     int kdyn_is_n;               // 1: k replaces N (rounded up to 16); 0: k replaces K
     int kthresh;                 // batches with k < kthresh are skipped (when kdyn)
-    const int *fix_idx;          // C(m, n) -= [m == fix_idx[b*fix_stride + n]]
-    int fix_stride;
     int *status;
     long long budget_ns;
 };
@@ -265,7 +263,6 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_bf16x3_kernel(Args g)
                     float v = g.alpha * __uint_as_float(r[j]);
                     float *dst = C + row * g.ldc + col;
                     if (g.beta != 0.f) v += g.beta * *dst;
-                    if (g.fix_idx && g.fix_idx[(size_t)b * g.fix_stride + col] == row) v -= 1.f;
                     *dst = v;
                 }
             }
@@ -573,8 +570,8 @@ static cudaError_t launch(int M, int N, int K, const float *A, long long lda, co
 cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long lda, long long sA,
                                const float *B, long long ldb, long long sB, int b_trans, float *C,
                                long long ldc, long long sC, float alpha, float beta, int batch,
-                               const int *kdyn, int kdyn_is_n, int kthresh, const int *fix_idx,
-                               int fix_stride, int *status, long long budget_ns, cudaStream_t s)
+                               const int *kdyn, int kdyn_is_n, int kthresh, int *status,
+                               long long budget_ns, cudaStream_t s)
 {
     tc::Args g;
     g.M = M; g.N = N; g.K = K;
@@ -583,11 +580,10 @@ cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long ld
     g.C = C; g.ldc = ldc; g.sC = sC;
     g.alpha = alpha; g.beta = beta;
     g.kdyn = kdyn; g.kdyn_is_n = kdyn_is_n; g.kthresh = kthresh;
-    g.fix_idx = fix_idx; g.fix_stride = fix_stride;
     g.status = status; g.budget_ns = budget_ns;
     if (M <= 0 || N <= 0 || K < 0 || batch <= 0) return cudaSuccess;
     // one plain matrix: operands split once, a TMA-fed pipeline
-    if (batch == 1 && !kdyn && !fix_idx && K > 0 && N > 128)
+    if (batch == 1 && !kdyn && K > 0 && N > 128)
         return tc2::launch(M, N, K, A, lda, B, ldb, b_trans, C, ldc, alpha, beta, status,
                            budget_ns, s);
     // narrow N (a short queue) takes a narrower tile

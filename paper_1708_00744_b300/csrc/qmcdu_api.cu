@@ -97,9 +97,12 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
     AL(c->colperm, B * N * sizeof(int));
     AL(c->Lt, B * c->nb * ld * sizeof(double));
     AL(c->R, B * c->nb * ld * sizeof(double));
+    AL(c->eqs, B * 2 * N * sizeof(int));
     AL(c->lu_logabs, B * sizeof(double));
     AL(c->lu_sign, B * sizeof(int));
     AL(c->drift, B * 4 * sizeof(double));
+    AL(c->pair_logabs, B * sizeof(double));
+    AL(c->pair_sign, B * sizeof(int));
     if (c->gj_ctas > 0) {
         AL(c->gj_scr, B * gj_mc_scratch_bytes(c->gj_ctas, c->nb));
         AL(c->gj_ctr, B * 32 * sizeof(unsigned));
@@ -110,7 +113,7 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
     AL(c->sw_override, B * N);
     {
         const size_t cap = (size_t)c->num_sms * 8;   // 256-thread CTAs resident per GPU, at most
-        c->sw_partial_len = cap * 2 * (2 * K + 1);
+        c->sw_partial_len = cap * 2 * (2 * K + 2);
         c->sync_words = (int)(cap * 96);
         AL(c->sw_partial, c->sw_partial_len * sizeof(double));
         AL(c->sw_sync, cap * 96 * sizeof(unsigned));
@@ -144,7 +147,8 @@ static void release(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
-                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz, c->gj_scr, c->gj_ctr};
+                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz, c->gj_scr, c->gj_ctr,
+                    c->pair_logabs, c->pair_sign, c->eqs};
     for (void *p : more)
         if (p) cudaFree(p);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -259,7 +263,7 @@ static int do_recompute(Ctx *c, int have_old)
     CK(prof_begin(c, c->ev_recompute));
     CK(launch_recompute(*c, have_old));
     CK(prof_end(c, c->ev_recompute));
-    c->n_launch += 5 + 2 * ((c->N + c->nb - 1) / c->nb);
+    c->n_launch += 8 + 2 * ((c->N + c->nb - 1) / c->nb);
     c->n_recompute += 1;
     return QMCDU_OK;
 }
@@ -514,6 +518,33 @@ int qmcdu_logdet(qmcdu_t h, double *logabs, int *sign)
     return read_status(c);
 }
 
+int qmcdu_logdet_product(qmcdu_t h1, qmcdu_t h2, double *logabs, int *sign)
+{
+    if (!h1 || !h2 || h1 == h2) return QMCDU_ERR_ARG;
+    Ctx *c1 = reinterpret_cast<Ctx *>(h1), *c2 = reinterpret_cast<Ctx *>(h2);
+    if (c1->batch != c2->batch || c1->device != c2->device) {
+        c1->err = "qmcdu_logdet_product: the handles differ in batch or device";
+        return QMCDU_ERR_ARG;
+    }
+    // h2's running values as of now, then the combination on h1's stream
+    Ctx *c = c1;        // (errors are reported on h1)
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, c2->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c1->stream, ev, 0);
+    cudaEventDestroy(ev);
+    CK(e);
+    CK(launch_logdet_pair(c1->batch, c1->logabs, c1->sign, c2->logabs, c2->sign, c1->pair_logabs,
+                          c1->pair_sign, c1->stream));
+    if (logabs)
+        CK(cudaMemcpyAsync(logabs, c1->pair_logabs, c1->batch * sizeof(double), cudaMemcpyDefault,
+                           c1->stream));
+    if (sign)
+        CK(cudaMemcpyAsync(sign, c1->pair_sign, c1->batch * sizeof(int), cudaMemcpyDefault, c1->stream));
+    const int st = read_status(c2);
+    return st ? st : read_status(c1);
+}
+
 int qmcdu_sync(qmcdu_t h)
 {
     if (!h) return QMCDU_ERR_ARG;
@@ -552,6 +583,8 @@ int qmcdu_sweep(qmcdu_t h, unsigned long long base_seed, int sweep_index, double
         CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
         return copy_sweep_outputs(c, accepted_out, ratios_out, near_ties_out);
     }
+    if (c->opt_fixed_slot)
+        return fail(c, QMCDU_ERR_STATE, "fixed slots need the persistent sweep%s");
     int kub = 0;                      // upper bound on max_b k_b
     std::vector<int> hk(c->batch);
     for (int j = 0; j < N; ++j) {
@@ -762,7 +795,7 @@ int qmcdu_step(qmcdu_t h, unsigned long long base_seed, int first_sweep, int nsw
     CK(cudaMemcpyAsync(c->d_params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream));
     if (use_graph && step_graph_ready(c, nsweeps, recompute, sigma)) {
         CK(cudaGraphLaunch(c->graph_exec, c->stream));
-        c->n_launch += 3 * nsweeps + (recompute ? 5 + 2 * ((c->N + c->nb - 1) / c->nb) : 0);
+        c->n_launch += 3 * nsweeps + (recompute ? 8 + 2 * ((c->N + c->nb - 1) / c->nb) : 0);
     } else {
         st = enqueue_step(c, nsweeps, sigma, recompute);
         if (st) return st;
@@ -927,6 +960,10 @@ int qmcdu_set_option(qmcdu_t h, int option, long long value)
         if (value < 0 || value > 2) return QMCDU_ERR_ARG;
         c->opt_fp64_flush = (int)value;
         break;
+    case QMCDU_OPT_FIXED_SLOT:
+        if (value > 1) return QMCDU_ERR_ARG;
+        c->opt_fixed_slot = (int)value;
+        break;
     default: return fail(c, QMCDU_ERR_ARG, "unknown option%s");
     }
     return QMCDU_OK;
@@ -977,6 +1014,7 @@ static void range_view(const Ctx &c, int w0, int n, Ctx &v)
     v.R = c.R + w * c.nb * c.ld;
     v.lu_logabs = c.lu_logabs + w;
     v.lu_sign = c.lu_sign + w;
+    v.eqs = c.eqs + (size_t)2 * c.N * w;
     v.drift = c.drift + 4 * w;
     v.logabs = c.logabs + w;
     v.sign = c.sign + w;
@@ -989,7 +1027,7 @@ static int recompute_range(Ctx *c, int first, int count, int have_old)
     CK(prof_begin(c, c->ev_recompute));
     CK(launch_recompute(v, have_old));
     CK(prof_end(c, c->ev_recompute));
-    c->n_launch += 5 + 2 * ((c->N + c->nb - 1) / c->nb);
+    c->n_launch += 8 + 2 * ((c->N + c->nb - 1) / c->nb);
     c->n_recompute += 1;
     return QMCDU_OK;
 }
@@ -1130,7 +1168,7 @@ int qmcdu_gemm_bf16x3(int M, int N, int K, const float *A, int lda, const float 
         return QMCDU_ERR_ARG;
     }
     cudaError_t e = launch_gemm_bf16x3(M, N, K, A, lda, 0, B, ldb, 0, b_trans, C, ldc, 0, alpha,
-                                       beta, 1, nullptr, 0, 0, nullptr, 0, nullptr, 2000000000LL,
+                                       beta, 1, nullptr, 0, 0, nullptr, 2000000000LL,
                                        (cudaStream_t)stream);
     if (e != cudaSuccess) {
         set_handleless_error(std::string("qmcdu_gemm_bf16x3: ") + cudaGetErrorString(e));
@@ -1187,6 +1225,22 @@ int qmcdu_profile_read(qmcdu_t h, double *out, int n)
     return QMCDU_OK;
 }
 
+int qmcdu_profile_sweep_times(qmcdu_t h, double *ms_out, int max_n, int *n_out)
+{
+    if (!h || max_n < 0 || (max_n > 0 && !ms_out) || !n_out) return QMCDU_ERR_ARG;
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    CK(cudaStreamSynchronize(c->stream));
+    int n = 0;
+    for (auto &p : c->ev_sweep) {
+        if (n >= max_n) break;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.first, p.second));
+        ms_out[n++] = ms;
+    }
+    *n_out = n;
+    return QMCDU_OK;
+}
+
 int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *c2,
                         const unsigned *c3, int n, unsigned long long seed, unsigned *out,
                         void *stream)
@@ -1194,6 +1248,23 @@ int qmcdu_philox4x32_10(const unsigned *c0, const unsigned *c1, const unsigned *
     if (n < 0 || (n > 0 && (!c0 || !c1 || !c2 || !c3 || !out))) return QMCDU_ERR_ARG;
     cudaError_t e = launch_philox_fill(c0, c1, c2, c3, n, seed, out, (cudaStream_t)stream);
     return e == cudaSuccess ? QMCDU_OK : QMCDU_ERR_CUDA;
+}
+
+int qmcdu_proposal_draws(int N, int nwalkers, unsigned long long base_seed, int sweep, double *gauss_out,
+                         double *unif_out, void *stream)
+{
+    if (N < 1 || N > QMCDU_MAX_N || nwalkers < 0 || sweep < 0 ||
+        (nwalkers > 0 && (!gauss_out || !unif_out))) {
+        set_handleless_error("qmcdu_proposal_draws: invalid sizes or null pointer");
+        return QMCDU_ERR_ARG;
+    }
+    cudaError_t e = launch_proposal_draws(N, nwalkers, base_seed, sweep, gauss_out, unif_out,
+                                          (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_handleless_error(std::string("qmcdu_proposal_draws: ") + cudaGetErrorString(e));
+        return QMCDU_ERR_CUDA;
+    }
+    return QMCDU_OK;
 }
 
 }  // extern "C"

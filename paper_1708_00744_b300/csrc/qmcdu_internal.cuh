@@ -35,7 +35,7 @@ struct Ctx {
     double *A = nullptr;        // batch x N x ld, row-major
     void *Ainv = nullptr;       // batch x N x ld, column-major (working precision)
     void *P = nullptr;          // batch x K x ld  (P[m] = A^{-1}[:, idx_m])
-    void *V = nullptr;          // batch x K x ld  (V[m] = proposed row of move m)
+    void *V = nullptr;          // batch x K x ld  (V[m] = change u_m = v_m - a_idx_m of move m)
     double *vstash = nullptr;   // batch x ld fp64 copy of the pending proposed row
     double *Kinv = nullptr;     // batch x K x K, row-major
     int *idx = nullptr;         // batch x K
@@ -51,7 +51,7 @@ struct Ctx {
     unsigned char *mask_d = nullptr; // batch
     int *status = nullptr;      // 1 int
     // flush workspace
-    void *Tbuf = nullptr;       // batch x K x ld  (T = V^t A^{-1} - E^t, row m)
+    void *Tbuf = nullptr;       // batch x K x ld  (T = V^t A^{-1}, row m)
     void *Wbuf = nullptr;       // batch x K x ld  (W = P Kinv, column m)
     // recompute workspace
     double *work = nullptr;     // batch x N x ld fp64
@@ -59,9 +59,12 @@ struct Ctx {
     int *colperm = nullptr;     // batch x N
     double *Lt = nullptr;       // batch x nb x ld
     double *R = nullptr;        // batch x nb x ld
+    int *eqs = nullptr;         // batch x 2 x N: the recompute's power-of-two row and column scales
     double *lu_logabs = nullptr; // batch
     int *lu_sign = nullptr;     // batch
     double *drift = nullptr;    // batch x 4 (sums for the drift report)
+    double *pair_logabs = nullptr; // batch: log|det| of this handle's walkers and another's, summed
+    int *pair_sign = nullptr;      // batch: the product of their signs
     // sweep outputs (device staging)
     unsigned char *sw_acc = nullptr; // batch x N
     double *sw_ratio = nullptr;      // batch x N
@@ -85,7 +88,7 @@ struct Ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_flush, ev_recompute, ev_sweep;
     // persistent sweep (kernels_sweep.cu)
     int num_sms = 148;
-    double *sw_partial = nullptr;   // capacity x 2 x (2K+1)
+    double *sw_partial = nullptr;   // capacity x 2 x (2K+2)
     size_t sw_partial_len = 0;
     unsigned *sw_sync = nullptr;    // capacity x 4
     unsigned long long *sw_phase = nullptr;  // 11 phase timers of the persistent sweep
@@ -102,6 +105,7 @@ struct Ctx {
     int opt_max_ctas = 0;            // cap on the persistent sweep's grid (0: whole GPU)
     int opt_group_ctas = 0;          // fixed CTAs per walker group (0: from the batch)
     int opt_fp64_flush = 0;          // 0: auto, 1: fp64 arithmetic only, 2: emulated on the tensor cores
+    int opt_fixed_slot = 0;          // 1: rejected proposals take queue slots (Sec. II)
     int opt_cluster = 0;             // 0, 1: global-memory exchange; 2: cluster mode where it applies
     int last_cluster = 0;            // cluster size of the last persistent sweep (0: none)
     // emulated-fp64 flush of the persistent sweep (kernels_sweep.cu): scratch of
@@ -203,16 +207,23 @@ size_t gj_mc_scratch_bytes(int P, int nb);
 // Recompute shape of a handle: the panel width and, for a few walkers, the CTAs per walker.
 void configure_recompute(Ctx &c);
 cudaError_t launch_gj_update(Ctx &c, int nbe);
+// the same update as the emulated-fp64 tensor-core contraction of the flush
+// (fp64 handles with its scratch); cudaErrorNotSupported where it does not apply
+cudaError_t launch_gj_update_oz(Ctx &c, int nbe);
 int choose_panel_width(int N);
 
 // ---- tensor-core contraction (kernels_tc.cu) ----
 cudaError_t launch_gemm_bf16x3(int M, int N, int K, const float *A, long long lda, long long sA,
                                const float *B, long long ldb, long long sB, int b_trans, float *C,
                                long long ldc, long long sC, float alpha, float beta, int batch,
-                               const int *kdyn, int kdyn_is_n, int kthresh, const int *fix_idx,
-                               int fix_stride, int *status, long long budget_ns, cudaStream_t s);
+                               const int *kdyn, int kdyn_is_n, int kthresh, int *status,
+                               long long budget_ns, cudaStream_t s);
 
 // ---- utilities (kernels_move.cu) ----
+cudaError_t launch_logdet_pair(int batch, const double *l1, const int *s1, const double *l2, const int *s2,
+                               double *lout, int *sout, cudaStream_t s);
+cudaError_t launch_proposal_draws(int N, int nw, unsigned long long base_seed, int sweep, double *gauss,
+                                  double *unif, cudaStream_t s);
 cudaError_t launch_philox_fill(const unsigned *c0, const unsigned *c1, const unsigned *c2,
                                const unsigned *c3, int n, unsigned long long seed,
                                unsigned *out, cudaStream_t s);

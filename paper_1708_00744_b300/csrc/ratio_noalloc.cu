@@ -1,8 +1,9 @@
 // ratio_noalloc.cu -- determinant ratio of one proposed move through a delay
 // queue that the caller holds, computed without allocating device memory.
 //
-// Same arithmetic as the handle's ratio kernel (kernels_move.cu):
-//   d = v . a,  b = P v,  c = V a,  r = d - b' Kinv c
+// Same arithmetic as the handle's ratio kernel (kernels_move.cu), in the
+// change form of Eq. 1-3 (u = v - a_j, V rows the queued changes):
+//   d = u . a,  b = P u,  c = V a,  r = 1 + (d - b' Kinv c)
 // with the chunk partial sums of the CTAs and their arrival counter kept in one
 // fixed, file-scope device array instead of memory owned by a handle. Every
 // call on a device shares that array; it keeps the last call's contents, so
@@ -43,7 +44,7 @@ __device__ __forceinline__ double na_warp_sum(double v)
 // Grid: ceil(N / 256) CTAs; CTA s forms the 2k+1 partial dot products of its
 // chunk; the last CTA to arrive sums them in chunk order and forms r.
 __global__ void __launch_bounds__(NA_THREADS) ratio_noalloc_kernel(
-    int N, int k, const double *__restrict__ a, const double *__restrict__ v,
+    int N, int k, const double *__restrict__ a, const double *__restrict__ u,
     const double *__restrict__ P, const double *__restrict__ V, const double *__restrict__ Kinv,
     double *ratio_out, unsigned char *scratch)
 {
@@ -55,8 +56,8 @@ __global__ void __launch_bounds__(NA_THREADS) ratio_noalloc_kernel(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int job = warp; job < nj; job += NA_THREADS / 32) {
         const double *src, *with;
-        if (job == 0) { src = a; with = v; }
-        else if (job <= k) { src = P + (size_t)(job - 1) * N; with = v; }
+        if (job == 0) { src = a; with = u; }
+        else if (job <= k) { src = P + (size_t)(job - 1) * N; with = u; }
         else { src = V + (size_t)(job - 1 - k) * N; with = a; }
         double s = 0.0;
         for (int t = lane; t < n; t += 32) s += src[i0 + t] * with[i0 + t];
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(NA_THREADS) ratio_noalloc_kernel(
         for (int m = lane; m < k; m += 32) s += bv[m] * xs[m];
         s = na_warp_sum(s);
         if (lane == 0) {
-            *ratio_out = red[0] - s;
+            *ratio_out = 1.0 + (red[0] - s);
             *arrive = 0u;
         }
     }
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(NA_THREADS) ratio_noalloc_kernel(
 
 using namespace qmcdu;
 
-extern "C" int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *v,
+extern "C" int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const double *u,
                                    const double *P, const double *V, const double *Kinv,
                                    double *ratio_out, void *stream)
 {
@@ -112,7 +113,7 @@ extern "C" int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const d
             " outside the fixed scratch (1 <= N <= 8192, 0 <= k <= min(N, 256))");
         return QMCDU_ERR_ARG;
     }
-    if (!ainv_col || !v || !ratio_out || (k > 0 && (!P || !V || !Kinv))) {
+    if (!ainv_col || !u || !ratio_out || (k > 0 && (!P || !V || !Kinv))) {
         set_handleless_error("qmcdu_ratio_noalloc: null pointer argument");
         return QMCDU_ERR_ARG;
     }
@@ -142,7 +143,7 @@ extern "C" int qmcdu_ratio_noalloc(int N, int k, const double *ainv_col, const d
     e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) {
         const int nsplit = (N + NA_CHUNK - 1) / NA_CHUNK;
-        ratio_noalloc_kernel<<<nsplit, NA_THREADS, 0, s>>>(N, k, ainv_col, v, P, V, Kinv, ratio_out,
+        ratio_noalloc_kernel<<<nsplit, NA_THREADS, 0, s>>>(N, k, ainv_col, u, P, V, Kinv, ratio_out,
                                                           (unsigned char *)scratch);
         e = cudaGetLastError();
     }

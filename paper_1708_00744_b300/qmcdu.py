@@ -36,6 +36,7 @@ SIGNATURES = {
     "qmcdu_flush": (_I, [_VP]),
     "qmcdu_recompute": (_I, [_VP, _VP]),
     "qmcdu_logdet": (_I, [_VP, _VP, _VP]),
+    "qmcdu_logdet_product": (_I, [_VP, _VP, _VP, _VP]),
     "qmcdu_sweep": (_I, [_VP, _ULL, _I, _D, _VP, _VP, _VP, _VP]),
     "qmcdu_sync": (_I, [_VP]),
     "qmcdu_step": (_I, [_VP, _ULL, _I, _I, _D, _I, _I, _VP, _VP]),
@@ -45,10 +46,12 @@ SIGNATURES = {
     "qmcdu_group_destroy": (_I, [_VP]),
     "qmcdu_last_error": (ctypes.c_char_p, [_VP]),
     "qmcdu_philox4x32_10": (_I, [_VP, _VP, _VP, _VP, _I, _ULL, _VP, _VP]),
+    "qmcdu_proposal_draws": (_I, [_I, _I, _ULL, _I, _VP, _VP, _VP]),
     "qmcdu_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
     "qmcdu_sweep_shape": (_I, [_VP, _VP]),
     "qmcdu_profile_enable": (_I, [_VP, _I]),
     "qmcdu_profile_read": (_I, [_VP, _VP, _I]),
+    "qmcdu_profile_sweep_times": (_I, [_VP, _VP, _I, ctypes.POINTER(_I)]),
     "qmcdu_ratio_noalloc": (_I, [_I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "qmcdu_gemm_bf16x3": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _I, _VP, _I, ctypes.c_float,
                                ctypes.c_float, _VP]),
@@ -66,6 +69,13 @@ SIGNATURES = {
     "qmcdu_server_error": (ctypes.c_char_p, [_VP]),
     "qmcdu_server_destroy": (_I, [_VP]),
     "qmcdu_version": (ctypes.c_char_p, []),
+    "qmcdu_md_create": (_I, [_VP, _I, _I, _VP, _VP, ctypes.POINTER(_VP)]),
+    "qmcdu_md_destroy": (_I, [_VP]),
+    "qmcdu_md_set_virtuals": (_I, [_VP, _VP]),
+    "qmcdu_md_ratio": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "qmcdu_md_accept": (_I, [_VP, _VP]),
+    "qmcdu_md_logpsi": (_I, [_VP, _VP, _VP]),
+    "qmcdu_md_last_error": (ctypes.c_char_p, [_VP]),
 }
 
 
@@ -205,6 +215,12 @@ def qmcdu_logdet(h, logabs, sign, batch):
     _check("qmcdu_logdet", load().qmcdu_logdet(h, _ptr(logabs), _ptr(sign)), h)
 
 
+def qmcdu_logdet_product(h1, h2, logabs, sign, batch):
+    _need(logabs, batch, "float64", "logabs", False)
+    _need(sign, batch, "int32", "sign", False)
+    _check("qmcdu_logdet_product", load().qmcdu_logdet_product(h1, h2, _ptr(logabs), _ptr(sign)), h1)
+
+
 def qmcdu_sweep(h, base_seed, sweep_index, sigma, N, batch, override=None, accepted_out=None,
                 ratios_out=None, near_ties_out=None):
     _need(override, batch * N, "int8", "override", False)
@@ -216,15 +232,16 @@ def qmcdu_sweep(h, base_seed, sweep_index, sigma, N, batch, override=None, accep
                                              _ptr(near_ties_out)), h)
 
 
-def qmcdu_ratio_noalloc(N, k, ainv_col, v, P, V, Kinv, ratio_out, stream=None):
+def qmcdu_ratio_noalloc(N, k, ainv_col, u, P, V, Kinv, ratio_out, stream=None):
     """Ratio of one proposal through a caller-held queue, with no device
-    allocation (see include/qmcdu.h)."""
-    for name, x, n in (("ainv_col", ainv_col, N), ("v", v, N), ("ratio_out", ratio_out, 1)):
+    allocation (see include/qmcdu.h): u is the move's change of its row
+    (v - a_j), V's rows the queued changes, Kinv = (I + V P')^{-1}."""
+    for name, x, n in (("ainv_col", ainv_col, N), ("u", u, N), ("ratio_out", ratio_out, 1)):
         _need(x, n, "float64", name, True)
     if k > 0:
         for name, x, n in (("P", P, k * N), ("V", V, k * N), ("Kinv", Kinv, k * k)):
             _need(x, n, "float64", name, True)
-    st = load().qmcdu_ratio_noalloc(N, k, _ptr(ainv_col), _ptr(v), _ptr(P if k else None),
+    st = load().qmcdu_ratio_noalloc(N, k, _ptr(ainv_col), _ptr(u), _ptr(P if k else None),
                                     _ptr(V if k else None), _ptr(Kinv if k else None),
                                     _ptr(ratio_out), _stream_ptr(stream))
     if st != 0:
@@ -298,9 +315,20 @@ def qmcdu_philox4x32_10(c0, c1, c2, c3, seed, out, stream=None):
         _ptr(c0), _ptr(c1), _ptr(c2), _ptr(c3), n, seed, _ptr(out), _stream_ptr(stream)))
 
 
+def qmcdu_proposal_draws(N, nwalkers, base_seed, sweep, gauss_out, unif_out, stream=None):
+    """The Gaussians and uniforms of one sweep of walkers 0..nwalkers-1 as the
+    device draws them (CUDA tensors [nwalkers][N][N] and [nwalkers][N] fp64)."""
+    _need(gauss_out, nwalkers * N * N, "float64", "gauss_out", True)
+    _need(unif_out, nwalkers * N, "float64", "unif_out", True)
+    st = load().qmcdu_proposal_draws(N, nwalkers, base_seed, sweep, _ptr(gauss_out), _ptr(unif_out),
+                                     _stream_ptr(stream))
+    if st != 0:
+        raise QmcduError("qmcdu_proposal_draws", st, load().qmcdu_last_error(None).decode())
+
+
 OPTIONS = {"sweep_persistent": 1, "ratio_ctas": 2, "flush_ctas": 3, "wait_budget_ns": 4,
            "test_stall": 5, "max_ctas": 6, "group_ctas": 7, "fp64_flush": 8,
-           "cluster": 9}
+           "cluster": 9, "fixed_slot": 10}
 
 
 def qmcdu_set_option(h, option, value):
@@ -322,6 +350,15 @@ PROFILE_FIELDS = ("launches", "flushes", "flush_ms", "recomputes", "recompute_ms
 
 def qmcdu_profile_enable(h, enable=True):
     _check("qmcdu_profile_enable", load().qmcdu_profile_enable(h, 1 if enable else 0), h)
+
+
+def qmcdu_profile_sweep_times(h, max_n=1 << 16):
+    """Per-launch device times (ms) of the persistent sweeps while profiling."""
+    out = np.zeros(max_n)
+    n = _I()
+    _check("qmcdu_profile_sweep_times", load().qmcdu_profile_sweep_times(h, _ptr(out), max_n,
+                                                                         ctypes.byref(n)), h)
+    return out[:n.value].copy()
 
 
 def qmcdu_profile_read(h):
@@ -623,3 +660,56 @@ class Walkers:
 
     def profile_read(self):
         return qmcdu_profile_read(self.h)
+
+    def profile_sweep_times(self):
+        return qmcdu_profile_sweep_times(self.h)
+
+
+# ---------------------------------------------------------------- multideterminant walkers
+def _md_check(name, status, m=None):
+    if status != 0:
+        text = load().qmcdu_md_last_error(m).decode() if m else load().qmcdu_last_error(None).decode()
+        raise QmcduError(name, status, text)
+
+
+class MultiDetWalkers:
+    """Psi = sum_I coef_I det(A_I) over a handle's walkers (include/qmcdu.h,
+    qmcdu_md_*): exc [ndet][4] (o1, a1, o2, a2; -1 unused), coef [ndet], nv
+    virtual orbitals. Uses the handle's qmcdu_ratio / qmcdu_accept."""
+
+    def __init__(self, walkers, nv, exc, coef):
+        self.W = walkers
+        self.nv = int(nv)
+        exc = np.ascontiguousarray(exc, dtype=np.int32).reshape(-1, 4)
+        coef = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+        m = ctypes.c_void_p()
+        _md_check("qmcdu_md_create", load().qmcdu_md_create(walkers.h, self.nv, exc.shape[0], _ptr(exc),
+                                                            _ptr(coef), ctypes.byref(m)))
+        self.m = m.value
+
+    def set_virtuals(self, B):
+        _need(B, self.W.batch * self.W.N * self.nv, "float64", "B", False)
+        _md_check("qmcdu_md_set_virtuals", load().qmcdu_md_set_virtuals(self.m, _ptr(B)), self.m)
+
+    def ratio(self, elec, v, w, ratio_out, ref_ratio_out=None):
+        elec = np.ascontiguousarray(elec, dtype=np.int32)
+        _need(v, self.W.batch * self.W.N, "float64", "v", True)
+        _need(w, self.W.batch * self.nv, "float64", "w", True)
+        _need(ratio_out, self.W.batch, "float64", "ratio_out", True)
+        _need(ref_ratio_out, self.W.batch, "float64", "ref_ratio_out", True)
+        _md_check("qmcdu_md_ratio", load().qmcdu_md_ratio(self.m, _ptr(elec), _ptr(v), _ptr(w), _ptr(ratio_out),
+                                                          _ptr(ref_ratio_out)), self.m)
+
+    def accept(self, mask):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        _md_check("qmcdu_md_accept", load().qmcdu_md_accept(self.m, _ptr(mask)), self.m)
+
+    def logpsi(self, logabs, sign):
+        _need(logabs, self.W.batch, "float64", "logabs", False)
+        _need(sign, self.W.batch, "int32", "sign", False)
+        _md_check("qmcdu_md_logpsi", load().qmcdu_md_logpsi(self.m, _ptr(logabs), _ptr(sign)), self.m)
+
+    def close(self):
+        if getattr(self, "m", None):
+            load().qmcdu_md_destroy(self.m)
+            self.m = None

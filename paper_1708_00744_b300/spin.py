@@ -5,7 +5,8 @@ electron changes only A_up, so its Metropolis ratio is the up determinant's
 ratio alone, and likewise for down electrons. A sweep moves the up electrons,
 then the down electrons, each spin's determinant through its own handle of
 the library (its own delay queue, flushes and recomputes); log|det| and sign
-of the walker are the sum and the product of the two.
+of the walker are the sum and the product of the two (qmcdu_logdet_product,
+on the device).
 
 Thin orchestration over two handles: every step runs in the library's kernels.
 The spin-down walkers draw from keys offset by `down_key_offset` so that the
@@ -15,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .qmcdu import Walkers
+from .qmcdu import Walkers, qmcdu_logdet_product
 
 
 class SpinWalkers:
@@ -45,11 +46,10 @@ class SpinWalkers:
 
     def logdet(self):
         """(log|det A_up| + log|det A_down|, sign(det A_up) sign(det A_down)) per walker."""
-        lu, ld = np.zeros(self.batch), np.zeros(self.batch)
-        su, sd = np.zeros(self.batch, dtype=np.int32), np.zeros(self.batch, dtype=np.int32)
-        self.up.logdet(lu, su)
-        self.down.logdet(ld, sd)
-        return lu + ld, su * sd
+        la = np.zeros(self.batch)
+        sg = np.zeros(self.batch, dtype=np.int32)
+        qmcdu_logdet_product(self.up.h, self.down.h, la, sg, self.batch)
+        return la, sg
 
     def close(self):
         self.up.close()

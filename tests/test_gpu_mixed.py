@@ -1,12 +1,23 @@
 """Mixed precision: A^{-1}, the panels and the flush in fp32 (SIMT or
-split-bf16 x3 on the tensor cores), with the k x k inverse, ratios, log-det and
-the recompute in fp64, against the fp64 oracle on the same trajectory (the
-oracle's decisions are replayed so that both walk the same path).
+split-bf16 x3 on the tensor cores), with the k x k algebra, ratios, log-det and
+the recompute in fp64, against the fp64 oracle on the same walk.
 
-Stated bound: a running inverse kept in working precision u_w differs from the
-exact one by about N u_w kappa_1(A) (the forward error of a linear solve), so
-ratios (|r - r_ref| / max(1, |r_ref|)), A^{-1} (norm-wise) and log|det| must
-agree within 8 N u_w kappa_1 with u_w = 2^-24 (fp32) or 2^-16 (split bf16)."""
+Decisions. A first run replays every oracle decision and measures the largest
+ratio error e of the walk; a second run replays only the decisions within 2e
+of a tie (|min(1, r^2) - u| < 2e, where the working precision may flip them)
+and every other decision must equal the oracle's bit for bit. The number of
+replayed decisions is reported.
+
+Bounds. A running inverse kept in working precision u_w (2^-24 fp32, 2^-16
+split bf16) errs by about u_w kappa_1(A) times a factor that depends on the
+walk; the factor is fitted here per precision, proposal width sigma and
+recompute interval R from the measured errors of these seeded walks (change
+form of Eq. 1-4: the queue holds the small changes u = v - a_j), and each
+metric is held to BOUND_MARGIN = 10 times the worst measured factor, so that a
+tenfold regression fails. Split bf16 at sigma = 1 (VMC-like) is outside any
+useful tolerance (ratio errors reach 0.16): the library documents it as a
+DMC-like (small sigma) precision only.
+"""
 import numpy as np
 import pytest
 
@@ -18,77 +29,150 @@ from gpu_common import logdet_err, need_gpu, rel_norm_err, rel_ratio_err, walker
 pytestmark = pytest.mark.gpu
 
 U_W = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16}
+BOUND_MARGIN = 10.0
+
+# worst measured err / (u_w kappa_1) per (precision, sigma, R): (ratio, A^{-1},
+# log|det|); R = 2 for the two-sweep walks without a recompute in between
+FIT = {
+    ("fp32", 0.1, 2): (2.0e-3, 2.2e-3, 2.2e-6),
+    ("fp32", 1.0, 2): (2.3, 2.0e-1, 7.4e-4),
+    ("fp32", 0.1, 1): (1.1e-3, 4.7e-5, 2.7e-9),
+    ("fp32", 0.1, 5): (1.2e-3, 2.7e-4, 1.1e-7),
+    ("fp32", 0.1, 20): (1.2e-2, 4.2e-3, 1.7e-6),
+    ("fp32", 1.0, 1): (6.8e-2, 1.9e-4, 2.5e-8),
+    ("fp32", 1.0, 5): (9.9e-1, 3.3e-3, 7.3e-7),
+    ("fp32", 1.0, 20): (9.9e-1, 1.7e-2, 1.8e-7),
+    ("bf16x3", 0.1, 2): (7.7e-6, 8.7e-6, 8.4e-9),
+    ("bf16x3", 1.0, 2): (9.0e-3, 7.7e-4, 2.9e-6),
+    ("bf16x3", 0.1, 1): (1.3e-4, 5.3e-6, 1.3e-9),
+    ("bf16x3", 0.1, 5): (1.3e-4, 2.3e-5, 2.8e-8),
+    ("bf16x3", 0.1, 20): (1.3e-3, 8.1e-4, 8.2e-7),
+    ("bf16x3", 1.0, 1): (6.8e-3, 2.2e-5, 4.0e-9),
+    ("bf16x3", 1.0, 5): (3.6e-2, 4.7e-4, 1.4e-7),
+    ("bf16x3", 1.0, 20): (4.5e-2, 3.5e-3, 8.8e-7),
+}
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
-@pytest.mark.parametrize("N,K,sigma", [(128, 16, 0.1), (300, 32, 1.0), (640, 64, 0.1)])
-def test_mixed_precision_within_stated_bound(precision, N, K, sigma):
-    need_gpu()
-    batch, nsweeps, base = 2, 2, 900 + N
-    A, G, U = walker_inputs(base, batch, N, nsweeps)
-    refs = [oracle.sweeps(oracle.SM, A[b], G[b], U[b], sigma) for b in range(batch)]
-    override = np.stack([r["accepted"].astype(np.int8) for r in refs], axis=1)   # [s][b][N]
+# the same for the drift a recompute finds after R sweeps (the largest over the
+# walk): (A^{-1} Frobenius-relative, log|det| absolute)
+FIT_DRIFT = {
+    ("fp32", 0.1, 1): (7.6e-4, 8.8e-4),
+    ("fp32", 0.1, 5): (9.6e-4, 4.7e-4),
+    ("fp32", 0.1, 20): (4.2e-3, 2.4e-3),
+    ("fp32", 1.0, 1): (2.2e-2, 1.5e-2),
+    ("fp32", 1.0, 5): (1.4e-1, 1.0e-1),
+    ("fp32", 1.0, 20): (1.7e-2, 3.6e-4),
+    ("bf16x3", 0.1, 1): (5.5e-5, 5.6e-5),
+    ("bf16x3", 0.1, 5): (1.2e-4, 1.4e-4),
+    ("bf16x3", 0.1, 20): (8.1e-4, 1.1e-3),
+    ("bf16x3", 1.0, 1): (2.1e-3, 2.3e-3),
+    ("bf16x3", 1.0, 5): (9.7e-3, 1.5e-2),
+    ("bf16x3", 1.0, 20): (3.5e-3, 1.8e-3),
+}
+
+
+def bounds(precision, sigma, R, kappa, table=FIT):
+    return [BOUND_MARGIN * c * U_W[precision] * kappa for c in table[(precision, sigma, R)]]
+
+
+def near_tie_override(ref, U, margin):
+    """-1 (decide) everywhere except the decisions within `margin` of a tie,
+    which replay the oracle's."""
+    p = np.minimum(1.0, ref["ratios"] ** 2)
+    near = np.abs(p - U) < margin
+    ov = np.full(U.shape, -1, dtype=np.int8)
+    ov[near] = ref["accepted"][near].astype(np.int8)
+    return ov, int(near.sum())
+
+
+def _run(precision, N, K, A, base, sigma, nsweeps, overrides, max_ctas=None, R=None):
+    """nsweeps sweeps of the walkers (decisions from overrides[s] [batch][N]);
+    returns ratios, accept masks, the inverse, log-det and sign after the last
+    sweep (before any recompute of it) and the largest recompute drift."""
+    batch = A.shape[0]
     W = Walkers(N, K, precision, batch)
+    if max_ctas:
+        W.set_option("max_ctas", max_ctas)
     W.set_matrix(A)
     acc = np.zeros((nsweeps, batch, N), dtype=np.uint8)
     rat = np.zeros((nsweeps, batch, N))
-    for s in range(nsweeps):
-        W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s]), accepted_out=acc[s],
-                ratios_out=rat[s])
     Ai = np.zeros((batch, N, N))
     la = np.zeros(batch)
     sg = np.zeros(batch, dtype=np.int32)
-    W.get_inverse(Ai)
-    W.logdet(la, sg)
-    drift = np.zeros((batch, 2))
-    W.recompute(drift)
+    drift_max = np.zeros((batch, 2))
+    for s in range(nsweeps):
+        W.sweep(base, s, sigma, override=np.ascontiguousarray(overrides[s]), accepted_out=acc[s],
+                ratios_out=rat[s])
+        if s == nsweeps - 1:
+            W.get_inverse(Ai)
+            W.logdet(la, sg)
+        if R and (s + 1) % R == 0:
+            d = np.zeros((batch, 2))
+            W.recompute(d)
+            drift_max = np.maximum(drift_max, d)
+    shape = W.sweep_shape()
     W.close()
+    return dict(acc=acc, rat=rat, Ainv=Ai, logabs=la, sign=sg, drift=drift_max, shape=shape)
+
+
+def _two_pass(precision, N, K, A, G, U, base, sigma, nsweeps, max_ctas=None, R=None):
+    batch = A.shape[0]
+    refs = [oracle.sweeps(oracle.SM, A[b], G[b], U[b], sigma) for b in range(batch)]
+    full = np.stack([r["accepted"].astype(np.int8) for r in refs], axis=1)     # [s][b][N]
+    first = _run(precision, N, K, A, base, sigma, nsweeps, full, max_ctas, R)
+    e = max(rel_ratio_err(first["rat"][:, b], refs[b]["ratios"]) for b in range(batch))
+    ovs, nrep = [], 0
+    for b in range(batch):
+        ov, n = near_tie_override(refs[b], U[b], 2.0 * e)
+        ovs.append(ov)
+        nrep += n
+    second = _run(precision, N, K, A, base, sigma, nsweeps, np.stack(ovs, axis=1), max_ctas, R)
+    for b in range(batch):
+        assert np.array_equal(second["acc"][:, b].astype(bool), refs[b]["accepted"]), b
+    return refs, second, nrep
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("N,K,sigma", [(128, 16, 0.1), (300, 32, 1.0), (640, 64, 0.1), (300, 32, 0.1),
+                                       (128, 16, 1.0)])
+def test_mixed_precision_within_fitted_bound(precision, N, K, sigma):
+    need_gpu()
+    batch, nsweeps, base = 2, 2, 900 + N
+    A, G, U = walker_inputs(base, batch, N, nsweeps)
+    refs, out, nrep = _two_pass(precision, N, K, A, G, U, base, sigma, nsweeps)
     for b, ref in enumerate(refs):
         kappa = max(np.linalg.cond(A[b], 1), np.linalg.cond(ref["A"], 1))
-        bound = 8 * N * U_W[precision] * kappa
-        errs = (rel_ratio_err(rat[:, b], ref["ratios"]), rel_norm_err(Ai[b], ref["Ainv"]),
-                logdet_err(la[b], ref["logabs"]))
-        flips = int(np.sum(np.abs(np.minimum(1, ref["ratios"] ** 2) - U[b]) < 2 * errs[0]))
-        print("%s N=%d K=%d sigma=%g walker %d: bound %.1e ratio %.1e inverse %.1e logdet %.1e "
-              "drift %.1e/%.1e decisions within error of a tie %d"
-              % ((precision, N, K, sigma, b, bound) + errs + tuple(drift[b]) + (flips,)))
-        assert np.array_equal(acc[:, b].astype(bool), ref["accepted"])
-        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
-        assert sg[b] == ref["sign"]
+        bnd = bounds(precision, sigma, 2, kappa)
+        errs = (rel_ratio_err(out["rat"][:, b], ref["ratios"]), rel_norm_err(out["Ainv"][b], ref["Ainv"]),
+                logdet_err(out["logabs"][b], ref["logabs"]))
+        print("%s N=%d K=%d sigma=%g walker %d: kappa_1 %.1e | ratio %.1e (bound %.1e) inverse %.1e "
+              "(%.1e) logdet %.1e (%.1e) | decisions replayed near a tie %d of %d"
+              % (precision, N, K, sigma, b, kappa, errs[0], bnd[0], errs[1], bnd[1], errs[2], bnd[2],
+                 nrep, batch * nsweeps * N))
+        assert errs[0] < bnd[0] and errs[1] < bnd[1] and errs[2] < bnd[2]
+        assert out["sign"][b] == ref["sign"]
 
 
 @pytest.mark.parametrize("N,K", [(768, 32), (700, 48)])
 def test_tensor_core_flush_inside_the_sweep(N, K):
     """Split-bf16 precision with flush blocks of >= 128 columns: the persistent
-    sweep applies Eq. 4 on tcgen05 (ragged last tile for N = 700)."""
+    sweep applies Eq. 4 on tcgen05 (ragged last tile for N = 700). Held to the
+    fitted bound of the bf16 tensor-core flush at sigma = 0.1 over 20 sweeps
+    between recomputes (a two-sweep walk stays well inside it)."""
     need_gpu()
     batch, nsweeps, base, sigma = 2, 2, 1500 + N, 0.1
     A, G, U = walker_inputs(base, batch, N, nsweeps)
-    refs = [oracle.sweeps(oracle.SM, A[b], G[b], U[b], sigma) for b in range(batch)]
-    override = np.stack([r["accepted"].astype(np.int8) for r in refs], axis=1)
-    W = Walkers(N, K, "bf16x3", batch)
-    W.set_option("max_ctas", 4)           # two CTAs per walker: flush blocks of N/2 columns
-    W.set_matrix(A)
-    rat = np.zeros((nsweeps, batch, N))
-    for s in range(nsweeps):
-        W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s]), ratios_out=rat[s])
-    shape = W.sweep_shape()
-    Ai = np.zeros((batch, N, N))
-    la = np.zeros(batch)
-    sg = np.zeros(batch, dtype=np.int32)
-    W.get_inverse(Ai)
-    W.logdet(la, sg)
-    W.close()
+    refs, out, nrep = _two_pass("bf16x3", N, K, A, G, U, base, sigma, nsweeps, max_ctas=4)
+    shape = out["shape"]
     assert shape["col_tile"] == 1000 and shape["flush_ctas"] == 2, shape   # tensor-core flush ran
     for b, ref in enumerate(refs):
         kappa = max(np.linalg.cond(A[b], 1), np.linalg.cond(ref["A"], 1))
-        bound = 8 * N * U_W["bf16x3"] * kappa
-        errs = (rel_ratio_err(rat[:, b], ref["ratios"]), rel_norm_err(Ai[b], ref["Ainv"]),
-                logdet_err(la[b], ref["logabs"]))
-        print("tc flush N=%d K=%d walker %d: bound %.1e ratio %.1e inverse %.1e logdet %.1e"
-              % ((N, K, b, bound) + errs))
-        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
-        assert errs[1] < 1e-2                 # far tighter than the bound: split bf16 is working
+        bnd = bounds("bf16x3", sigma, 20, kappa)
+        errs = (rel_ratio_err(out["rat"][:, b], ref["ratios"]), rel_norm_err(out["Ainv"][b], ref["Ainv"]),
+                logdet_err(out["logabs"][b], ref["logabs"]))
+        print("tc flush N=%d K=%d walker %d: kappa_1 %.1e ratio %.1e (%.1e) inverse %.1e (%.1e) logdet "
+              "%.1e (%.1e) replayed %d" % ((N, K, b, kappa) + sum(zip(errs, bnd), ()) + (nrep,)))
+        assert errs[0] < bnd[0] and errs[1] < bnd[1] and errs[2] < bnd[2]
 
 
 _TRAJ = {}
@@ -98,7 +182,7 @@ def _oracle_trajectory(N, nsweeps, sigma, base):
     key = (N, nsweeps, sigma, base)
     if key not in _TRAJ:
         A, G, U = walker_inputs(base, 1, N, nsweeps)
-        _TRAJ[key] = (A, U[0], oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma))
+        _TRAJ[key] = (A, G[0], U[0], oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma))
     return _TRAJ[key]
 
 
@@ -106,51 +190,34 @@ def _oracle_trajectory(N, nsweeps, sigma, base):
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_error_vs_recompute_interval(precision, sigma):
     """Working-precision walkers recomputed in fp64 every R sweeps, R in
-    {1, 5, 20}, over 20 sweeps of the oracle's trajectory (decisions replayed).
-    Per R: the largest ratio error of the run, the largest drift the recomputes
-    found (the error accumulated over R sweeps, against the fp64 LU of the
-    current A), and A^{-1} and log|det| against the oracle after the last sweep,
-    before its recompute. The running inverse takes one rounding error per
-    update, so the bound grows with the sweeps between recomputes:
-    8 N u_w kappa_1 max(1, R / 2) (the two-sweep bound above at R <= 2)."""
+    {1, 5, 20}, over 20 sweeps. Per R: the largest ratio error of the run, the
+    largest drift the recomputes found (against the fp64 LU of the current A),
+    and A^{-1} and log|det| against the oracle after the last sweep, before
+    its recompute, each within its fitted bound; decisions as described above."""
     need_gpu()
     N, K, nsweeps, base = 512, 32, 20, 4100
-    A, U, ref = _oracle_trajectory(N, nsweeps, sigma, base)
+    A, G, U, ref = _oracle_trajectory(N, nsweeps, sigma, base)
     kappa = max(np.linalg.cond(A[0], 1), np.linalg.cond(ref["A"], 1))
-    override = ref["accepted"].astype(np.int8)
+    full = ref["accepted"].astype(np.int8)[:, None, :]
     for R in (1, 5, 20):
-        W = Walkers(N, K, precision, 1)
+        mc = 1 if precision == "bf16x3" else None     # one CTA: a 512-column flush block, on tcgen05
+        first = _run(precision, N, K, A, base, sigma, nsweeps, full, mc, R)
+        e = rel_ratio_err(first["rat"][:, 0], ref["ratios"])
+        ov, nrep = near_tie_override(ref, U, 2.0 * e)
+        out = _run(precision, N, K, A, base, sigma, nsweeps, ov[:, None, :], mc, R)
         if precision == "bf16x3":
-            W.set_option("max_ctas", 1)    # one CTA: a 512-column flush block, on tcgen05
-        W.set_matrix(A)
-        rat = np.zeros((nsweeps, 1, N))
-        drift_max = np.zeros(2)
-        Ai = np.zeros((1, N, N))
-        la = np.zeros(1)
-        sg = np.zeros(1, dtype=np.int32)
-        for s in range(nsweeps):
-            W.sweep(base, s, sigma, override=np.ascontiguousarray(override[s][None]),
-                    ratios_out=rat[s])
-            if s == nsweeps - 1:
-                W.get_inverse(Ai)
-                W.logdet(la, sg)
-            if (s + 1) % R == 0:
-                drift = np.zeros((1, 2))
-                W.recompute(drift)
-                drift_max = np.maximum(drift_max, drift[0])
-        shape = W.sweep_shape()
-        W.close()
-        if precision == "bf16x3":
-            assert shape["col_tile"] == 1000, shape          # the tensor-core flush ran
-        bound = 8 * N * U_W[precision] * kappa * max(1.0, R / 2.0)
-        errs = (rel_ratio_err(rat[:, 0], ref["ratios"]), rel_norm_err(Ai[0], ref["Ainv"]),
-                logdet_err(la[0], ref["logabs"]))
-        flips = int(np.sum(np.abs(np.minimum(1, ref["ratios"] ** 2) - U) < 2 * errs[0]))
-        print("R-study %s sigma=%g R=%d: acceptance %.3f kappa_1 %.1e bound %.1e | ratio %.1e "
-              "inverse %.1e logdet %.1e | drift logdet %.1e inverse %.1e | decisions within "
-              "error of a tie %d of %d"
-              % ((precision, sigma, R, ref["accepted"].mean(), kappa, bound) + errs +
-                 tuple(drift_max) + (flips, nsweeps * N)))
-        assert errs[0] < bound and errs[1] < bound and errs[2] < bound
-        assert drift_max[0] < bound and drift_max[1] < bound
-        assert sg[0] == ref["sign"]
+            assert out["shape"]["col_tile"] == 1000, out["shape"]      # the tensor-core flush ran
+        assert np.array_equal(out["acc"][:, 0].astype(bool), ref["accepted"])
+        bnd = bounds(precision, sigma, R, kappa)
+        errs = (rel_ratio_err(out["rat"][:, 0], ref["ratios"]), rel_norm_err(out["Ainv"][0], ref["Ainv"]),
+                logdet_err(out["logabs"][0], ref["logabs"]))
+        drift = out["drift"][0]
+        print("R-study %s sigma=%g R=%d: acceptance %.3f kappa_1 %.1e | ratio %.1e (bound %.1e) inverse "
+              "%.1e (%.1e) logdet %.1e (%.1e) | drift logdet %.1e inverse %.1e | decisions replayed near "
+              "a tie %d of %d"
+              % (precision, sigma, R, ref["accepted"].mean(), kappa, errs[0], bnd[0], errs[1], bnd[1],
+                 errs[2], bnd[2], drift[0], drift[1], nrep, nsweeps * N))
+        assert errs[0] < bnd[0] and errs[1] < bnd[1] and errs[2] < bnd[2]
+        dbnd = bounds(precision, sigma, R, kappa, FIT_DRIFT)
+        assert drift[1] < dbnd[0] and drift[0] < dbnd[1], (drift, dbnd)
+        assert out["sign"][0] == ref["sign"]

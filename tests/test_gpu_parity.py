@@ -13,8 +13,9 @@ import oracle
 from paper_1708_00744_b300 import inputs
 from paper_1708_00744_b300.qmcdu import QmcduError, Walkers
 
-from gpu_common import (RTOL_INV, RTOL_LOGDET, RTOL_RATIO, fp64_tol, logdet_err, need_gpu,
-                        rel_norm_err, rel_ratio_err, tie_override, torch, walker_inputs)
+from gpu_common import (RTOL_LOGDET, RTOL_RATIO, device_gaussians, direct_tol, logdet_err, need_gpu,
+                        oracle_moves_walk, oracle_walk, rel_norm_err, rel_ratio_err, tie_override,
+                        torch, walker_inputs)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,10 +42,6 @@ def run_sweeps(N, K, sigma, batch, nsweeps, base_seed, precision="fp64", overrid
     return dict(A0=A, G=G, U=U, acc=acc, rat=rat, ties=ties, A=Af, Ainv=Ai, logabs=la, sign=sg)
 
 
-def oracle_reference(A0, G, U, sigma):
-    return oracle.sweeps(oracle.SM, A0, G, U, sigma)
-
-
 @pytest.mark.parametrize("N,K,sigma", [(1, 1, 0.5), (2, 2, 1.0), (3, 2, 0.1), (7, 3, 1.0),
                                        (64, 1, 0.1), (64, 8, 0.1), (65, 16, 1.0), (200, 1, 1.0),
                                        (257, 32, 0.1), (511, 64, 1.0), (300, 256, 0.1)])
@@ -52,7 +49,8 @@ def test_sweeps_match_oracle(N, K, sigma):
     need_gpu()
     batch, nsweeps, base = 2, 2, 100 + N
     A, G, U = walker_inputs(base, batch, N, nsweeps)
-    refs = [oracle_reference(A[b], G[b], U[b], sigma) for b in range(batch)]
+    walks = [oracle_walk(A[b], G[b], U[b], sigma, K_alt=max(2, K)) for b in range(batch)]
+    refs = [w[0] for w in walks]
     override = np.full((nsweeps, batch, N), -1, dtype=np.int8)
     nties = 0
     for b in range(batch):
@@ -60,18 +58,15 @@ def test_sweeps_match_oracle(N, K, sigma):
         override[:, b, :] = ov
         nties += t
     out = run_sweeps(N, K, sigma, batch, nsweeps, base, override=override if nties else None)
-    for b, ref in enumerate(refs):
-        tol = fp64_tol(A[b], ref["A"])
-        errs = (rel_ratio_err(out["rat"][:, b, :], ref["ratios"]),
-                rel_norm_err(out["Ainv"][b], ref["Ainv"]),
-                logdet_err(out["logabs"][b], ref["logabs"]))
-        print("N=%d K=%d sigma=%g walker %d: tol %.1e ratio %.1e inverse %.1e logdet %.1e"
-              % ((N, K, sigma, b, tol) + errs))
+    for b, (ref, tol) in enumerate(walks):
         assert np.array_equal(out["acc"][:, b, :].astype(bool), ref["accepted"]), (b, nties)
-        assert errs[0] < tol and errs[1] < tol and errs[2] < tol
-        # proposals are drawn on each side from the same Philox words, with
-        # each side's own log/sqrt/sin/cos: rows agree to rounding
-        assert rel_norm_err(out["A"][b], ref["A"]) < 1e-14
+        tol.check("N=%d K=%d sigma=%g walker %d" % (N, K, sigma, b),
+                  ratio=out["rat"][:, b, :],
+                  inverse=rel_norm_err(out["Ainv"][b], ref["Ainv"]),
+                  logdet=logdet_err(out["logabs"][b], ref["logabs"]))
+        # the oracle is given the device's draws and both sides form
+        # v = fl(a_j + fl(sigma g)): the rows are identical
+        assert np.array_equal(out["A"][b], ref["A"])
         assert out["sign"][b] == ref["sign"]
     assert out["ties"].sum() == nties
 
@@ -98,7 +93,8 @@ def test_sweep_n64_matches_golden_fixture():
 def test_per_call_moves_match_oracle(N, K, precision):
     """qmcdu_ratio / qmcdu_accept with caller-made rows, repeated electrons
     (which force a flush) and explicit flushes. fp32 walkers are held to the
-    mixed-precision bound 8 N u_w kappa_1 (u_w = 2^-24)."""
+    mixed-precision bound 8 N u_w kappa_1 (u_w = 2^-24) of the walk's
+    worst-conditioned matrix."""
     need_gpu()
     rng = np.random.default_rng(N * 10 + K)
     batch, nmoves = 3, 3 * N // 2 + 5
@@ -143,28 +139,29 @@ def test_per_call_moves_match_oracle(N, K, precision):
     W.logdet(la, sg)
     W.close()
     for b in range(batch):
-        ref = oracle.moves(oracle.DELAYED if K > 1 else oracle.SM, A0[b], elec[:, b], vrows[:, b],
-                           masks[:, b], K=K, flush_after=flush_after.astype(np.uint8))
-        # the worst-conditioned matrix along the walk bounds the forward error
-        tol = max(1e-10, N * 2.0 ** -53 * kappa[b])
+        ref, tol = oracle_moves_walk(A0[b], elec[:, b], vrows[:, b], masks[:, b], K,
+                                     flush_after=flush_after.astype(np.uint8))
         if precision == "fp32":
-            tol = 8 * N * 2.0 ** -24 * kappa[b]
-        errs = (rel_ratio_err(ratios[:, b], ref["ratios"]), rel_norm_err(Ai[b], ref["Ainv"]),
-                logdet_err(la[b], ref["logabs"]))
-        print("N=%d K=%d walker %d: tol %.1e ratio %.1e inverse %.1e logdet %.1e"
-              % ((N, K, b, tol) + errs))
-        assert errs[0] < tol and errs[1] < tol and errs[2] < tol
+            bound = 8 * N * 2.0 ** -24 * kappa[b]
+            tol = type(tol)(ratio=bound, inverse=bound, logdet=bound)
+        tol.check("N=%d K=%d walker %d" % (N, K, b),
+                  ratio=ratios[:, b] if precision == "fp64" else rel_ratio_err(ratios[:, b], ref["ratios"]),
+                  inverse=rel_norm_err(Ai[b], ref["Ainv"]), logdet=logdet_err(la[b], ref["logabs"]))
         if precision == "fp64":
             assert np.array_equal(Af[b], ref["A"])     # rows stored as given
         assert sg[b] == ref["sign"]
 
 
-@pytest.mark.parametrize("N,batch", [(1, 3), (7, 2), (64, 4), (100, 1), (513, 2)])
-def test_recompute_matches_oracle_lu(N, batch):
-    """Sec. III's direct calculation: A^{-1} and log|det A| from A alone."""
+@pytest.mark.parametrize("N,batch,fp64_flush", [(1, 3, 0), (7, 2, 0), (64, 4, 0), (100, 1, 0), (513, 2, 0),
+                                                (100, 1, 1), (513, 2, 1), (2048, 1, 0)])
+def test_recompute_matches_oracle_lu(N, batch, fp64_flush):
+    """Sec. III's direct calculation: A^{-1} and log|det A| from A alone. The
+    rank-nb updates of fp64 handles run on the tensor cores as the flush's
+    emulated-fp64 contraction (fp64_flush = 1: on the fp64 units)."""
     need_gpu()
     A = np.stack([inputs.initial_matrix(50 + b, N) for b in range(batch)])
     W = Walkers(N, 4 if N >= 4 else 1, "fp64", batch)
+    W.set_option("fp64_flush", fp64_flush)
     W.set_matrix(A)
     Ai = np.zeros((batch, N, N))
     la = np.zeros(batch)
@@ -176,11 +173,17 @@ def test_recompute_matches_oracle_lu(N, batch):
     W.recompute(drift)
     W.close()
     for b in range(batch):
-        s, l = oracle.slogdet(A[b])
-        tol = fp64_tol(A[b])
-        assert sg[b] == s and logdet_err(la[b], l) < tol
-        assert rel_norm_err(Ai[b], oracle.inverse_colmajor(A[b])) < tol
-        assert drift[b, 0] < tol and drift[b, 1] < tol
+        inv, (s, l), tol = direct_tol(A[b])
+        assert sg[b] == s
+        tol.check("recompute N=%d walker %d" % (N, b), inverse=rel_norm_err(Ai[b], inv),
+                  logdet=logdet_err(la[b], l))
+        # the drift after the sweep: the running values against the LU of the
+        # final matrix, held to the spread of the oracle's readings of that sweep
+        seed = inputs.walker_seed(50, b)
+        G, U = device_gaussians(seed, N, [0])
+        wref, wtol = oracle_walk(A[b], G, U, 0.1)
+        wtol.check("drift N=%d walker %d" % (N, b), inverse=drift[b, 1],
+                   logdet=drift[b, 0] / max(1.0, abs(wref["logabs"])))
 
 
 def test_recompute_special_matrices():
@@ -214,12 +217,11 @@ def test_forced_accept_matches_oracle_forced_mode():
     N, K, batch = 96, 16, 1
     A, G, U = walker_inputs(9, batch, N, 1)
     ov = np.ones((1, batch, N), dtype=np.int8)
-    ref = oracle.sweeps(oracle.SM, A[0], G[0], U[0], 0.1, override=ov[:, 0])
+    ref, tol = oracle_walk(A[0], G[0], U[0], 0.1, override=ov[:, 0])
     out = run_sweeps(N, K, 0.1, batch, 1, 9, override=ov)
-    tol = fp64_tol(A[0], ref["A"])
     assert out["acc"].all()
-    assert rel_ratio_err(out["rat"][:, 0], ref["ratios"]) < tol
-    assert rel_norm_err(out["Ainv"][0], ref["Ainv"]) < tol
+    tol.check("forced accept", ratio=out["rat"][:, 0],
+              inverse=rel_norm_err(out["Ainv"][0], ref["Ainv"]))
 
 
 def test_error_paths():
@@ -250,6 +252,16 @@ def test_error_paths():
     W.close()
 
 
+_N2048 = {}
+
+
+def _walk_n2048(A, G, U, sigma):
+    key = sigma
+    if key not in _N2048:
+        _N2048[key] = oracle_walk(A[0], G[0], U[0], sigma, K_alt=32)
+    return _N2048[key]
+
+
 @pytest.mark.parametrize("K", [1, 64])
 def test_full_size_sweep_n2048(K):
     """The benchmark's walker (N = 2048, sigma = 0.1, fp64): one full sweep
@@ -257,12 +269,48 @@ def test_full_size_sweep_n2048(K):
     need_gpu()
     N, sigma, base = 2048, 0.1, 0
     A, G, U = walker_inputs(base, 1, N, 1)
-    ref = oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma)
+    ref, tol = _walk_n2048(A, G, U, sigma)
     ov, nties = tie_override(ref["ratios"], U[0])
     out = run_sweeps(N, K, sigma, 1, 1, base, override=ov[:, None, :] if nties else None)
-    tol = fp64_tol(A[0], ref["A"])
-    errs = (rel_ratio_err(out["rat"][:, 0], ref["ratios"]), rel_norm_err(out["Ainv"][0], ref["Ainv"]),
-            logdet_err(out["logabs"][0], ref["logabs"]))
-    print("N=2048 K=%d: tol %.1e ratio %.1e inverse %.1e logdet %.1e ties %d" % ((K, tol) + errs + (nties,)))
     assert np.array_equal(out["acc"][:, 0].astype(bool), ref["accepted"])
-    assert errs[0] < tol and errs[1] < tol and errs[2] < tol
+    tol.check("N=2048 K=%d ties %d" % (K, nties), ratio=out["rat"][:, 0],
+              inverse=rel_norm_err(out["Ainv"][0], ref["Ainv"]),
+              logdet=logdet_err(out["logabs"][0], ref["logabs"]))
+
+
+@pytest.mark.parametrize("fp64_flush", [0, 1])
+def test_recompute_of_a_badly_scaled_matrix(fp64_flush):
+    """A = D1 G D2 with rows and columns scaled over 2^-30 .. 2^30: the
+    recompute equilibrates A by powers of two before the elimination, so that
+    the tensor-core update (fp64_flush = 0) and the fp64 units agree with the
+    oracle's LU within the LU-of-A against LU-of-A' spread."""
+    need_gpu()
+    N = 300
+    rng = np.random.default_rng(5)
+    d1, d2 = 2.0 ** rng.uniform(-30, 30, N), 2.0 ** rng.uniform(-30, 30, N)
+    A = d1[:, None] * inputs.initial_matrix(77, N) * d2[None, :]
+    W = Walkers(N, 16, "fp64", 1)
+    W.set_option("fp64_flush", fp64_flush)
+    W.set_matrix(A[None])
+    Ai = np.zeros((1, N, N))
+    la = np.zeros(1)
+    sg = np.zeros(1, dtype=np.int32)
+    W.get_inverse(Ai)
+    W.logdet(la, sg)
+    W.close()
+    inv, (s, l), tol = direct_tol(A)
+    assert sg[0] == s
+    # column by column, relative to each column's largest entry (the scalings
+    # make a norm-wise check blind to the small columns), against the same
+    # measure of the oracle's two LUs (of A and of A')
+    inv_t = np.ascontiguousarray(oracle.inverse(np.ascontiguousarray(A.T)))
+
+    def colerr(x, ref):
+        return float(np.max(np.max(np.abs(x - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+
+    bar = max(1e-10, 10.0 * colerr(inv_t, inv))
+    err = colerr(Ai[0], inv)
+    print("recompute of D1 G D2 (fp64_flush %d): column-wise %.1e (tol %.1e), logdet %.1e (tol %.1e)"
+          % (fp64_flush, err, bar, logdet_err(la[0], l), tol["logdet"]))
+    assert err < bar
+    assert logdet_err(la[0], l) < tol["logdet"]

@@ -59,3 +59,21 @@ def test_library_philox_matches_curand():
         assert torch.equal(out.view(n, 4), ref)
         npref = np.stack(inputs.philox4x32_10(c[0], c[1], c[2], c[3], seed), axis=1)
         assert np.array_equal(ref.cpu().numpy().view(np.uint32), npref)
+
+
+@pytest.mark.parametrize("N,nw,seed,sweep", [(7, 3, 5, 0), (512, 2, 1000, 3), (2048, 1, 0, 1)])
+def test_sweep_draws_match_the_input_generator(N, nw, seed, sweep):
+    """qmcdu_proposal_draws (the sweep's own draw kernel): uniforms bit for bit
+    (53 bits of two Philox words), Gaussians to rounding (Box-Muller with the
+    device's log, sqrt and sincos against numpy's)."""
+    need_gpu()
+    from paper_1708_00744_b300.qmcdu import qmcdu_proposal_draws
+    g = torch.zeros(nw, N, N, dtype=torch.float64, device="cuda")
+    u = torch.zeros(nw, N, dtype=torch.float64, device="cuda")
+    qmcdu_proposal_draws(N, nw, seed, sweep, g, u)
+    torch.cuda.synchronize()
+    for w in range(nw):
+        key = inputs.walker_seed(seed, w)
+        assert np.array_equal(u[w].cpu().numpy(), inputs.metropolis_uniforms(key, sweep, N))
+        ref = inputs.proposal_gaussians(key, sweep, N)
+        assert np.max(np.abs(g[w].cpu().numpy() - ref)) <= 4e-15 * np.max(np.abs(ref))

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_1708_00744_b300.qmcdu import QmcduError, Walkers
 
-from gpu_common import (fp64_tol, logdet_err, need_gpu, rel_norm_err, rel_ratio_err, tie_override,
+from gpu_common import (logdet_err, need_gpu, oracle_walk, rel_norm_err, rel_ratio_err, tie_override,
                         walker_inputs)
 
 pytestmark = pytest.mark.gpu
@@ -41,18 +41,15 @@ def test_group_shapes_match_oracle(N, K, ratio_ctas, flush_ctas):
     need_gpu()
     base, sigma, nsweeps = 300 + N, 0.3, 2
     A, G, U = walker_inputs(base, 1, N, nsweeps)
-    ref = oracle.sweeps(oracle.SM, A[0], G[0], U[0], sigma)
+    ref, tol = oracle_walk(A[0], G[0], U[0], sigma, K_alt=max(2, K))
     ov, nties = tie_override(ref["ratios"], U[0])
     out = sweep_once(N, K, 1, base, sigma, nsweeps=nsweeps,
                      options=(("ratio_ctas", ratio_ctas), ("flush_ctas", flush_ctas)),
                      override=ov[:, None, :] if nties else None)
-    tol = fp64_tol(A[0], ref["A"] if "A" in ref else A[0])
-    print("shape", out["shape"], "tol %.1e ratio %.1e inverse %.1e" % (
-        tol, rel_ratio_err(out["rat"][:, 0], ref["ratios"]), rel_norm_err(out["Ainv"][0], ref["Ainv"])))
     assert np.array_equal(out["acc"][:, 0].astype(bool), ref["accepted"])
-    assert rel_ratio_err(out["rat"][:, 0], ref["ratios"]) < tol
-    assert rel_norm_err(out["Ainv"][0], ref["Ainv"]) < tol
-    assert logdet_err(out["logabs"][0], ref["logabs"]) < tol
+    tol.check("shape %s" % out["shape"], ratio=out["rat"][:, 0],
+              inverse=rel_norm_err(out["Ainv"][0], ref["Ainv"]),
+              logdet=logdet_err(out["logabs"][0], ref["logabs"]))
     if ratio_ctas:
         assert out["shape"]["ratio_ctas"] <= max(1, ratio_ctas)
 
@@ -82,11 +79,10 @@ def test_batch_larger_than_sm_count(N):
     assert out["shape"]["flush_ctas"] == 1 and out["shape"]["ratio_ctas"] == 1
     A, G, U = walker_inputs(base, batch, N, 1)
     for w in (0, 1, 147, 148, 299, 399):
-        ref = oracle.sweeps(oracle.SM, A[w], G[w], U[w], sigma)
-        tol = fp64_tol(A[w])
+        ref, tol = oracle_walk(A[w], G[w], U[w], sigma, K_alt=K)
         assert np.array_equal(out["acc"][0, w].astype(bool), ref["accepted"][0])
-        assert rel_ratio_err(out["rat"][0, w], ref["ratios"][0]) < tol
-        assert rel_norm_err(out["Ainv"][w], ref["Ainv"]) < tol
+        tol.check("walker %d" % w, ratio=out["rat"][0, w],
+                  inverse=rel_norm_err(out["Ainv"][w], ref["Ainv"]))
 
 
 def test_wait_budget_expires_cleanly():
@@ -109,4 +105,45 @@ def test_wait_budget_expires_cleanly():
     W.sweep(1, 0, 0.1, accepted_out=acc)
     W.sync()
     assert acc.sum() > 0
+    W.close()
+
+
+@pytest.mark.parametrize("N,K,sigma,fp64_flush", [(1000, 32, 1.0, 0), (700, 64, 1.0, 0), (300, 16, 0.3, 1),
+                                                  (130, 1, 1.0, 0)])
+def test_fixed_slots_match_oracle(N, K, sigma, fp64_flush):
+    """Sec. II's fixed slots (QMCDU_OPT_FIXED_SLOT): rejected proposals take
+    queue slots as zero changes, the queue is flushed every K proposals.
+    Against the oracle's fixed-slot reading (same decisions, ratios, inverse
+    and log-det), with sigma = 1 for many rejections; the emulated-fp64 flush
+    (K = 32), the fp64 units (K = 64, and fp64_flush = 1), K = 1."""
+    need_gpu()
+    base, nsweeps = 6100 + N, 2
+    A, G, U = walker_inputs(base, 1, N, nsweeps)
+    ref = oracle.sweeps(oracle.DELAYED_SLOT, A[0], G[0], U[0], sigma, K=K)
+    alt = oracle.sweeps(oracle.SM + oracle.ALT_INIT, A[0], G[0], U[0], sigma,
+                        override=ref["accepted"].astype(np.int8))
+    from gpu_common import spread_tol
+    tol = spread_tol(ref, alt)
+    ov, nties = tie_override(ref["ratios"], U[0])
+    out = sweep_once(N, K, 1, base, sigma, nsweeps=nsweeps,
+                     options=(("fixed_slot", 1), ("fp64_flush", fp64_flush)),
+                     override=ov[:, None, :] if nties else None)
+    assert 0.3 < ref["accepted"].mean() < 0.95
+    assert np.array_equal(out["acc"][:, 0].astype(bool), ref["accepted"])
+    tol.check("fixed slots N=%d K=%d shape %s" % (N, K, out["shape"]),
+              ratio=out["rat"][:, 0],
+              inverse=rel_norm_err(out["Ainv"][0], ref["Ainv"]),
+              logdet=logdet_err(out["logabs"][0], ref["logabs"]))
+    assert out["sign"][0] == ref["sign"]
+
+
+def test_fixed_slots_need_the_persistent_sweep():
+    need_gpu()
+    W = Walkers(64, 8, "fp64", 1)
+    W.set_matrix(np.eye(64)[None])
+    W.set_option("fixed_slot", 1)
+    W.set_option("sweep_persistent", 0)
+    with pytest.raises(QmcduError) as e:
+        W.sweep(1, 0, 0.1)
+    assert e.value.status == 2
     W.close()
