@@ -122,21 +122,24 @@ def workload_name(a):
 
 
 def config(a, world):
+    def k_of(c):
+        k = c.get("K", a.K)
+        return int(k) if str(k).isdigit() else k
     return {"workload": workload_name(a), "name": a.workload,
-            "classes": [dict(c, K=c.get("K", a.K)) for c in a.classes],
+            "classes": [{"N": c["N"], "batch": c["batch"], "K": k_of(c)} for c in a.classes],
             "precision": a.precision, "sigma": a.sigma, "sweeps_per_step": a.sweeps_per_step,
             "recompute_every_sweeps": a.sweeps_per_step if a.workload == "single" else None,
             "l2": "flushed between timed steps (256 MB write)", "parallelism": "walkers x %d" % world}
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_sample(a, max_moves, K, t_setup=None):
+def cpu_oracle_sample(a, max_moves, K, threads=1):
     """The fp64 CPU oracle (delayed look-ahead + Woodbury with the same K; K = 1:
     Sherman-Morrison) on the first `max_moves` proposals of sweep 0 of one
-    walker. The oracle's setup (an O(N^3) LU inverse of the starting matrix) is
-    timed by a zero-proposal run (unless `t_setup` gives an earlier timing) and
-    subtracted, so that the figure is the update throughput. Returns (accepted,
-    seconds of update work, seconds of setup)."""
+    walker, on `threads` OpenMP threads (0: all cores). The oracle times its
+    update work itself, after its setup (an O(N^3) LU inverse of the starting
+    matrix), so that the figure is the update throughput. Returns (accepted,
+    seconds of update work, threads used)."""
     import oracle
     from paper_1708_00744_b300 import inputs
     A = inputs.initial_matrix(a.seed, a.N)
@@ -144,15 +147,25 @@ def cpu_oracle_sample(a, max_moves, K, t_setup=None):
     U = inputs.metropolis_uniforms(a.seed, 0, a.N)[None]
     method = oracle.SM if K == 1 else oracle.DELAYED
     oracle.build()
-    if t_setup is None:
-        t0 = time.perf_counter()
-        oracle.sweeps(method, A, G, U, a.sigma, K=K, max_moves=0)
-        t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
+    used = oracle.set_threads(threads)
     out = oracle.sweeps(method, A, G, U, a.sigma, K=K, max_moves=max_moves)
-    dt = time.perf_counter() - t0 - t_setup
+    dt = oracle.last_update_seconds()
     acc = int(out["accepted"][0, :max_moves].sum())
-    return acc, max(dt, 1e-9), t_setup
+    return acc, dt, used
+
+
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
 
 
 def cpu_sample_size(a, K, seconds=15.0):
@@ -264,6 +277,8 @@ def run_ours(a, rank, world, local_rank):
         else:
             c["K"] = 64 if a.K == "auto" else int(a.K)
             c.setdefault("ratio_ctas", 0)
+    if a.K == "auto" and len({c["K"] for c in a.classes}) == 1:
+        a.K = str(a.classes[0]["K"])          # the configuration names the K that ran
     barrier()
 
     # ---- handles: one per size class, each on its own stream
@@ -276,7 +291,8 @@ def run_ours(a, rank, world, local_rank):
         W = Walkers(c["N"], c["K"], a.precision, c["batch"], stream=st)
         W.set_option("ratio_ctas", c.get("ratio_ctas", 0))
         W.set_matrix(A0)
-        hs.append(dict(W=W, stream=st, base=base, A0=A0, cls=c))
+        drift = torch.zeros(c["batch"], 2, dtype=torch.float64, device=dev)
+        hs.append(dict(W=W, stream=st, base=base, A0=A0, cls=c, drift=drift))
     s0 = hs[0]["stream"]
     group = qmcdu_group_create([h["W"].h for h in hs]) if len(hs) > 1 else None
     nprop = sum(c["N"] * c["batch"] for c in a.classes) * nsw
@@ -285,7 +301,8 @@ def run_ours(a, rank, world, local_rank):
         if len(handles) == 1 or group is None:
             for h in handles:
                 h["W"].step(h["base"], sweep0, nsw, a.sigma, recompute=recompute,
-                            use_graph=use_graph)
+                            use_graph=use_graph,
+                            drift_out=h.get("drift") if recompute else None)
         else:
             qmcdu_group_step(group, [h["base"] for h in handles], sweep0, nsw, a.sigma, recompute,
                              use_graph)
@@ -299,6 +316,8 @@ def run_ours(a, rank, world, local_rank):
             tot += int(acc.sum())
         return tot
 
+    last = {}     # the drift of the last timed run
+
     def timed(handles, nsteps, nwarm, sweep0, use_graph, profile=False):
         stream = handles[0]["stream"]
         sweep = sweep0
@@ -310,6 +329,7 @@ def run_ours(a, rank, world, local_rank):
             for h in handles:
                 h["W"].profile_enable(True)
         ms, accepted = [], 0
+        drift_max = np.zeros(2)
         for _ in range(nsteps):
             flush_buf.zero_()
             torch.cuda.synchronize()
@@ -322,15 +342,23 @@ def run_ours(a, rank, world, local_rank):
             ev1.synchronize()
             ms.append(ev0.elapsed_time(ev1))
             accepted += accepted_in_step(handles)
-        prof = [h["W"].profile_read() for h in handles] if profile else None
+            if recompute:
+                for h in handles:
+                    if "drift" in h:
+                        drift_max = np.maximum(drift_max, h["drift"].cpu().numpy().max(axis=0))
+        prof = None
         if profile:
+            prof = [dict(h["W"].profile_read(), sweep_times_ms=h["W"].profile_sweep_times().tolist())
+                    for h in handles]
             for h in handles:
                 h["W"].profile_enable(False)
+        last["drift"] = drift_max if recompute else None
         return ms, accepted, prof, sweep
 
     clocks = ClockSampler(local_rank)
     clocks.start()
     ms, accepted, prof, sweep_next = timed(hs, a.steps, a.warmup, 0, use_graph=False, profile=True)
+    drift = last["drift"]
     flush_kinds = [h["W"].sweep_shape()["col_tile"] for h in hs]
     clk = clocks.stop()
     # the same steps replayed from the captured CUDA graph
@@ -373,9 +401,10 @@ def run_ours(a, rank, world, local_rank):
         W1 = Walkers(c["N"], 1, a.precision, c["batch"], stream=s0)
         W1.set_matrix(hs[0]["A0"])
         h1 = [dict(W=W1, stream=s0, base=hs[0]["base"], cls=dict(c, K=1))]
-        ms1, acc1, _, _ = timed(h1, a.k1_steps, 1, 0, use_graph=True)
+        # eager launches: the profile's per-launch events are recorded there
+        ms1, acc1, prof1, _ = timed(h1, a.k1_steps, 1, 0, use_graph=False, profile=True)
         W1.close()
-        k1 = (ms1, acc1)
+        k1 = (ms1, acc1, prof1[0])
 
     # end-of-run reduction over ranks (the only collective): sums of counts,
     # max of times
@@ -387,9 +416,9 @@ def run_ours(a, rank, world, local_rank):
     res = dict(ms=ms, total_ms=red["total_ms"], accepted=red["accepted"], prof=prof, clocks=clk,
                graph_ms=red["graph_ms"], graph_accepted=red["graph_accepted"],
                e2e_s=red["e2e_s"], e2e_acc=red["e2e_acc"], h2d=h2d, d2h=d2h,
-               nprop=nprop, tuned=tuned, k1=None, flush_kinds=flush_kinds)
+               nprop=nprop, tuned=tuned, k1=None, flush_kinds=flush_kinds, drift=drift)
     if k1 is not None:
-        res["k1"] = dict(ms=red["k1_ms"], accepted=red["k1_accepted"])
+        res["k1"] = dict(ms=red["k1_ms"], accepted=red["k1_accepted"], prof=k1[2])
     return res
 
 
@@ -714,6 +743,23 @@ def roofline_for(a, res):
     return out
 
 
+def k1_roofline(a, k1):
+    """K = 1's sweep kernel (Sherman-Morrison, Eq. 2, on the fp64 units):
+    4 N^2 flops per accepted move plus the ratio's 2 x 2 N per proposal,
+    against the fp64 units' peak."""
+    prof = k1.get("prof") or {}
+    ms = prof.get("sweep_kernel_ms", 0.0)
+    if ms <= 0:
+        return None
+    N = a.N
+    props = a.k1_steps * a.sweeps_per_step * N * a.classes[0]["batch"]
+    flops = 4.0 * N * N * k1["accepted"] + 4.0 * N * props
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "sweep_kernel, K = 1", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "derived: 148 SMs x 2 FP64 FMA/clk x 2 x 2032 MHz"}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -725,14 +771,18 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        # K = 32 is what the GPU arm's autotuner settles on for this workload
-        # (one N = 2048 fp64 walker), so that both arms report the same config
-        K = 32 if a.K == "auto" else int(a.K)
-        a.K = K
-        nm = cpu_sample_size(a, K, seconds=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
-        vals, t_setup = [], None
+        # the K the autotuner settles on for this workload, from its host-side
+        # rule (the reference arm runs before, and without, any GPU work)
+        from paper_1708_00744_b300 import autotune
+        K = autotune.default_K(a.N, a.precision) if a.K == "auto" else int(a.K)
+        a.K = str(K)
+        # every host core (the oracle's loops over independent elements run on
+        # OpenMP threads); each step a bounded sample sized from a one-core
+        # estimate, so that the run ends within about a minute
+        nm = cpu_sample_size(a, K, seconds=max(4.0, 120.0 / max(1, a.steps + a.warmup)))
+        vals, used = [], 1
         for it in range(a.warmup + a.steps):
-            acc, dt, t_setup = cpu_oracle_sample(a, nm, K, t_setup)     # setup timed once
+            acc, dt, used = cpu_oracle_sample(a, nm, K, threads=0)
             if it >= a.warmup:
                 vals.append(acc / dt)
         v = float(np.median(vals))
@@ -740,9 +790,11 @@ def main():
                 "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
                 "higher_is_better": True, "dtype": "f64", "data": "synthetic",
                 "config": config(a, 1),
-                "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                                 "sample": "first %d proposals of sweep 0 of one N=%d walker, K=%d "
-                                           "(setup inverse timed apart and excluded)" % (nm, a.N, K)},
+                "cpu_baseline": {"value": v, "unit": "updates/s", "cores": used, "kind": "oracle",
+                                 "host": host_cpu(),
+                                 "sample": "first %d proposals of sweep 0 of one N=%d walker, K=%d, "
+                                           "update work timed by the oracle after its setup inverse; "
+                                           "median of %d steps" % (nm, a.N, K, a.steps)},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -824,9 +876,23 @@ def main():
     if res["k1"]:
         k1v = res["k1"]["accepted"] / (res["k1"]["ms"] * 1e-3)
         line["k1_sherman_morrison"] = {"value": k1v, "unit": "updates/s",
-                                       "ms_per_step": res["k1"]["ms"] / a.k1_steps}
+                                       "ms_per_step": res["k1"]["ms"] / a.k1_steps,
+                                       "roofline": k1_roofline(a, res["k1"])}
         line["speedup_vs_k1"] = value / k1v
     line["roofline"] = roofline_for(a, res)
+    profs0 = res["prof"] or []
+    if len(profs0) == 1 and profs0[0].get("sweep_times_ms"):
+        st = np.asarray(profs0[0]["sweep_times_ms"])
+        line["sweep_latency_ms"] = {"p50": float(np.percentile(st, 50)), "p99": float(np.percentile(st, 99)),
+                                    "sweeps": int(st.size),
+                                    "what": "device time of each persistent sweep launch (CUDA events), "
+                                            "one sweep of the timed walker"}
+    if res.get("drift") is not None:
+        line["error"] = {"drift_logdet": float(res["drift"][0]), "drift_inverse": float(res["drift"][1]),
+                         "what": "largest drift over the timed steps of the running log|det A| "
+                                 "(absolute) and A^{-1} (Frobenius, relative) against the fp64 "
+                                 "recompute that ends each step; element-wise parity with the CPU "
+                                 "oracle at this configuration: tests/test_gpu_headline.py"}
     line["e2e"] = {"value": res["e2e_acc"] / res["e2e_s"], "unit": "updates/s",
                    "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]}
     profs = res["prof"] or []
@@ -842,21 +908,22 @@ def main():
         nprop = a.steps * a.sweeps_per_step * a.N
         line["sweep_phases_us_per_proposal"] = {
             k[6:-3]: v * 1000.0 / nprop for k, v in prof.items()
-            if k.startswith("sweep_") and k.endswith("_ms") and k != "sweep_kernel_ms"}
+            if k.startswith("sweep_") and k.endswith("_ms") and k != "sweep_kernel_ms"
+            and isinstance(v, float)}
     line["clocks"] = res["clocks"]
     if a.gpus == 1:
         K = a.classes[0]["K"]
         nm = cpu_sample_size(a, K)
-        acc, dt, t_setup = cpu_oracle_sample(a, nm, K)
-        # the sample's time is a difference of two runs (with and without the
-        # moves); below a tenth of the setup it is lost in the setup's noise
-        timed = dt >= 0.1 * t_setup
-        line["cpu_baseline"] = {"value": acc / dt if timed else None, "unit": "updates/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": "first %d proposals of sweep 0 of one walker (N=%d, K=%d): "
-                                          "%.1f s of updates; the %.1f s setup inverse excluded%s"
-                                          % (nm, a.N, K, dt, t_setup,
-                                             "" if timed else " (too short to time against the setup: no value)")}
+        acc, dt, _ = cpu_oracle_sample(a, nm, K, threads=1)
+        nall = a.N
+        acc_all, dt_all, used = cpu_oracle_sample(a, nall, K, threads=0)
+        line["cpu_baseline"] = {
+            "value": acc / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d proposals of sweep 0 of one walker (N=%d, K=%d): %.1f s of update work "
+                      "on one thread, timed by the oracle after its setup inverse" % (nm, a.N, K, dt),
+            "all_cores": {"value": acc_all / dt_all, "cores": used,
+                          "sample": "the whole sweep 0 (%d proposals), %.1f s" % (nall, dt_all)},
+            "host": host_cpu()}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
