@@ -298,6 +298,188 @@ __global__ void __launch_bounds__(TTHREADS) ratio_dots_kernel(RatioParams<T> p, 
     }
 }
 
+// The same dot products by persistent CTAs. Items are (walker, 32 consecutive
+// rows t of that walker's 2k + 1); CTA x takes items x, x + grid, ... Warp 8
+// loads, per item, both of the walker's vectors (u, for rows t <= k, and the
+// column, for the rest) into one of two vector buffers. Consumer warp w takes
+// rows w, w + 8, ... of each item and streams their segments through a ring
+// of SPW slots of its own: its lane 0 issues the bulk copies SPW segments
+// ahead of the reads, across item boundaries, and the warp waits for each in
+// turn, so that every warp keeps SPW copies in flight with no producer in
+// between (one producer lane for all warps issued too slowly: 21% of HBM at
+// 128 x N = 512, fp32; per-warp copies drained at each item: 36%). A slot is
+// refilled only by the warp that has just read it (after a proxy fence), so a
+// wait on a fill's phase parity is never answered by an older fill. When a
+// warp is done with an item it releases the item's vector buffer. Waits are
+// bounded as in ratio_dots_kernel.
+constexpr int PRU = 32;      // rows per item
+constexpr int SPW = 4;       // ring slots of each consumer warp
+template <typename T>
+__global__ void __launch_bounds__(TTHREADS) ratio_dots_persist_kernel(RatioParams<T> p, int U, int nitems,
+                                                                      long long budget_ns)
+{
+    using V16 = typename Vec16<T>::type;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(tsm);   // [8][SPW]
+    unsigned long long *vfull = full + 8 * SPW;                               // [2]
+    unsigned long long *vempty = vfull + 2;                                   // [2]
+    const int K = p.K, ld = p.ld;
+    const unsigned rowbytes = (unsigned)ld * sizeof(T);                      // a multiple of 128
+    const unsigned slot = min((unsigned)TSEG, rowbytes);                      // bytes per ring slot
+    unsigned char *vec = tsm + 512;                                          // [2][u, column][rowbytes]
+    unsigned char *ring = vec + 4 * (size_t)rowbytes;                        // [8][SPW][slot]
+    __shared__ int abort_s, nvec_s, issued_cnt[8];
+    const int nseg = (int)((rowbytes + slot - 1) / slot);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t wK = (size_t)K * ld;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 8 * SPW; ++s) mbar_init_count(&full[s], 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init_count(&vfull[q], 1);
+            mbar_init_count(&vempty[q], 8);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+        nvec_s = 0;
+        for (int w = 0; w < 8; ++w) issued_cnt[w] = 0;
+    }
+    __syncthreads();
+
+    // item -> walker b, first row rb, rows nrows (0: nothing to do)
+    auto item = [&](int it, int &b, int &k, int &rb, int &nrows) {
+        b = it / U;
+        const int u = it - b * U;
+        k = p.kcount[b];
+        rb = u * PRU;
+        nrows = (k < 0 || k >= K) ? 0 : max(0, min(rb + PRU, 2 * k + 1) - rb);
+    };
+
+    if (warp == 8) {
+        // the vectors of every item, two buffers ahead
+        if (lane == 0) {
+            int nv = 0;
+            for (int it = blockIdx.x; it < nitems && !*(volatile int *)&abort_s; it += gridDim.x) {
+                int b, k, rb, nrows;
+                item(it, b, k, rb, nrows);
+                if (nrows == 0) continue;
+                const int buf = nv & 1;
+                if (nv >= 2 && !mbar_wait(&vempty[buf], ((nv >> 1) - 1) & 1, p.status, budget_ns)) {
+                    abort_s = 1;
+                    break;
+                }
+                const T *Pw = p.P + b * wK, *Vw = p.V + b * wK;
+                mbar_expect(&vfull[buf], 2 * rowbytes);
+                bulk_g2s(vec + (size_t)(2 * buf) * rowbytes, Vw + (size_t)k * ld, rowbytes, &vfull[buf]);
+                bulk_g2s(vec + (size_t)(2 * buf + 1) * rowbytes, Pw + (size_t)k * ld, rowbytes, &vfull[buf]);
+                ++nv;
+                nvec_s = nv;
+            }
+        }
+    } else {
+        unsigned long long *myfull = full + warp * SPW;
+        unsigned char *myring = ring + (size_t)warp * SPW * slot;
+        // This warp's segments form one stream over its items: rows r = warp,
+        // warp + 8, ... of each item, nseg segments per row. Lane 0 keeps an
+        // issue cursor SPW segments ahead of the reads, across item
+        // boundaries, so that the warp's copies stay in flight between items.
+        struct Cur { int it, j, m, b, k, rb; };
+        auto seek = [&](Cur &q, int it) {       // the first item >= it with segments for this warp
+            q.j = 0;
+            for (q.it = it; q.it < nitems; q.it += gridDim.x) {
+                int nrows;
+                item(q.it, q.b, q.k, q.rb, nrows);
+                const int myrows = nrows > warp ? (nrows - warp + 7) / 8 : 0;
+                q.m = myrows * nseg;
+                if (q.m > 0) return;
+            }
+            q.m = 0;
+        };
+        Cur is = {nitems, 0, 0, 0, 0, 0};         // issue cursor (lane 0)
+        int n_issued = 0;
+        auto issue_next = [&]() {
+            if (is.it >= nitems) return;
+            const int r = warp + 8 * (is.j / nseg), sg = is.j - (is.j / nseg) * nseg;
+            const int t = is.rb + r, kk = is.k;
+            const T *Pw = p.P + is.b * wK, *Vw = p.V + is.b * wK;
+            const T *row = t == 0 ? Pw + (size_t)kk * ld
+                                  : (t <= kk ? Pw + (size_t)(t - 1) * ld : Vw + (size_t)(t - 1 - kk) * ld);
+            const int s = n_issued % SPW;
+            const unsigned off = (unsigned)sg * slot;
+            const unsigned bytes = min(slot, rowbytes - off);
+            mbar_expect(&myfull[s], bytes);
+            bulk_g2s(myring + (size_t)s * slot, reinterpret_cast<const unsigned char *>(row) + off, bytes,
+                     &myfull[s]);
+            ++n_issued;
+            issued_cnt[warp] = n_issued;
+            if (++is.j == is.m) seek(is, is.it + gridDim.x);
+        };
+        if (lane == 0) {
+            seek(is, blockIdx.x);
+            for (int q = 0; q < SPW; ++q) issue_next();
+        }
+        int nv = 0, c = 0;        // c: segments this warp has read
+        bool ok = true;
+        for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+            int b, k, rb, nrows;
+            item(it, b, k, rb, nrows);
+            if (nrows == 0) continue;
+            const int buf = nv & 1;
+            const int myrows = nrows > warp ? (nrows - warp + 7) / 8 : 0;
+            const int m = myrows * nseg;
+            if (!mbar_wait(&vfull[buf], (nv >> 1) & 1, p.status, budget_ns) || *(volatile int *)&abort_s) {
+                ok = false;
+                break;
+            }
+            T acc = 0;
+            for (int j = 0; j < m; ++j) {
+                const int n = c + j, s = n % SPW, sg = j - (j / nseg) * nseg;
+                if (!mbar_wait(&myfull[s], (n / SPW) & 1, p.status, budget_ns) || *(volatile int *)&abort_s) {
+                    ok = false;
+                    break;
+                }
+                const int t = rb + warp + 8 * (j / nseg);
+                const V16 *wv = reinterpret_cast<const V16 *>(vec + (size_t)(2 * buf + (t <= k ? 0 : 1)) * rowbytes) +
+                                sg * (slot / 16);
+                const int nvv = (int)(min(slot, rowbytes - (unsigned)sg * slot) / 16);
+                const V16 *x = reinterpret_cast<const V16 *>(myring + (size_t)s * slot);
+#pragma unroll 4
+                for (int v = lane; v < nvv; v += 32) fma16(acc, x[v], wv[v]);
+                if (sg == nseg - 1) {
+                    const T tot = warp_sum(acc);
+                    if (lane == 0) p.partial[(size_t)b * (2 * K + 1) + t] = (double)tot;
+                    acc = 0;
+                }
+                // every lane's reads of slot s are done before the copy that refills it
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) issue_next();
+            }
+            if (!ok) break;
+            c += m;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&vempty[buf]);
+            ++nv;
+        }
+        if (!ok) abort_s = 1;
+    }
+    __syncthreads();
+    if (abort_s) {
+        // copies issued but not waited for may still be landing: wait for each
+        // warp's last SPW segments and the last two vector loads (bounded)
+        // before the CTA's shared memory goes away
+        if (threadIdx.x == 0) {
+            for (int w = 0; w < 8; ++w)
+                for (int n = max(0, issued_cnt[w] - SPW); n < issued_cnt[w]; ++n)
+                    mbar_wait(&full[w * SPW + n % SPW], (n / SPW) & 1, p.status, budget_ns);
+            const int nv = nvec_s;
+            for (int q = max(0, nv - 2); q < nv; ++q)
+                mbar_wait(&vfull[q & 1], (q >> 1) & 1, p.status, budget_ns);
+        }
+        __syncthreads();
+    }
+}
+
 // The k x k pass, grid (kparts, batch): CTA part takes rows m in
 // [part KROWS, +KROWS) of Kinv (four per warp), writes x_m = (Kinv c)_m, and
 // leaves its share of y = Kinv' b and of b.x in scratch; the last CTA of the
@@ -546,12 +728,29 @@ static cudaError_t launch_ratio_t(Ctx &c, const RatioLaunch &L)
     if (e != cudaSuccess) return e;
     // units of TRU rows sharing a vector, from the largest queue the host knows of
     const int kmax = L.kmax >= 0 ? std::min(L.kmax, c.K - 1) : c.K - 1;
-    const int U = 2 * ((kmax + 1 + TRU - 1) / TRU);
-    const size_t smem = dots_smem_bytes((size_t)c.ld * sizeof(T));
-    e = cudaFuncSetAttribute(ratio_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    ratio_dots_kernel<T><<<dim3(U, c.batch), TTHREADS, smem, c.stream>>>(p, U, c.opt_budget_ns);
+    const size_t rowbytes = (size_t)c.ld * sizeof(T);
+    if (4 * rowbytes <= 64 * 1024) {
+        // persistent CTAs streaming items of 32 rows (rows of up to 16 KB, so
+        // that two pairs of vector buffers fit beside the ring)
+        const int Up = (2 * kmax + 1 + PRU - 1) / PRU;
+        const int nitems = Up * c.batch;
+        const size_t smem = 512 + 4 * rowbytes + (size_t)8 * SPW * std::min((size_t)TSEG, rowbytes);
+        e = cudaFuncSetAttribute(ratio_dots_persist_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ratio_dots_persist_kernel<T>, TTHREADS, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * c.num_sms));
+        ratio_dots_persist_kernel<T><<<grid, TTHREADS, smem, c.stream>>>(p, Up, nitems, c.opt_budget_ns);
+    } else {
+        const int U = 2 * ((kmax + 1 + TRU - 1) / TRU);
+        const size_t smem = dots_smem_bytes(rowbytes);
+        e = cudaFuncSetAttribute(ratio_dots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        ratio_dots_kernel<T><<<dim3(U, c.batch), TTHREADS, smem, c.stream>>>(p, U, c.opt_budget_ns);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int kparts = std::max(1, (kmax + KROWS - 1) / KROWS);
