@@ -40,8 +40,6 @@ struct RatioParams {
     const int *kcount;
     double *rs;
     double *partial;
-    double *scr;                // [batch][kparts][K + 1]: partial y and b.x of the k x k pass
-    unsigned *arrive;
     int *status;
     const double *v_in;
     const int *elec;
@@ -101,8 +99,8 @@ struct Vec16<float> {
 //                          d = u . A^{-1}[:, j],  b_m = P[m] . u,  c_m = V[m] . A^{-1}[:, j]:
 //                        grid-stride over (walker, row), one warp per row, so
 //                        that every warp streams rows from HBM the whole time
-//   ratio_finish_kernel  per walker: x = Kinv c and y = Kinv' b in one
-//                        coalesced pass over Kinv, r = 1 + (d - b' Kinv c)
+//   ratio_finish_kernel  per walker (one CTA): x = Kinv c and y = Kinv' b in
+//                        one coalesced pass over Kinv, r = 1 + (d - b' Kinv c)
 //                        (the Schur complement of the bordered I + V'P, Eq. 3)
 // Rows are padded to ld with zeros (nothing writes past N), so 16-byte vectors
 // that reach into the padding add nothing.
@@ -150,7 +148,6 @@ __global__ void __launch_bounds__(RTHREADS) ratio_stage_kernel(RatioParams<T> p)
     }
 }
 
-constexpr int KROWS = 32;   // rows of Kinv per CTA of the k x k pass
 constexpr int TSEG = 4096;   // bytes of a streamed row segment (one bulk copy)
 constexpr int TNS = 16;      // stages of the segment ring
 constexpr int TRU = 32;      // rows per CTA of the dots
@@ -480,24 +477,30 @@ __global__ void __launch_bounds__(TTHREADS) ratio_dots_persist_kernel(RatioParam
     }
 }
 
-// The k x k pass, grid (kparts, batch): CTA part takes rows m in
-// [part KROWS, +KROWS) of Kinv (four per warp), writes x_m = (Kinv c)_m, and
-// leaves its share of y = Kinv' b and of b.x in scratch; the last CTA of the
-// walker to arrive sums the shares in part order (deterministic) and forms
-// r = d - b.x.
+// The k x k pass, one CTA per walker (grid = batch), over parts of 32 rows of
+// Kinv in turn: in part p, warp w takes rows 32 p + 4 w .. + 3, its lanes the
+// columns q = lane, lane + 32, ...; x_m = (Kinv c)_m is a fixed shuffle tree
+// over the lanes; each lane's share of y = Kinv' b over the warp's four rows
+// and each warp's share of b.x are added over the warps in warp order, and the
+// parts in part order: r = 1 + (d - b.x) (the Schur complement of the
+// bordered I + V'P, Eq. 3), deterministic, with no cross-CTA hand-off, and in
+// the association of the earlier kernel that took one CTA per part (the
+// bordered update of Kinv that x and y feed amplifies rounding differences on
+// ill-conditioned walks).
 template <typename T>
-__global__ void __launch_bounds__(RTHREADS) ratio_finish_kernel(RatioParams<T> p, int kparts)
+__global__ void __launch_bounds__(RTHREADS) ratio_finish_kernel(RatioParams<T> p)
 {
-    const int b = blockIdx.y, part = blockIdx.x;
+    const int b = blockIdx.x;
     const int N = p.N, K = p.K;
     const int k = p.kcount[b];
     const int j = p.elec ? p.elec[b] : p.uniform_elec;
     if (j < 0 || j >= N || k < 0 || k >= K) return;     // flagged by the stage kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int njobs = 2 * k + 1;
+    constexpr int QL = QMCDU_MAX_K / 32;
     __shared__ double red[2 * QMCDU_MAX_K + 1];
     __shared__ double ypart[RTHREADS / 32][QMCDU_MAX_K];
-    __shared__ double bx[RTHREADS / 32];
+    __shared__ double bxw_s[RTHREADS / 32];
     for (int job = threadIdx.x; job < njobs; job += RTHREADS)
         red[job] = p.partial[(size_t)b * (2 * K + 1) + job];
     __syncthreads();
@@ -505,82 +508,91 @@ __global__ void __launch_bounds__(RTHREADS) ratio_finish_kernel(RatioParams<T> p
     const double *bv = red + 1, *cv = red + 1 + k;
     double *rec = p.rs + (size_t)b * rs_stride(K);
     const double *Kb = p.Kinv + (size_t)b * K * K;
-    double *scr = p.scr + ((size_t)b * kparts + part) * (K + 1);
-    constexpr int QL = QMCDU_MAX_K / 32;
-    double yl[QL];
+    double cq[QL];
 #pragma unroll
-    for (int s2 = 0; s2 < QL; ++s2) yl[s2] = 0.0;
-    double bxw = 0.0;
-    const int m0 = part * KROWS + warp * 4;
-    if (m0 < k) {
-        double xm[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s2 = 0; s2 < QL; ++s2) {
+        const int q = lane + 32 * s2;
+        cq[s2] = q < k ? cv[q] : 0.0;
+    }
+    double ysum[QMCDU_MAX_K / RTHREADS + 1];       // thread t: y_q for q = t, t + RTHREADS
 #pragma unroll
-        for (int s2 = 0; s2 < QL; ++s2) {
-            const int q = lane + 32 * s2;
-            if (q < k) {
-                const double cq = cv[q];
+    for (int e = 0; e < QMCDU_MAX_K / RTHREADS + 1; ++e) ysum[e] = 0.0;
+    double bxsum = 0.0;                            // thread 0
+    for (int m0p = 0; m0p < k; m0p += 32) {
+        const int m0 = m0p + warp * 4;
+        double yl[QL];
+        double bxw = 0.0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int m = m0 + r;
-                    if (m < k) {
-                        const double kv = __ldg(Kb + (size_t)m * K + q);
-                        xm[r] += kv * cq;
-                        yl[s2] += bv[m] * kv;
+        for (int s2 = 0; s2 < QL; ++s2) yl[s2] = 0.0;
+        if (m0 < k) {
+            double kv[4][QL];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int s2 = 0; s2 < QL; ++s2) {
+                    const int q = lane + 32 * s2, m = m0 + r;
+                    kv[r][s2] = (q < k && m < k) ? __ldg(Kb + (size_t)m * K + q) : 0.0;
+                }
+            double xm[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int s2 = 0; s2 < QL; ++s2) {
+                const int q = lane + 32 * s2;
+                if (q < k) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int m = m0 + r;
+                        if (m < k) {
+                            xm[r] += kv[r][s2] * cq[s2];
+                            yl[s2] += bv[m] * kv[r][s2];
+                        }
                     }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const double x = warp_sum(xm[r]);
+                if (m0 + r < k) {
+                    bxw += bv[m0 + r] * x;
+                    if (lane == 0) rec[4 + m0 + r] = x;
                 }
             }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const double x = warp_sum(xm[r]);
-            if (m0 + r < k) {
-                bxw += bv[m0 + r] * x;
-                if (lane == 0) rec[4 + m0 + r] = x;
+        for (int s2 = 0; s2 < QL; ++s2) {
+            const int q = lane + 32 * s2;
+            if (q < k) ypart[warp][q] = yl[s2];
+        }
+        if (lane == 0) bxw_s[warp] = bxw;
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < QMCDU_MAX_K / RTHREADS + 1; ++e) {
+            const int q = threadIdx.x + e * RTHREADS;
+            if (q < k) {
+                double y = 0.0;
+#pragma unroll
+                for (int w = 0; w < RTHREADS / 32; ++w) y += ypart[w][q];
+                ysum[e] += y;
             }
         }
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < RTHREADS / 32; ++w) t += bxw_s[w];
+            bxsum += t;
+        }
+        __syncthreads();
     }
 #pragma unroll
-    for (int s2 = 0; s2 < QL; ++s2) {
-        const int q = lane + 32 * s2;
-        if (q < k) ypart[warp][q] = yl[s2];
-    }
-    if (lane == 0) bx[warp] = bxw;
-    __syncthreads();
-    for (int q = threadIdx.x; q < k; q += RTHREADS) {
-        double y = 0.0;
-#pragma unroll
-        for (int w = 0; w < RTHREADS / 32; ++w) y += ypart[w][q];
-        scr[q] = y;
+    for (int e = 0; e < QMCDU_MAX_K / RTHREADS + 1; ++e) {
+        const int q = threadIdx.x + e * RTHREADS;
+        if (q < k) rec[4 + K + q] = ysum[e];
     }
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < RTHREADS / 32; ++w) t += bx[w];
-        scr[K] = t;
-    }
-    // the last CTA of the walker sums the parts
-    __threadfence();
-    __syncthreads();
-    __shared__ unsigned ticket;
-    if (threadIdx.x == 0) ticket = atomicAdd(&p.arrive[b], 1u);
-    __syncthreads();
-    if (ticket != (unsigned)(kparts - 1)) return;
-    __threadfence();
-    const double *s0 = p.scr + (size_t)b * kparts * (K + 1);
-    for (int q = threadIdx.x; q < k; q += RTHREADS) {
-        double y = 0.0;
-        for (int pp = 0; pp < kparts; ++pp) y += __ldcg(s0 + (size_t)pp * (K + 1) + q);
-        rec[4 + K + q] = y;
-    }
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int pp = 0; pp < kparts; ++pp) s += __ldcg(s0 + (size_t)pp * (K + 1) + K);
-        const double r = 1.0 + (d - s);
+        const double r = 1.0 + (d - bxsum);
         rec[0] = d;
         rec[1] = r;
         rec[2] = (double)k;
         rec[3] = (double)j;
         if (p.ratio_out) p.ratio_out[b] = r;
-        p.arrive[b] = 0u;
     }
 }
 
@@ -718,7 +730,7 @@ static cudaError_t launch_ratio_t(Ctx &c, const RatioLaunch &L)
     p.N = c.N; p.K = c.K; p.ld = c.ld;
     p.A = c.A; p.Ainv = (const T *)c.Ainv; p.P = (T *)c.P; p.V = (T *)c.V;
     p.vstash = c.vstash; p.Kinv = c.Kinv; p.kcount = c.kcount; p.rs = c.rs;
-    p.partial = c.partial; p.scr = c.ratio_scr; p.arrive = c.arrive; p.status = c.status;
+    p.partial = c.partial; p.status = c.status;
     p.v_in = L.v_in; p.elec = L.elec; p.uniform_elec = L.uniform_elec;
     p.generate = L.generate; p.seed = L.seed; p.sweep = L.sweep; p.sigma = L.sigma;
     p.ratio_out = L.ratio_out;
@@ -753,8 +765,7 @@ static cudaError_t launch_ratio_t(Ctx &c, const RatioLaunch &L)
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int kparts = std::max(1, (kmax + KROWS - 1) / KROWS);
-    ratio_finish_kernel<T><<<dim3(kparts, c.batch), RTHREADS, 0, c.stream>>>(p, kparts);
+    ratio_finish_kernel<T><<<c.batch, RTHREADS, 0, c.stream>>>(p);
     return cudaGetLastError();
 }
 

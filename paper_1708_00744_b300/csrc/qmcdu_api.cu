@@ -82,8 +82,6 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
     AL(c->sign, B * sizeof(int));
     AL(c->rs, B * rs_stride(K) * sizeof(double));
     AL(c->partial, B * c->nsplit * (2 * K + 1) * sizeof(double));
-    AL(c->ratio_scr, B * ((K + 31) / 32) * (K + 1) * sizeof(double));
-    AL(c->arrive, B * sizeof(unsigned));
     AL(c->acc, B);
     AL(c->elec_d, B * sizeof(int));
     AL(c->mask_d, B);
@@ -139,7 +137,7 @@ static cudaError_t alloc_state(Ctx *c, bool do_alloc, size_t *total)
 static void release(Ctx *c)
 {
     void *ptrs[] = {c->A, c->Ainv, c->P, c->V, c->vstash, c->Kinv, c->idx, c->kcount, c->logabs,
-                    c->sign, c->rs, c->partial, c->arrive, c->acc, c->elec_d, c->mask_d,
+                    c->sign, c->rs, c->partial, c->acc, c->elec_d, c->mask_d,
                     c->status, c->Tbuf, c->Wbuf, c->work, c->piv, c->colperm, c->Lt, c->R,
                     c->lu_logabs, c->lu_sign, c->drift, c->sw_acc, c->sw_ratio, c->sw_ties,
                     c->sw_override, c->sw_partial, c->sw_sync, c->sw_phase, c->sw_gauss,
@@ -147,7 +145,7 @@ static void release(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *more[] = {c->d_params, c->step_acc, c->step_ratio, c->step_ties, c->d_wlist,
-                    c->d_wseed, c->d_wsweep, c->d_lseed, c->ratio_scr, c->oz, c->gj_scr, c->gj_ctr,
+                    c->d_wseed, c->d_wsweep, c->d_lseed, c->oz, c->gj_scr, c->gj_ctr,
                     c->pair_logabs, c->pair_sign, c->eqs};
     for (void *p : more)
         if (p) cudaFree(p);
@@ -382,7 +380,6 @@ int qmcdu_set_matrix(qmcdu_t h, const double *A)
                          N * c->batch, cudaMemcpyDefault, c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->kcount, 0, c->batch * sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->arrive, 0, c->batch * sizeof(unsigned), c->stream));
     clear_queues(c);
     c->pending = false;
     return do_recompute(c, 0);
@@ -1055,7 +1052,6 @@ int qmcdu_load_walkers(qmcdu_t h, int first, int count, const double *A,
         c->n_launch += 1;
     }
     CK(cudaMemsetAsync(c->kcount + first, 0, count * sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->arrive + first, 0, count * sizeof(unsigned), c->stream));
     return recompute_range(c, first, count, 0);
 }
 

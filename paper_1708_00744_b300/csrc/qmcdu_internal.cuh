@@ -44,8 +44,6 @@ struct Ctx {
     int *sign = nullptr;        // batch
     double *rs = nullptr;       // batch x rs_stride(K)
     double *partial = nullptr;  // batch x nsplit x (2K+1)
-    double *ratio_scr = nullptr; // batch x ceil(K/32) x (K+1): shares of the ratio's k x k pass
-    unsigned *arrive = nullptr; // batch
     unsigned char *acc = nullptr; // batch: decision of the last resolved proposal
     int *elec_d = nullptr;      // batch
     unsigned char *mask_d = nullptr; // batch
