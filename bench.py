@@ -51,11 +51,10 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the sweep kernel,
 # from one ncu capture; keyed by the sha256 of kernels_sweep.cu at capture time
 # and the workload (a stale key gives null).
-#   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush:
-#   101.1 MB read + 88.1 MB written (the working set stays in L2). Taken on the
-#   revision before the partial buffers were indexed by the proposal count, so
-#   the current source reports null until the counters are taken again.
-NCU_TRAFFIC = {"a458043c9ab1b176:single": 101.069056e6 + 88.081152e6}
+#   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush: the
+#   mean of two launches, 102.1 MB read + 78.1 MB written (the working set stays
+#   in L2); command in profiles/sweep_kernel_fp64_emulated_n2048_k32.md.
+NCU_TRAFFIC = {"307d5650cbf7e2a0:single": (101.710848e6 + 79.166976e6 + 102.494976e6 + 76.966656e6) / 2}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],
