@@ -183,3 +183,63 @@ def test_group_at_batched_workload_shapes_matches_oracle():
             assert sg[b] == ref["sign"]
     for c in classes:
         c.close()
+
+
+@pytest.mark.parametrize("precision,R", [("fp32", 2), ("bf16x3", 20)])
+def test_group_at_mixed_workload_shapes_matches_oracle(precision, R):
+    """The mixed workload's two size classes in one walker group at full size:
+    64 walkers of N = 2048 and 8 of N = 4096, K = 64, sigma = 0.1, one sweep
+    through qmcdu_group_step (captured as a CUDA graph). One sampled walker of
+    each class against the fp64 oracle (Sherman-Morrison, its own decisions),
+    within the fitted mixed-precision bound of tests/test_gpu_mixed.py (the
+    split-bf16 bound is that of its in-sweep tensor-core flush). The device
+    decides every move: a decision may differ from the oracle's only within
+    twice the walk's ratio error of a tie, and the walks part there, so the
+    comparison stops at the first such decision (A^{-1} and log|det| are
+    compared only if there is none)."""
+    need_gpu()
+    from test_gpu_mixed import bounds
+    from gpu_common import device_gaussians
+    from paper_1708_00744_b300 import inputs
+    sigma, K = 0.1, 64
+    classes = [SizeClass(2048, K, 64, precision, base_seed=3000), SizeClass(4096, K, 8, precision, base_seed=4000)]
+    for c in classes:
+        c.load()
+    grp = WalkerGroup(classes)
+    grp.step(0, 1, sigma, recompute=False, use_graph=True)
+    grp.synchronize()
+    res = [c.results(1) for c in classes]
+    oracle.set_threads(0)
+    for c, (acc_all, rat_all), b in zip(classes, res, (37, 5)):
+        key = inputs.walker_seed(c.base_seed, b)
+        A = inputs.initial_matrix(key, c.N)
+        G, U = device_gaussians(key, c.N, [0])
+        ref = oracle.sweeps(oracle.SM, A, G, U, sigma)
+        acc, rat = acc_all[0, b].astype(bool), rat_all[0, b]
+        kappa = max(np.linalg.cond(A, 1), np.linalg.cond(ref["A"], 1))
+        bnd = bounds(precision, sigma, R, kappa)
+        p = np.minimum(1.0, ref["ratios"][0] ** 2)
+        diff = np.nonzero(acc != ref["accepted"][0])[0]
+        upto = int(diff[0]) if len(diff) else c.N
+        e = rel_ratio_err(rat[:upto + 1], ref["ratios"][0][:upto + 1])
+        for j in diff[:1]:
+            assert abs(p[j] - U[0, j]) < 2 * e, ("decision far from a tie differs", c.N, b, int(j))
+        line = "%s group N=%d walker %d: kappa_1 %.1e | ratio %.1e (bound %.1e) over %d of %d proposals" % (
+            precision, c.N, b, kappa, e, bnd[0], upto + 1 if len(diff) else c.N, c.N)
+        assert e < bnd[0], line
+        if not len(diff):
+            Ai = torch.zeros(c.batch, c.N, c.N, dtype=torch.float64, device="cuda")
+            c.walkers.get_inverse(Ai)
+            inv_b = Ai[b].cpu().numpy()
+            del Ai
+            la = np.zeros(c.batch)
+            sg = np.zeros(c.batch, dtype=np.int32)
+            c.walkers.logdet(la, sg)
+            ei, el = rel_norm_err(inv_b, ref["Ainv"]), logdet_err(la[b], ref["logabs"])
+            line += " | inverse %.1e (%.1e) logdet %.1e (%.1e)" % (ei, bnd[1], el, bnd[2])
+            assert ei < bnd[1] and el < bnd[2], line
+            assert sg[b] == ref["sign"]
+        print(line)
+    grp.close()
+    for c in classes:
+        c.close()
