@@ -2742,27 +2742,32 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
         if (r == 0 && tid == 0) la += log(fabs(pv));     // one thread: fp64 log is costly here
         if (pv < 0.0) sg = -sg;
         if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : __ldcg(g.candrow + ((size_t)par * P + rp) * nb + tid) / pv;
-        // the owner of row p takes row c's old panel values; rows c and p of X
-        // outside the panel are interchanged in column shares
-        if (p != c) {
-            if (p >= i0 && p < i0 + nr)
-                for (int t = tid; t < nbe; t += GJ_THREADS) S[t * Rr + (p - i0)] = __ldcg(g.rowc + par * nb + t);
-            for (int x = x0 + tid; x < x1; x += GJ_THREADS) {
-                if (x >= c0 && x < c0 + nbe) continue;
-                const double s = X[(size_t)c * ld + x];
-                X[(size_t)c * ld + x] = X[(size_t)p * ld + x];
-                X[(size_t)p * ld + x] = s;
-            }
-        }
+        // the owner of row p takes row c's old panel values
+        if (p != c && p >= i0 && p < i0 + nr)
+            for (int t = tid; t < nbe; t += GJ_THREADS) S[t * Rr + (p - i0)] = __ldcg(g.rowc + par * nb + t);
         __syncthreads();
-        for (int li = tid; li < nr; li += GJ_THREADS) {
-            const int gi = i0 + li;
-            if (gi == c) {
-                for (int t = 0; t < nbe; ++t) S[t * Rr + li] = prow[t];
-            } else {
-                const double f = S[q * Rr + li];
-                S[q * Rr + li] = 0.0;
-                for (int t = 0; t < nbe; ++t) S[t * Rr + li] -= f * prow[t];
+        if (warp == GJ_THREADS / 32 - 1) {
+            // the last warp interchanges rows c and p of X outside the panel
+            // (its column share; the same lane takes the same columns at every
+            // pivot, so the interchanges stay in order) while the others
+            // eliminate: the round trip to memory leaves the pivot's chain
+            if (p != c)
+                for (int x = x0 + lane; x < x1; x += 32) {
+                    if (x >= c0 && x < c0 + nbe) continue;
+                    const double s = X[(size_t)c * ld + x];
+                    X[(size_t)c * ld + x] = X[(size_t)p * ld + x];
+                    X[(size_t)p * ld + x] = s;
+                }
+        } else {
+            for (int li = tid; li < nr; li += GJ_THREADS - 32) {
+                const int gi = i0 + li;
+                if (gi == c) {
+                    for (int t = 0; t < nbe; ++t) S[t * Rr + li] = prow[t];
+                } else {
+                    const double f = S[q * Rr + li];
+                    S[q * Rr + li] = 0.0;
+                    for (int t = 0; t < nbe; ++t) S[t * Rr + li] -= f * prow[t];
+                }
             }
         }
         __syncthreads();
