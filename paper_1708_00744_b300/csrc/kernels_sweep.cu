@@ -2640,6 +2640,7 @@ __device__ inline GjScratch gj_scratch(unsigned char *base, int P, int nb)
 
 constexpr int GJ_THREADS = 256;
 constexpr int GJ_CTR_STRIDE = 32;     // one 128-byte line per walker
+constexpr int GJ_NBMAX = 32;          // panel width at most (the cluster form)
 
 __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, int nb, int c0, int nbe, int P,
                                                                 double *work, int *piv, double *Lt, double *R,
@@ -2650,6 +2651,7 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
     extern __shared__ double S[];              // [nb][Rr]: column q of the CTA's rows at S + q*Rr
     __shared__ double wval[GJ_THREADS / 32], prow[64];
     __shared__ int widx[GJ_THREADS / 32], win_s, wr_s;
+    __shared__ double pvs[32], pvs_log[32];
     const int b = blockIdx.x / P, r = blockIdx.x - b * P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Rr = (N + P - 1) / P;
@@ -2739,7 +2741,7 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
             singular = 1;
             continue;
         }
-        if (r == 0 && tid == 0) la += log(fabs(pv));     // one thread: fp64 log is costly here
+        if (tid == 0) pvs[q] = pv;     // its log after the panel, off the pivot chain
         if (pv < 0.0) sg = -sg;
         if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : __ldcg(g.candrow + ((size_t)par * P + rp) * nb + tid) / pv;
         // the owner of row p takes row c's old panel values
@@ -2785,7 +2787,191 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
     for (int q = 0; q < nbe; ++q)
         for (int x = x0 + tid; x < x1; x += GJ_THREADS)
             Rb[(size_t)q * ld + x] = (x >= c0 && x < c0 + nbe) ? 0.0 : X[(size_t)(c0 + q) * ld + x];
+    // log|det| of the panel's pivots, added in pivot order as one thread would
+    // (the fp64 log of each pivot, on the slow fp64 pipe, stays off the chain
+    // of pivot steps)
+    if (r == 0 && warp == 0) {
+        pvs_log[lane] = (lane < nbe && !singular) ? log(fabs(pvs[lane])) : 0.0;
+        __syncwarp();
+    }
     if (r == 0 && tid == 0) {
+        for (int q = 0; q < nbe && !singular; ++q) la += pvs_log[q];
+        if (singular) {
+            atomicOr(status, ST_SINGULAR);
+            lu_logabs[b] = -INFINITY;
+            lu_sign[b] = 0;
+        } else if (lu_sign[b] != 0) {
+            lu_logabs[b] += la;
+            lu_sign[b] *= sg;
+        }
+    }
+}
+
+// The same panel elimination over one thread-block cluster of GJ_CL CTAs per
+// walker. Each pivot column costs one hardware cluster barrier instead of a
+// group barrier in global memory. Every CTA writes its candidate (value,
+// row, the row's panel values) and, if it owns row c, row c's panel values
+// into a buffer of its own shared memory, alternating between two parities.
+// After the barrier every CTA reads the GJ_CL candidates, the winner's row and
+// row c from its siblings' shared memory. A CTA writes a parity again only
+// after the next barrier, which its siblings pass only once they have read
+// it. The interchange of rows c and p outside the panel goes to the last warp,
+// beside the elimination. Every CTA executes the same sequence of cluster
+// barriers (a singular pivot is seen by all), and a last barrier ends every
+// read of a sibling's shared memory before any CTA exits.
+constexpr int GJ_CL = 16;
+__global__ void __launch_bounds__(GJ_THREADS) gj_panel_cl_kernel(int N, int ld, int nb, int c0, int nbe,
+                                                                double *work, int *piv, double *Lt, double *R,
+                                                                double *lu_logabs, int *lu_sign, int *status)
+{
+    extern __shared__ double S[];              // [nb][Rr]: column q of the CTA's rows at S + q*Rr
+    __shared__ double cand_v[2], cand_row[2][GJ_NBMAX], rowc_b[2][GJ_NBMAX];
+    __shared__ int cand_i[2];
+    __shared__ double wval[GJ_THREADS / 32], prow[GJ_NBMAX], crow_s[GJ_NBMAX], rowc_s[GJ_NBMAX];
+    __shared__ int widx[GJ_THREADS / 32], win_s, wr_s;
+    __shared__ double pvs[GJ_NBMAX], pvs_log[32];
+    constexpr int P = GJ_CL;
+    const int b = blockIdx.x / P, r = blockIdx.x - b * P;       // r: the CTA's rank in its cluster
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Rr = (N + P - 1) / P;
+    const int i0 = min(N, r * Rr), nr = min(Rr, N - i0);
+    double *X = work + (size_t)b * N * ld;
+    const int xs = (N + P - 1) / P, x0 = min(N, r * xs), x1 = min(N, x0 + xs);
+
+    for (int e = tid; e < nr * nbe; e += GJ_THREADS) {
+        const int li = e / nbe, q = e - li * nbe;
+        S[q * Rr + li] = X[(size_t)(i0 + li) * ld + c0 + q];
+    }
+    __syncthreads();
+    double la = 0.0;
+    int sg = 1, singular = 0;
+    for (int q = 0; q < nbe; ++q) {
+        const int c = c0 + q, par = q & 1;
+        double best = -1.0;
+        int bi = N;
+        for (int li = tid; li < nr; li += GJ_THREADS) {
+            const int gi = i0 + li;
+            if (gi < c) continue;
+            const double v = fabs(S[q * Rr + li]);
+            if (v > best || (v == best && gi < bi)) { best = v; bi = gi; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < GJ_THREADS / 32 ? wval[lane] : -1.0;
+            bi = lane < GJ_THREADS / 32 ? widx[lane] : N;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) {
+                cand_v[par] = best;
+                cand_i[par] = bi;
+                win_s = bi;
+            }
+        }
+        __syncthreads();
+        const int mine = win_s;
+        if (mine < N && tid < nbe) cand_row[par][tid] = S[tid * Rr + (mine - i0)];
+        if (c >= i0 && c < i0 + nr && tid >= 32 && tid < 32 + nbe) rowc_b[par][tid - 32] = S[(tid - 32) * Rr + (c - i0)];
+        cl_barrier();
+        // the winner: largest candidate, lowest row on ties, in a fixed order
+        if (warp == 0) {
+            double bv = -1.0;
+            int bidx = N, brk = 0;
+            if (lane < P) {
+                bv = cl_ld_f64(cl_map(&cand_v[par], lane));
+                bidx = (int)cl_ld_acquire(cl_map(&cand_i[par], lane));
+                brk = lane;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+                const int ok_ = __shfl_xor_sync(0xffffffffu, brk, o);
+                if (ov > bv || (ov == bv && oi < bidx)) { bv = ov; bidx = oi; brk = ok_; }
+            }
+            if (lane == 0) {
+                win_s = bidx < N ? bidx : c;
+                wr_s = bidx < N ? brk : -1;
+            }
+        }
+        __syncthreads();
+        {
+            const int rw = wr_s;
+            if (tid < nbe) crow_s[tid] = rw >= 0 ? cl_ld_f64(cl_map(&cand_row[par][tid], rw)) : 0.0;
+            else if (tid >= 32 && tid < 32 + nbe) rowc_s[tid - 32] = cl_ld_f64(cl_map(&rowc_b[par][tid - 32], c / Rr));
+        }
+        __syncthreads();
+        const int p = win_s, rp = wr_s;
+        const double pv = rp >= 0 ? crow_s[q] : 0.0;
+        if (r == 0 && tid == 0) piv[(size_t)b * N + c] = p;
+        if (p != c) sg = -sg;
+        if (pv == 0.0) {
+            singular = 1;
+            continue;
+        }
+        if (tid == 0) pvs[q] = pv;     // its log after the panel, off the pivot chain
+        if (pv < 0.0) sg = -sg;
+        if (tid < nbe) prow[tid] = (tid == q) ? 1.0 / pv : crow_s[tid] / pv;
+        // the owner of row p takes row c's old panel values
+        if (p != c && p >= i0 && p < i0 + nr)
+            for (int t = tid; t < nbe; t += GJ_THREADS) S[t * Rr + (p - i0)] = rowc_s[t];
+        __syncthreads();
+        if (warp == GJ_THREADS / 32 - 1) {
+            if (p != c)
+                for (int x = x0 + lane; x < x1; x += 32) {
+                    if (x >= c0 && x < c0 + nbe) continue;
+                    const double s = X[(size_t)c * ld + x];
+                    X[(size_t)c * ld + x] = X[(size_t)p * ld + x];
+                    X[(size_t)p * ld + x] = s;
+                }
+        } else {
+            for (int li = tid; li < nr; li += GJ_THREADS - 32) {
+                const int gi = i0 + li;
+                if (gi == c) {
+                    for (int t = 0; t < nbe; ++t) S[t * Rr + li] = prow[t];
+                } else {
+                    const double f = S[q * Rr + li];
+                    S[q * Rr + li] = 0.0;
+                    for (int t = 0; t < nbe; ++t) S[t * Rr + li] -= f * prow[t];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // every CTA's interchanges of X are done, and every read of a sibling's
+    // shared memory, before the pivot rows are read and any CTA exits
+    __threadfence();
+    cl_barrier();
+    double *Ltb = Lt + (size_t)b * nb * ld;
+    double *Rb = R + (size_t)b * nb * ld;
+    for (int e = tid; e < nr * nbe; e += GJ_THREADS) {
+        const int li = e / nbe, q = e - li * nbe, gi = i0 + li;
+        const double v = S[q * Rr + li];
+        X[(size_t)gi * ld + c0 + q] = v;
+        Ltb[(size_t)q * ld + gi] = v - (gi == c0 + q ? 1.0 : 0.0);
+    }
+    for (int q = 0; q < nbe; ++q)
+        for (int x = x0 + tid; x < x1; x += GJ_THREADS)
+            Rb[(size_t)q * ld + x] = (x >= c0 && x < c0 + nbe) ? 0.0 : X[(size_t)(c0 + q) * ld + x];
+    // log|det| of the panel's pivots, added in pivot order as one thread would
+    // (the fp64 log of each pivot, on the slow fp64 pipe, stays off the chain
+    // of pivot steps)
+    if (r == 0 && warp == 0) {
+        pvs_log[lane] = (lane < nbe && !singular) ? log(fabs(pvs[lane])) : 0.0;
+        __syncwarp();
+    }
+    if (r == 0 && tid == 0) {
+        for (int q = 0; q < nbe && !singular; ++q) la += pvs_log[q];
         if (singular) {
             atomicOr(status, ST_SINGULAR);
             lu_logabs[b] = -INFINITY;
@@ -2799,8 +2985,45 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
 
 size_t gj_mc_scratch_bytes(int P, int nb) { return (gj_scratch_bytes(P, nb) + 255) / 256 * 256; }
 
+// The cluster form of the panel (gj_panel_cl_kernel): one cluster of GJ_CL
+// CTAs per walker. cudaErrorNotSupported where it cannot run (its shared
+// memory, a panel wider than GJ_NBMAX, no co-resident cluster of that size).
+static cudaError_t launch_gj_panel_cl(Ctx &c, int c0, int nbe)
+{
+    const int N = c.N, Rr = (N + GJ_CL - 1) / GJ_CL;
+    const size_t smem = (size_t)c.nb * Rr * sizeof(double);
+    if (c.nb > GJ_NBMAX || smem > 160 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(gj_panel_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(gj_panel_cl_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = GJ_CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(c.batch * GJ_CL);
+    cfg.blockDim = dim3(GJ_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, (const void *)gj_panel_cl_kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (ncl < 1) return cudaErrorNotSupported;
+    return cudaLaunchKernelEx(&cfg, gj_panel_cl_kernel, N, c.ld, c.nb, c0, nbe, c.work, c.piv, c.Lt, c.R,
+                              c.lu_logabs, c.lu_sign, c.status);
+}
+
 cudaError_t launch_gj_panel_mc(Ctx &c, int c0, int nbe)
 {
+    {
+        const cudaError_t ec = launch_gj_panel_cl(c, c0, nbe);
+        if (ec != cudaErrorNotSupported) return ec;
+        cudaGetLastError();
+    }
     const int P = c.gj_ctas, N = c.N;
     const int Rr = (N + P - 1) / P;
     const size_t smem = (size_t)c.nb * Rr * sizeof(double);
