@@ -52,9 +52,9 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 # from one ncu capture; keyed by the sha256 of kernels_sweep.cu at capture time
 # and the workload (a stale key gives null).
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush: the
-#   mean of two launches, 102.1 MB read + 78.1 MB written (the working set stays
+#   mean of two launches, 102.0 MB read + 78.0 MB written (the working set stays
 #   in L2); command in profiles/sweep_kernel_fp64_emulated_n2048_k32.md.
-NCU_TRAFFIC = {"307d5650cbf7e2a0:single": (101.710848e6 + 79.166976e6 + 102.494976e6 + 76.966656e6) / 2}
+NCU_TRAFFIC = {"7cd132129547e673:single": (101.727744e6 + 78.962432e6 + 102.284288e6 + 76.954112e6) / 2}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],
