@@ -2016,17 +2016,18 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                         const double *pbj = pb + job;
                         unsigned long long deadline = 0;
                         const size_t stp = (size_t)G * njs;
-                        for (; q < Gr; q += 8 * G) {
-                            const int cnt = min(8, (Gr - q + G - 1) / G);
+                        constexpr int PL = 16;          // tagged loads in flight per lane and round
+                        for (; q < Gr; q += PL * G) {
+                            const int cnt = min(PL, (Gr - q + G - 1) / G);
                             const double *pq = pbj + (size_t)q * njs;
-                            unsigned long long x[8];
+                            unsigned long long x[PL];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
+                            for (int e = 0; e < PL; ++e)
                                 if (e < cnt) x[e] = ld_tagged(pq + e * stp);
                             for (unsigned spins = 1;; ++spins) {
                                 unsigned stale = 0;
 #pragma unroll
-                                for (int e = 0; e < 8; ++e)
+                                for (int e = 0; e < PL; ++e)
                                     if (e < cnt && tag_of(x[e]) != want) stale |= 1u << e;
                                 if (!stale || late) break;
                                 if ((spins & 15u) == 0) {
@@ -2035,11 +2036,11 @@ __device__ void sweep_body(const SweepParams<T> &p, unsigned char *smem, uint32_
                                     else if (now > deadline || (*(volatile const int *)p.status & ST_TIMEOUT)) late = 1;
                                 }
 #pragma unroll
-                                for (int e = 0; e < 8; ++e)
+                                for (int e = 0; e < PL; ++e)
                                     if ((stale >> e) & 1u) x[e] = ld_tagged(pq + e * stp);
                             }
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
+                            for (int e = 0; e < PL; ++e)
                                 if (e < cnt) s = df_add(s, untag(x[e]));
                         }
                     }
