@@ -1470,11 +1470,14 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
     // ------------------------------------------------------------ phase B
     {
         // T = sum_rc T'_rc, eight consecutive m per thread, the kp / 8
-        // threads of a column adjacent in the warp
+        // threads of a column adjacent in the warp. Chunks of 32 tasks go to
+        // the group's warps round-robin over its CTAs (chunk cn to CTA cn mod Gf),
+        // so that every SM takes a share
         const int ng = kp / 8;
         const int totT = N * ng;
-        for (int base = rank * STHREADS; base < totT; base += Gf * STHREADS) {
-            const int e = base + tid;
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int cn = rank + Gf * warp; cn * 32 < totT; cn += Gf * SWARPS) {
+            const int e = cn * 32 + lane;
             const bool in = e < totT;
             const int c = in ? e / ng : 0, m0 = (e - (e / ng) * ng) * 8;
             double t[8];
@@ -1491,6 +1494,7 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
                     S[q] = 0;
                     g[q] = 0.f;
                 }
+#pragma unroll 4
                 for (int rc = 0; rc < Ly.nrc; ++rc) {
                     const size_t o = ((size_t)rc * Nc + c) * kp + m0;
                     const longlong2 *s2 = reinterpret_cast<const longlong2 *>(partS + o);
@@ -1539,36 +1543,36 @@ __device__ __noinline__ bool oz_phase_b(const SweepParams<T> &p, int w, int k, i
                 if (m0 == 0) tex[c] = em;
             }
         }
-        // W: one thread per row i, all kp values of m; the row exponent over
-        // the scaled entries W[m][i] 2^f_m
-        for (int i = rank * STHREADS + tid; i < N; i += Gf * STHREADS) {
-            double x[32];
+        // W: the kp / 8 threads of a row i adjacent in the warp, eight values
+        // of m each (chunks of 32 tasks round-robin over the CTAs as for T);
+        // the row exponent over the scaled entries W[m][i] 2^f_m
+        const int totW = N * ng;
+        for (int cn = rank + Gf * warp; cn * 32 < totW; cn += Gf * SWARPS) {
+            const int e = cn * 32 + lane;
+            const bool in = e < totW;
+            const int i = in ? e / ng : 0, g = e - (e / ng) * ng;
+            double y[8];
             int em = 0;
 #pragma unroll
-            for (int m = 0; m < 32; ++m) {
-                x[m] = (m < k) ? __ldcg(Wb + (size_t)m * ld + i) : 0.0;
-                if (nz(x[m])) em = max(em, bexp(x[m]) + fs[m]);
+            for (int q = 0; q < 8; ++q) {
+                const int m = g * 8 + q;
+                y[q] = (in && m < k) ? __ldcg(Wb + (size_t)m * ld + i) : 0.0;
+                if (nz(y[q])) em = max(em, bexp(y[q]) + fs[m]);
             }
-            const int rb = i / CM;
+            for (int o = 1; o < ng; o <<= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+            if (in) {
+                int emq[8];
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (g * 8 < kp) {
-                    double y[8];
-                    int emq[8];
+                for (int q = 0; q < 8; ++q) emq[q] = em - fs[g * 8 + q];
+                uint4 sl[NS];
+                slice8(y, emq, sl);
+                const int rb = i / CM;
+                const uint32_t o = coff(i - rb * CM, g * 8, kp) >> 1;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        y[q] = x[g * 8 + q];
-                        emq[q] = em - fs[g * 8 + q];
-                    }
-                    uint4 sl[NS];
-                    slice8(y, emq, sl);
-                    const uint32_t o = coff(i - rb * CM, g * 8, kp) >> 1;
-#pragma unroll
-                    for (int j = 0; j < NS; ++j)
-                        *reinterpret_cast<uint4 *>(wsl + ((size_t)rb * NS + j) * CM * kp + o) = sl[j];
-                }
+                for (int j = 0; j < NS; ++j)
+                    *reinterpret_cast<uint4 *>(wsl + ((size_t)rb * NS + j) * CM * kp + o) = sl[j];
+                if (g == 0) wex[i] = em;
             }
-            wex[i] = em;
         }
     }
     return true;
