@@ -54,7 +54,7 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush: the
 #   mean of two launches, 102.0 MB read + 78.0 MB written (the working set stays
 #   in L2); command in profiles/sweep_kernel_fp64_emulated_n2048_k32.md.
-NCU_TRAFFIC = {"0b35178a808c3f14:single": (101.562624e6 + 80.118016e6 + 102.626560e6 + 78.051584e6) / 2}
+NCU_TRAFFIC = {"6d6388aee8b9c394:single": (101.697280e6 + 79.211264e6 + 101.731584e6 + 77.067264e6) / 2}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],

@@ -994,7 +994,11 @@ __host__ __device__ inline Layout layout(int N, int kp)
 constexpr int NBAR = 8;
 // arrivals per phase: 6, 7 are phase A's stage-full barriers (one per warp)
 __host__ __device__ inline unsigned bar_count(int q) { return q >= 6 ? 8u : 1u; }
-__host__ __device__ inline size_t raw_bytes(int) { return (size_t)AM * AK * sizeof(double); }
+// phase A's raw fp64 K-blocks: column stride RS = AK + 2 doubles, so that the
+// 16-byte accesses of a warp (lanes 64 bytes apart in the column, two lanes per
+// column) spread over the shared-memory banks instead of 16 lanes per bank group
+constexpr int RS = AK + 2;
+__host__ __device__ inline size_t raw_bytes(int) { return (size_t)AM * RS * sizeof(double); }
 __host__ __device__ inline size_t phase_a_bytes(int kp)
 {
     return NSLOT * raw_bytes(kp) + (size_t)2 * NS * AM * AK * 2 + (size_t)NSLOT * NS * kp * AK * 2;
@@ -1268,7 +1272,7 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
         const int nA = Ly.nca * Ly.nrc;
         const int nkb = AR / AK;
         const size_t aplane = (size_t)AM * AK, bplane = (size_t)kp * AK;   // fp16 elements
-        double *raw = (double *)reg;                                       // [NSLOT][AM * AK]
+        double *raw = (double *)reg;                                       // [NSLOT][AM][RS]
         __half *sa = (__half *)(reg + NSLOT * raw_bytes(kp));              // [2][NS][AM*AK]
         __half *sv = sa + 2 * NS * aplane;                                 // [NSLOT][NS][kp*AK]
         const __half *vg = (const __half *)(scr + Ly.vsl);                 // [nrc*AR/AK][NS][kp*AK]
@@ -1295,13 +1299,13 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
             auto issue = [&](int kb, int kbv) {
                 if (kb < nkb) {
                     const int i = r0 + kb * AK;
-                    double *dst = raw + (size_t)(kb % NSLOT) * AM * AK;
+                    double *dst = raw + (size_t)(kb % NSLOT) * AM * RS;
                     const bool ina = i < ld && ca < ncol;
                     const double *srca = Ab + (size_t)(c0 + (ina ? ca : 0)) * ld + (ina ? i + kk : 0);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                     ::"r"(su32(dst + (size_t)ca * AK + kk + 2 * q)), "l"(ina ? srca + 2 * q : srca),
+                                     ::"r"(su32(dst + (size_t)ca * RS + kk + 2 * q)), "l"(ina ? srca + 2 * q : srca),
                                        "r"(ina ? 16 : 0) : "memory");
                 }
                 if (kbv >= 0 && kbv < nkb) {
@@ -1324,14 +1328,14 @@ __device__ __noinline__ bool oz_phase_a(const SweepParams<T> &p, int w, int k, i
                 issue(kb + 2, kb + 1);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");     // blocks kb (raw, V) complete
                 const int i = r0 + kb * AK;
-                const double *rw = raw + (size_t)sl * AM * AK;
+                const double *rw = raw + (size_t)sl * AM * RS;
                 if (!bad) {
                     {
                         double x[8];
                         const bool in = ca < ncol && i < ld;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + ca * AK + kk + 2 * q)
+                            const double2 u = in ? *reinterpret_cast<const double2 *>(rw + ca * RS + kk + 2 * q)
                                                  : make_double2(0.0, 0.0);
                             x[2 * q] = u.x;
                             x[2 * q + 1] = u.y;
