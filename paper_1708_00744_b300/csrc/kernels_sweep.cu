@@ -652,6 +652,18 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t *r)
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// the same load without the wait: several loads in flight, then tmem_wait_ld()
+__device__ __forceinline__ void ld16_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+        " [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // shared-memory region of the tensor-core flush, for kp = K rounded up to 16:
 // two stages of the T' operands (A^{-1} and V blocks), T as the update's B
 // operand, two stages of the update's W block, four mbarriers
@@ -1692,20 +1704,26 @@ __device__ __noinline__ bool oz_phase_c(const SweepParams<T> &p, int w, int k, i
             }
             for (int j0 = cb; j0 < cb + 32; j0 += 16) {
                 long long S[16];
-                uint32_t v[16];
+                uint32_t v[3][16];
+                const uint32_t lrow = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)j0;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) S[e] = 0;
+                // the diagonals three loads at a time, one wait per three
 #pragma unroll
-                for (int d = 0; d < NS - 1; ++d) {
-                    ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(d * CN + j0), v);
+                for (int d0 = 0; d0 < NS - 1; d0 += 3) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + __float2int_rz(__uint_as_float(v[e]));
+                    for (int t = 0; t < 3; ++t) ld16_nw(lrow + (uint32_t)((d0 + t) * CN), v[t]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) S[e] = S[e] * 256 + __float2int_rz(__uint_as_float(v[t][e]));
                 }
                 // S = sum_{d <= 5} D_d 2^(8(5 - d)) < 2^61.02; the d = 6 diagonal
                 // joins as 2 S + round(D_6 / 2^7) (an error of 2^-63 of the leading term)
-                ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)((NS - 1) * CN + j0), v);
+                ld16(lrow + (uint32_t)((NS - 1) * CN), v[0]);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) S[e] = 2 * S[e] + ((__float2int_rz(__uint_as_float(v[e])) + 64) >> 7);
+                for (int e = 0; e < 16; ++e) S[e] = 2 * S[e] + ((__float2int_rz(__uint_as_float(v[0][e])) + 64) >> 7);
                 double y[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) y[e] = xa[e] - scaled_i64(S[e], ei + stx[b * CN + j0 + e] - 2101);
