@@ -54,7 +54,7 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush: the
 #   mean of two launches, 102.0 MB read + 78.0 MB written (the working set stays
 #   in L2); command in profiles/sweep_kernel_fp64_emulated_n2048_k32.md.
-NCU_TRAFFIC = {"00a5f46ce0b8b984:single": (101.588224e6 + 78.799104e6 + 101.716480e6 + 75.908352e6) / 2}
+NCU_TRAFFIC = {"8bcbd83ca33cca6d:single": (101.862400e6 + 78.765312e6 + 101.406720e6 + 76.131072e6) / 2}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],
