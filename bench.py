@@ -54,7 +54,7 @@ HBM_PEAK_FALLBACK_GBS = 6400.0
 #   single: one sweep of one N = 2048 fp64 walker, K = 32, emulated flush: the
 #   mean of two launches, 102.0 MB read + 78.0 MB written (the working set stays
 #   in L2); command in profiles/sweep_kernel_fp64_emulated_n2048_k32.md.
-NCU_TRAFFIC = {"8bcbd83ca33cca6d:single": (101.862400e6 + 78.765312e6 + 101.406720e6 + 76.131072e6) / 2}
+NCU_TRAFFIC = {"33173a30f5baa151:single": (102.494208e6 + 78.629376e6 + 101.690624e6 + 76.275712e6) / 2}
 
 WORKLOADS = {
     "single": [dict(N=2048, batch=1)],

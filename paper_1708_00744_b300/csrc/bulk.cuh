@@ -68,6 +68,15 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// pivot-search key of x: the bit pattern of |x|, which orders non-negative
+// doubles as their values do, compared on the integer pipe; NaN gives -2, below
+// the empty key -1, so that it never wins (as an fp64 comparison leaves it)
+__device__ __forceinline__ long long gj_key(double x)
+{
+    const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
+    return b > 0x7FF0000000000000ll ? -2ll : b;
+}
+
 __device__ __forceinline__ void mbar_init_count(unsigned long long *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");

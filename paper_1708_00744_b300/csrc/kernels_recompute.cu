@@ -29,6 +29,7 @@
 
 #include "qmcdu_internal.cuh"
 #include "philox.cuh"
+#include "bulk.cuh"
 
 namespace qmcdu {
 
@@ -190,27 +191,27 @@ __global__ void __launch_bounds__(PTHREADS) gj_panel_kernel(int N, int ld, int n
     int sg = 1;
     for (int q = 0; q < nbe; ++q) {
         const int c = c0 + q;
-        // pivot search
-        double best = -1.0;
+        // pivot search, by integer keys (gj_key)
+        long long best = -1;
         int bi = N;
         for (int i = c + tid; i < N; i += blockDim.x) {
-            const double v = fabs(S[q * N + i]);
+            const long long v = gj_key(S[q * N + i]);
             if (v > best) { best = v; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
-        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        if (lane == 0) { wval[warp] = __longlong_as_double(best); widx[warp] = bi; }
         __syncthreads();
         if (warp == 0) {
-            best = lane < (blockDim.x >> 5) ? wval[lane] : -1.0;
+            best = lane < (blockDim.x >> 5) ? __double_as_longlong(wval[lane]) : -1;
             bi = lane < (blockDim.x >> 5) ? widx[lane] : N;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }

@@ -2699,34 +2699,34 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
     int sg = 1, singular = 0;
     for (int q = 0; q < nbe; ++q) {
         const int c = c0 + q, par = q & 1;
-        // my candidate
-        double best = -1.0;
+        // my candidate, by integer keys (gj_key)
+        long long best = -1;
         int bi = N;
         for (int li = tid; li < nr; li += GJ_THREADS) {
             const int gi = i0 + li;
             if (gi < c) continue;
-            const double v = fabs(S[q * Rr + li]);
+            const long long v = gj_key(S[q * Rr + li]);
             if (v > best || (v == best && gi < bi)) { best = v; bi = gi; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
-        if (lane == 0) { wval[warp] = best; widx[warp] = bi; }
+        if (lane == 0) { wval[warp] = __longlong_as_double(best); widx[warp] = bi; }
         __syncthreads();
         if (warp == 0) {
-            best = lane < GJ_THREADS / 32 ? wval[lane] : -1.0;
+            best = lane < GJ_THREADS / 32 ? __double_as_longlong(wval[lane]) : -1;
             bi = lane < GJ_THREADS / 32 ? widx[lane] : N;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
             if (lane == 0) {
-                g.candv[par * P + r] = best;
+                g.candv[par * P + r] = __longlong_as_double(best);
                 g.candi[par * P + r] = bi;
                 win_s = bi;
             }
@@ -2740,16 +2740,16 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
         if (!group_barrier(ctr, (++nbar) * P, status, budget_ns)) return;
         // the winner: largest candidate, lowest row on ties, in a fixed order
         if (warp == 0) {
-            double bv = -1.0;
+            long long bv = -1;
             int bidx = N, brk = 0;
             for (int k = lane; k < P; k += 32) {
-                const double v = __ldcg(g.candv + par * P + k);
+                const long long v = __double_as_longlong(__ldcg(g.candv + par * P + k));
                 const int i = __ldcg(g.candi + par * P + k);
                 if (v > bv || (v == bv && i < bidx)) { bv = v; bidx = i; brk = k; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
                 const int ok_ = __shfl_xor_sync(0xffffffffu, brk, o);
                 if (ov > bv || (ov == bv && oi < bidx)) { bv = ov; bidx = oi; brk = ok_; }
@@ -2847,13 +2847,6 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel_mc_kernel(int N, int ld, 
 // barriers (a singular pivot is seen by all), and a last barrier ends every
 // read of a sibling's shared memory before any CTA exits.
 constexpr int GJ_CL = 16;
-// pivot-search key of x: the bit pattern of |x| (non-negative doubles order as
-// their patterns do); NaN gives -2, below the empty key -1, so it never wins
-__device__ __forceinline__ long long gj_key(double x)
-{
-    const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
-    return b > 0x7FF0000000000000ll ? -2ll : b;
-}
 __global__ void __launch_bounds__(GJ_THREADS) gj_panel_cl_kernel(int N, int ld, int nb, int c0, int nbe,
                                                                 double *work, int *piv, double *Lt, double *R,
                                                                 double *lu_logabs, int *lu_sign, int *status)
